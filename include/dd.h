@@ -1,0 +1,187 @@
+/*
+ * dd.h -- C ABI of the GB300 profiled-dedispersion library (libdd.so).
+ *
+ * The library computes, for every trial dispersion measure d, the profiled
+ * dedispersion sum of eq. p_dedisp (Sec. 2.1)
+ *
+ *     out[d][t] = sum_c sum_{k < n_dc} w_dck * I[c][t_offset + t + delta_dc + k]
+ *
+ * over a channelised filterbank I[c][t], followed by boxcar S/N detection over a
+ * list of widths (eq. snr, Sec. 2.1, and the boxcar detector of Sec. 5).  Each trial
+ * d has a programmable per-channel profile: a start delay delta_dc (Sec. 3, t_A), a
+ * tap count n_dc covering the intra-channel smear (Sec. 3, Delta tau_c) and per-tap
+ * weights w_dck.
+ *
+ * Conventions
+ *   - Frequencies in MHz, times in ms, DM in pc cm^-3.  k_dm = 1/kappa in ms GHz^2.
+ *   - Channel c has low edge f_lo_mhz + c*df_mhz (descending = 0) or the mirror image
+ *     (descending = 1).  nu_c is the channel's highest frequency (Sec. 3).
+ *   - Arrays are row-major.  "d_" pointers are CUDA device pointers; all others are
+ *     host pointers.  The caller owns every data buffer and stream; the plan owns its
+ *     tables and workspace.  `stream` is a cudaStream_t (NULL = legacy default stream).
+ *   - Device calls are asynchronous and stream-ordered.  Argument and plan errors are
+ *     reported synchronously by the return value; CUDA launch errors as DD_ERR_CUDA.
+ *   - A plan may be used from one stream at a time (its workspace is shared).
+ *   - Input rows are `in_ld` elements apart; in_ld * element size must be a multiple of
+ *     16 bytes and the input base pointer 16-byte aligned (rows are staged in 16-byte
+ *     chunks).  Violations return DD_ERR_ARG.
+ *   - No call here allocates device memory except dd_plan_create / dd_set_profiles /
+ *     the first device call on a plan (tables) and dd_boxcar_snr when the width
+ *     count grows (normaliser workspace).
+ */
+#ifndef DD_H
+#define DD_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct dd_plan_s* dd_plan_t;
+
+typedef enum {
+    DD_OK = 0,
+    DD_ERR_ARG = 1,         /* bad argument (null pointer, size, alignment, range)      */
+    DD_ERR_OVERFLOW = 2,    /* a size or sum would overflow the integer type used       */
+    DD_ERR_OOM = 3,         /* host or device allocation failed                         */
+    DD_ERR_CUDA = 4,        /* a CUDA runtime call or kernel launch failed              */
+    DD_ERR_STATE = 5,       /* call not valid in the plan's current state               */
+    DD_ERR_TIMEOUT = 6,     /* a bounded device wait gave up                            */
+    DD_ERR_CAPACITY = 7,    /* more results than the caller's buffer holds (truncated)  */
+    DD_ERR_UNSUPPORTED = 8  /* valid request outside what the kernels implement         */
+} dd_status;
+
+typedef enum { DD_U8 = 0, DD_F32 = 1 } dd_dtype;
+
+/* Band and sampling of the filterbank (Sec. 2.1, Sec. 3). */
+typedef struct {
+    int32_t nchan;       /* C > 0                                                  */
+    double f_lo_mhz;     /* lower edge of the band, > 0                            */
+    double df_mhz;       /* channel width Delta nu, > 0                            */
+    int32_t descending;  /* 0: channel 0 is the lowest frequency                   */
+    double dt_ms;        /* sampling time Delta t, > 0                             */
+    int64_t nsamp;       /* default samples per dedispersion call                  */
+    int32_t in_type;     /* dd_dtype of I                                          */
+    double k_dm;         /* 1/kappa in ms GHz^2; <= 0 selects 4.15                 */
+} dd_band;
+
+/* One detection: trial d, width index, first sample t of the boxcar, and S/N. */
+typedef struct {
+    int32_t dm_index;
+    int32_t width_index;
+    int32_t t;
+    float snr;
+} dd_candidate;
+
+/* Trial DM list of eq. trial DMs (Sec. 6.3):
+ *   DM_n = DM_0 + (2 eps / C) sum_{i<n} sqrt(DM_i^2 + DM_diag^2 + DM_tau^2),
+ * with DM_diag and DM_tau of Sec. 6.2 (tau_av_ms = average scattered pulse width
+ * tau'_av) and eps found by bisection so that DM_{n-1} = dm_max.  smear_terms = 2
+ * keeps both smear terms as printed; 1 keeps DM_diag only.  Host only; writes n
+ * doubles to dms_out and the DM error factor to *eps_out (may be NULL).
+ * Errors: DD_ERR_ARG for n < 2, dm_max <= dm0, bad band or null output. */
+dd_status dd_trial_dms(const dd_band* band, double dm0, double dm_max, int32_t n,
+                       double tau_av_ms, int32_t smear_terms, double* dms_out,
+                       double* eps_out);
+
+/* Creates a plan for `ndm` trial DMs (host array, copied).  Builds the default
+ * profile tables on the host (no device work):
+ *   delta_dc = floor(k_dm * DM_d * (nu_c^-2 - nu_top^-2) / dt)        (Sec. 3, t_A)
+ *   n_dc     = max(1, ceil(k_dm * DM_d * ((nu_c - dnu)^-2 - nu_c^-2) / dt))
+ * with unit weights.  Errors: DD_ERR_ARG (null, ndm < 1, bad band, DM < 0),
+ * DD_ERR_OOM. */
+dd_status dd_plan_create(dd_plan_t* plan, const dd_band* band, const double* dms,
+                         int32_t ndm);
+
+/* Replaces the profiles (host arrays, copied).  delay [ndm][nchan] (NULL keeps the
+ * formula), ntaps [ndm][nchan] (NULL keeps the formula), w [ndm][nchan][kmax] fp32
+ * (NULL = unit weights; taps beyond n_dc are ignored).  Requires delay >= 0,
+ * 1 <= n_dc, and n_dc <= kmax when w is given.  Unit-weight uint8 plans produce
+ * int32 sums; all other plans produce fp32 sums.  Errors: DD_ERR_ARG,
+ * DD_ERR_OVERFLOW (int32 sums could overflow), DD_ERR_UNSUPPORTED (profile too wide
+ * for the kernels' shared-memory staging). */
+dd_status dd_set_profiles(dd_plan_t plan, const int32_t* delay, const int32_t* ntaps,
+                          const float* w, int32_t kmax);
+
+/* Replaces the per-tap weights from device memory (stream-ordered copy; no host
+ * round trip).  d_w is [ndm][nchan][kmax] fp32; the delay and tap tables are kept and
+ * every n_dc must be <= kmax.  A unit-weight plan becomes a weighted one (fp32 sums).
+ * Meant for training loops (the autograd binding calls it before each forward and
+ * backward).  Errors: DD_ERR_ARG, DD_ERR_OOM, DD_ERR_CUDA. */
+dd_status dd_set_weights_device(dd_plan_t plan, const float* d_w, int32_t kmax, void* stream);
+
+/* Plan facts: t_out = nsamp - d_max for the default nsamp, d_max = max(delta + n - 1),
+ * kmax = max n_dc, ns_total = sum_{d,c} n_dc, out_is_int = 1 when sums are int32.
+ * Any output pointer may be NULL. */
+dd_status dd_plan_info(dd_plan_t plan, int64_t* t_out, int32_t* d_max, int32_t* kmax,
+                       int64_t* ns_total, int32_t* out_is_int);
+
+/* Copies the plan's delay and tap tables ([ndm][nchan] int32, host) out. */
+dd_status dd_get_tables(dd_plan_t plan, int32_t* delay, int32_t* ntaps);
+
+/* eq. p_dedisp.  d_in: [nchan][in_ld] uint8 or fp32 (band.in_type); d_out: [ndm][out_ld]
+ * int32 or fp32 (see dd_set_profiles).  Computes out[d][t] for 0 <= t < nsamp - d_max,
+ * reading columns t_offset .. t_offset + nsamp - 1 of every row (nsamp <= 0 uses the
+ * band's).  Chunked calls with t_offset advancing by L reproduce the one-shot result.
+ * Errors: DD_ERR_ARG (null, alignment, t_offset + nsamp > in_ld, out_ld too small,
+ * nsamp <= d_max), DD_ERR_CUDA. */
+dd_status dd_dedisperse(dd_plan_t plan, const void* d_in, int64_t in_ld, int64_t t_offset,
+                        int64_t nsamp, void* d_out, int64_t out_ld, void* stream);
+
+/* Per-channel noise statistics of the input over columns t_offset .. t_offset+nsamp-1:
+ * mean and population standard deviation (fp64, device arrays of nchan), the cell
+ * noise sigma_n of Sec. 2.1 as measured.  Errors: DD_ERR_ARG, DD_ERR_CUDA. */
+dd_status dd_channel_stats(dd_plan_t plan, const void* d_in, int64_t in_ld,
+                           int64_t t_offset, int64_t nsamp, double* d_mean, double* d_std,
+                           void* stream);
+
+/* Boxcar S/N of every trial and width (eq. snr; Sec. 5 boxcar detector).
+ * d_series: the dedisperse output ([ndm][ld], int32 or fp32 as the plan produces),
+ * t_len valid samples per row.  widths: host array of nw strictly increasing widths,
+ * 1 <= w <= t_len.  For each (d, w):
+ *   B_w[t] = sum_{j<w} x[d][t+j],  0 <= t <= t_len - w,
+ *   snr    = (B_w - mu_dw) / sigma_dw,
+ * where mu_dw and sigma_dw are the mean and deviation of B_w on noise with the given
+ * per-channel mean and std (device fp64 [nchan]):
+ *   mu_dw = sum_c mu_c sum_m v_dcm,  sigma_dw^2 = sum_c sigma_c^2 sum_m v_dcm^2,
+ *   v_dc = w_dc (*) 1_w   (eq. P_N_dedisp generalised to weighted boxcar sums).
+ * Writes d_peak_snr [ndm][nw] (fp32) and d_peak_t [ndm][nw] (earliest t of the
+ * maximum).  If d_cands != NULL, every (d, w) whose peak exceeds thresh is appended
+ * to d_cands (capacity cap, order unspecified) and *d_ncands counts them all (it must
+ * be zeroed by the caller); overflow is visible as *d_ncands > cap.  Integer series
+ * are summed exactly (int32 or int64 around a per-trial integer offset).
+ * Errors: DD_ERR_ARG, DD_ERR_OOM, DD_ERR_CUDA. */
+dd_status dd_boxcar_snr(dd_plan_t plan, const void* d_series, int64_t ld, int64_t t_len,
+                        const int32_t* widths, int32_t nw, const double* d_chan_mean,
+                        const double* d_chan_std, float* d_peak_snr, int32_t* d_peak_t,
+                        float thresh, dd_candidate* d_cands, int32_t cap,
+                        int32_t* d_ncands, void* stream);
+
+/* Adjoint of the weighted map of eq. p_dedisp (no counterpart in the paper): given
+ * g = d(loss)/d(out) (d_gout [ndm][gout_ld] fp32, nsamp - d_max valid columns),
+ *   d_gw [ndm][nchan][kmax] : gw_dck   = sum_t g[d][t] I[c][t_offset + t + delta + k]
+ *                             (zero for k >= n_dc), NULL to skip;
+ *   d_gin [nchan][gin_ld]   : gI[c][tau] += sum_{d,k} w_dck g[d][tau - t_offset - delta - k]
+ *                             for every column, NULL to skip.  Columns outside
+ *                             t_offset .. t_offset + nsamp - 1 are left unchanged; the
+ *                             columns inside are overwritten.
+ * fp32 plans only (fp32 input).  Errors: DD_ERR_ARG, DD_ERR_UNSUPPORTED, DD_ERR_CUDA. */
+dd_status dd_backward(dd_plan_t plan, const float* d_in, int64_t in_ld, int64_t t_offset,
+                      int64_t nsamp, const float* d_gout, int64_t gout_ld, float* d_gw,
+                      float* d_gin, int64_t gin_ld, void* stream);
+
+/* Releases the plan's host and device memory (after its work has finished). */
+dd_status dd_plan_destroy(dd_plan_t plan);
+
+/* Static, human-readable name of a status code. */
+const char* dd_status_str(dd_status s);
+
+/* Library version, as major*10000 + minor*100 + patch. */
+int32_t dd_version(void);
+
+#ifdef __cplusplus
+}
+#endif
+#endif /* DD_H */

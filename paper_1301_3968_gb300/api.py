@@ -1,0 +1,246 @@
+"""Python binding of libdd.so: argument marshalling around the C ABI (include/dd.h).
+
+Every step of the computation runs in the library's CUDA kernels; PyTorch supplies
+device memory and the current stream.  There is no CPU fallback: a missing library
+raises at import of this module's first call.
+"""
+from __future__ import annotations
+
+import ctypes
+from dataclasses import dataclass
+
+import numpy as np
+import torch
+
+from . import _lib
+from ._lib import DD_F32, DD_U8, check, dd_band, dd_candidate
+
+
+@dataclass(frozen=True)
+class Band:
+    """Filterbank geometry (Sec. 2.1): C channels of width df from f_lo, sampling dt."""
+    nchan: int
+    f_lo_mhz: float
+    df_mhz: float
+    dt_ms: float
+    nsamp: int = 0
+    in_type: str = "u8"          # "u8" or "f32"
+    descending: bool = False
+    k_dm: float = 4.15           # 1/κ in ms·GHz²
+
+    def c_struct(self) -> dd_band:
+        return dd_band(int(self.nchan), float(self.f_lo_mhz), float(self.df_mhz),
+                       int(bool(self.descending)), float(self.dt_ms), int(self.nsamp),
+                       DD_U8 if self.in_type == "u8" else DD_F32, float(self.k_dm))
+
+
+def _ptr(t) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if t is None else t.data_ptr())
+
+
+def _np_ptr(a) -> ctypes.c_void_p:
+    return ctypes.c_void_p(0 if a is None else a.ctypes.data)
+
+
+def _stream(stream=None) -> ctypes.c_void_p:
+    s = torch.cuda.current_stream() if stream is None else stream
+    return ctypes.c_void_p(s.cuda_stream)
+
+
+def trial_dms(band: Band, dm0: float, dm_max: float, n: int, tau_av_ms: float | None = None,
+              smear_terms: int = 2):
+    """Trial DMs of eq. trial DMs (Sec. 6.3) ending exactly at dm_max; returns (dms, ε)."""
+    lib = _lib.load()
+    out = np.zeros(n, dtype=np.float64)
+    eps = ctypes.c_double(0.0)
+    b = band.c_struct()
+    tau = band.dt_ms if tau_av_ms is None else tau_av_ms
+    check(lib.dd_trial_dms(ctypes.byref(b), dm0, dm_max, n, tau, smear_terms, _np_ptr(out),
+                           ctypes.cast(ctypes.byref(eps), ctypes.c_void_p)), "dd_trial_dms")
+    return out, eps.value
+
+
+class Plan:
+    """A dedispersion plan: trial DMs, per-(trial, channel) delays, taps and weights."""
+
+    def __init__(self, band: Band, dms):
+        self._lib = _lib.load()
+        self.band = band
+        self.dms = np.ascontiguousarray(dms, dtype=np.float64)
+        self.ndm = len(self.dms)
+        self._b = band.c_struct()
+        h = ctypes.c_void_p()
+        check(self._lib.dd_plan_create(ctypes.byref(h), ctypes.byref(self._b), _np_ptr(self.dms),
+                                       self.ndm), "dd_plan_create")
+        self._h = h
+        self._kw = 0
+
+    # ------------------------------------------------------------------ profiles
+    def set_profiles(self, delay=None, taps=None, weights=None) -> None:
+        """Host tables: delay/taps int32 [D][C], weights fp32 [D][C][K] (None = unit)."""
+        d = None if delay is None else np.ascontiguousarray(delay, dtype=np.int32)
+        t = None if taps is None else np.ascontiguousarray(taps, dtype=np.int32)
+        w = None if weights is None else np.ascontiguousarray(weights, dtype=np.float32)
+        for a, shp in ((d, (self.ndm, self.band.nchan)), (t, (self.ndm, self.band.nchan))):
+            if a is not None and a.shape != shp:
+                raise ValueError(f"table shape {a.shape} != {shp}")
+        k = 0
+        if w is not None:
+            if w.ndim != 3 or w.shape[:2] != (self.ndm, self.band.nchan):
+                raise ValueError(f"weights shape {w.shape}")
+            k = w.shape[2]
+        check(self._lib.dd_set_profiles(self._h, _np_ptr(d), _np_ptr(t), _np_ptr(w), k),
+              "dd_set_profiles")
+        self._kw = k
+
+    def set_weights(self, w: torch.Tensor, stream=None) -> None:
+        """Device weights [D][C][K] fp32 (contiguous), copied in stream order."""
+        if not (w.is_cuda and w.dtype == torch.float32 and w.is_contiguous() and w.dim() == 3):
+            raise ValueError("weights must be a contiguous CUDA float32 [D][C][K] tensor")
+        check(self._lib.dd_set_weights_device(self._h, _ptr(w), int(w.shape[2]), _stream(stream)),
+              "dd_set_weights_device")
+        self._kw = int(w.shape[2])
+
+    def info(self) -> dict:
+        t_out = ctypes.c_int64()
+        d_max = ctypes.c_int32()
+        kmax = ctypes.c_int32()
+        ns = ctypes.c_int64()
+        oi = ctypes.c_int32()
+        check(self._lib.dd_plan_info(self._h, *(ctypes.cast(ctypes.byref(v), ctypes.c_void_p)
+                                                for v in (t_out, d_max, kmax, ns, oi))),
+              "dd_plan_info")
+        return dict(t_out=t_out.value, d_max=d_max.value, kmax=kmax.value, ns_total=ns.value,
+                    out_is_int=bool(oi.value))
+
+    @property
+    def d_max(self) -> int:
+        return self.info()["d_max"]
+
+    def tables(self):
+        d = np.zeros((self.ndm, self.band.nchan), np.int32)
+        t = np.zeros((self.ndm, self.band.nchan), np.int32)
+        check(self._lib.dd_get_tables(self._h, _np_ptr(d), _np_ptr(t)), "dd_get_tables")
+        return d, t
+
+    # ------------------------------------------------------------------ compute
+    def _check_input(self, x: torch.Tensor):
+        want = torch.uint8 if self.band.in_type == "u8" else torch.float32
+        if not x.is_cuda or x.dtype != want or x.dim() != 2 or x.stride(1) != 1:
+            raise ValueError(f"input must be a CUDA {want} [C][ld] tensor with unit column stride")
+        if x.shape[0] != self.band.nchan:
+            raise ValueError("input rows != nchan")
+        return x.stride(0)
+
+    def out_dtype(self):
+        return torch.int32 if self.info()["out_is_int"] else torch.float32
+
+    def dedisperse(self, x: torch.Tensor, t_offset: int = 0, nsamp: int | None = None,
+                   out: torch.Tensor | None = None, stream=None) -> torch.Tensor:
+        """eq. p_dedisp for every trial: returns [D][nsamp - d_max]."""
+        ld = self._check_input(x)
+        nsamp = (x.shape[1] - t_offset) if nsamp is None else nsamp
+        t_out = nsamp - self.d_max
+        if out is None:
+            out = torch.empty((self.ndm, max(t_out, 0)), dtype=self.out_dtype(), device=x.device)
+        check(self._lib.dd_dedisperse(self._h, _ptr(x), ld, t_offset, nsamp, _ptr(out),
+                                      out.stride(0), _stream(stream)), "dd_dedisperse")
+        return out
+
+    def channel_stats(self, x: torch.Tensor, t_offset: int = 0, nsamp: int | None = None,
+                      stream=None):
+        ld = self._check_input(x)
+        nsamp = (x.shape[1] - t_offset) if nsamp is None else nsamp
+        mean = torch.empty(self.band.nchan, dtype=torch.float64, device=x.device)
+        sd = torch.empty_like(mean)
+        check(self._lib.dd_channel_stats(self._h, _ptr(x), ld, t_offset, nsamp, _ptr(mean),
+                                         _ptr(sd), _stream(stream)), "dd_channel_stats")
+        return mean, sd
+
+    def boxcar_snr(self, series: torch.Tensor, widths, mean: torch.Tensor, sd: torch.Tensor,
+                   t_len: int | None = None, thresh: float | None = None, cap: int = 0,
+                   stream=None):
+        """Boxcar S/N (eq. snr; Sec. 5): returns (peak_snr [D][W], peak_t [D][W], cands)."""
+        wl = np.ascontiguousarray(widths, dtype=np.int32)
+        t_len = series.shape[1] if t_len is None else t_len
+        dev = series.device
+        peak = torch.empty((self.ndm, len(wl)), dtype=torch.float32, device=dev)
+        arg = torch.empty((self.ndm, len(wl)), dtype=torch.int32, device=dev)
+        cands = ncand = None
+        if thresh is not None and cap > 0:
+            cands = torch.zeros((cap, 4), dtype=torch.int32, device=dev)
+            ncand = torch.zeros(1, dtype=torch.int32, device=dev)
+        check(self._lib.dd_boxcar_snr(self._h, _ptr(series), series.stride(0), t_len,
+                                      _np_ptr(wl), len(wl), _ptr(mean), _ptr(sd), _ptr(peak),
+                                      _ptr(arg), float(thresh if thresh is not None else np.inf),
+                                      _ptr(cands), int(cap), _ptr(ncand), _stream(stream)),
+              "dd_boxcar_snr")
+        if cands is None:
+            return peak, arg, None
+        return peak, arg, (cands, ncand)
+
+    def backward(self, x: torch.Tensor, gout: torch.Tensor, t_offset: int = 0,
+                 nsamp: int | None = None, want_gw: bool = True, want_gin: bool = True,
+                 stream=None):
+        """Adjoint of the weighted map: (gw [D][C][K], gI [C][ld])."""
+        ld = self._check_input(x)
+        nsamp = (x.shape[1] - t_offset) if nsamp is None else nsamp
+        gw = gin = None
+        if want_gw:
+            gw = torch.empty((self.ndm, self.band.nchan, self._kw), dtype=torch.float32, device=x.device)
+        if want_gin:
+            gin = torch.zeros_like(x)
+        check(self._lib.dd_backward(self._h, _ptr(x), ld, t_offset, nsamp, _ptr(gout),
+                                    gout.stride(0), _ptr(gw), _ptr(gin),
+                                    gin.stride(0) if gin is not None else 0, _stream(stream)),
+              "dd_backward")
+        return gw, gin
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.dd_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+def candidates_to_list(cands) -> list[tuple[int, int, int, float]]:
+    """Decodes the (cap, 4) int32 candidate buffer into (d, width_index, t, snr) tuples."""
+    buf, n = cands
+    k = min(int(n.item()), buf.shape[0])
+    raw = buf[:k].cpu().numpy()
+    snr = raw[:, 3].copy().view(np.float32)
+    return [(int(r[0]), int(r[1]), int(r[2]), float(s)) for r, s in zip(raw, snr)]
+
+
+class DDFunction(torch.autograd.Function):
+    """Differentiable profiled dedispersion: out = A(w) I.
+
+    Forward stores only its inputs (I, w); the dedispersed series is not kept, and any
+    later use of it is recomputed (checkpointing).  Backward calls the adjoint kernels
+    for ∂/∂w and ∂/∂I.
+    """
+
+    @staticmethod
+    def forward(ctx, x, w, plan, t_offset=0, nsamp=None):
+        plan.set_weights(w.detach().contiguous())
+        out = plan.dedisperse(x.detach(), t_offset=t_offset, nsamp=nsamp)
+        ctx.save_for_backward(x, w)
+        ctx.plan = plan
+        ctx.t_offset = t_offset
+        ctx.nsamp = nsamp
+        return out
+
+    @staticmethod
+    def backward(ctx, gout):
+        x, w = ctx.saved_tensors
+        plan = ctx.plan
+        plan.set_weights(w.detach().contiguous())
+        gw, gin = plan.backward(x.detach(), gout.contiguous(), t_offset=ctx.t_offset,
+                                nsamp=ctx.nsamp, want_gw=ctx.needs_input_grad[1],
+                                want_gin=ctx.needs_input_grad[0])
+        return gin, gw, None, None, None

@@ -1,0 +1,412 @@
+// Detection statistic: per-channel noise statistics, the boxcar normaliser and the
+// boxcar S/N scan (eq. snr and eq. P_N_dedisp, Sec. 2.1; boxcar detector, Sec. 5).
+//
+//   B_w[t] = sum_{j<w} x[d][t+j],      snr = (B_w - mu_dw) / sigma_dw
+//   mu_dw = w * sum_c mu_c s_dc          (s_dc = sum_k w_dck)
+//   sigma_dw^2 = sum_c sigma_c^2 Q_dc(w),  Q_dc(w) = || w_dc (*) 1_w ||^2
+//
+// All reductions run in a fixed order, so results are deterministic.
+#include <cfloat>
+#include <climits>
+#include <cstdint>
+
+#include "dd_internal.h"
+
+namespace dd {
+namespace {
+
+// ----------------------------------------------------------------------------- stats
+
+template <typename T>
+__device__ __forceinline__ T warp_sum(T v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// One CTA per channel.  uint8: exact int64 sums of x and x^2.  fp32: double sums of
+// (x - x0) and (x - x0)^2 around the row's first sample, which keeps the variance
+// free of cancellation for rows with a large mean.
+template <typename TIN>
+__global__ void __launch_bounds__(256) k_chan_stats(const TIN* in, int64_t ld, int64_t t_offset,
+                                                    int64_t n, double* mean, double* sd) {
+    const int c = blockIdx.x;
+    const TIN* row = in + (int64_t)c * ld + t_offset;
+    __shared__ double sh1[8], sh2[8];
+    __shared__ long long si1[8], si2[8];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    if (sizeof(TIN) == 1) {
+        long long s1 = 0, s2 = 0;
+        for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+            long long v = (long long)row[t];
+            s1 += v;
+            s2 += v * v;
+        }
+        s1 = warp_sum(s1);
+        s2 = warp_sum(s2);
+        if (lane == 0) {
+            si1[warp] = s1;
+            si2[warp] = s2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            long long a = 0, b = 0;
+            for (int i = 0; i < 8; ++i) {
+                a += si1[i];
+                b += si2[i];
+            }
+            const double m = (double)a / (double)n;
+            double var = (double)b / (double)n - m * m;
+            mean[c] = m;
+            sd[c] = sqrt(var > 0 ? var : 0.0);
+        }
+    } else {
+        const double x0 = (double)row[0];
+        double s1 = 0, s2 = 0;
+        for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
+            double v = (double)row[t] - x0;
+            s1 += v;
+            s2 += v * v;
+        }
+        s1 = warp_sum(s1);
+        s2 = warp_sum(s2);
+        if (lane == 0) {
+            sh1[warp] = s1;
+            sh2[warp] = s2;
+        }
+        __syncthreads();
+        if (threadIdx.x == 0) {
+            double a = 0, b = 0;
+            for (int i = 0; i < 8; ++i) {
+                a += sh1[i];
+                b += sh2[i];
+            }
+            const double m = a / (double)n;
+            double var = b / (double)n - m * m;
+            mean[c] = x0 + m;
+            sd[c] = sqrt(var > 0 ? var : 0.0);
+        }
+    }
+}
+
+// ----------------------------------------------------------------------------- normaliser
+
+// || 1_n (*) 1_w ||^2: a trapezoid with plateau min(n,w) of length |n-w|+1.
+__device__ __forceinline__ float q_unit(int n, int w) {
+    const float m = (float)min(n, w);
+    return (m - 1.f) * m * (2.f * m - 1.f) / 3.f + m * m * (float)(abs(n - w) + 1);
+}
+
+// One CTA per trial.  Phase 1: the per-trial offset o_d (rounded for integer series)
+// = expected mean of x_d.  Phase 2: lanes take channels, loop over widths, and the
+// warp sums of sigma_c^2 Q_dc(w) are accumulated per warp and then across warps.
+__global__ void __launch_bounds__(256) k_norm(const int32_t* taps, const float* w, int32_t kpad,
+                                              int32_t nchan, const double* mean, const double* sd,
+                                              const int32_t* widths, int32_t nw, int int_off,
+                                              double* off, float* mu_out, float* isd_out) {
+    extern __shared__ float red[];  // [8][nw]
+    __shared__ double shm[8];
+    const int d = blockIdx.x;
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int32_t* tp = taps + (int64_t)d * nchan;
+    const float* wd = w ? w + (int64_t)d * nchan * kpad : nullptr;
+
+    double m1 = 0.0;
+    for (int c = threadIdx.x; c < nchan; c += blockDim.x) {
+        const int n = tp[c];
+        float s = 0.f;
+        if (wd) {
+            for (int k = 0; k < n; ++k) s += wd[(int64_t)c * kpad + k];
+        } else {
+            s = (float)n;
+        }
+        m1 += mean[c] * (double)s;
+    }
+    m1 = warp_sum(m1);
+    if (lane == 0) shm[warp] = m1;
+    for (int i = threadIdx.x; i < 8 * nw; i += blockDim.x) red[i] = 0.f;
+    __syncthreads();
+    double mu1 = 0.0;
+    for (int i = 0; i < 8; ++i) mu1 += shm[i];
+    const double o = int_off ? rint(mu1) : mu1;
+
+    for (int cb = warp * 32; cb < nchan; cb += 256) {
+        const int c = cb + lane;
+        const bool ok = c < nchan;
+        const int n = ok ? tp[c] : 1;
+        const float s2 = ok ? (float)(sd[c] * sd[c]) : 0.f;
+        // weighted taps: A = (sum w)^2 and Bp = 2 sum_{D>=1} D R(D) give
+        // Q(w) = w A - Bp for w >= n; shorter widths use the direct sum.
+        float A = 0.f, Bp = 0.f;
+        const float* wk = (wd && ok) ? wd + (int64_t)c * kpad : nullptr;
+        if (wk) {
+            float s = 0.f;
+            for (int k = 0; k < n; ++k) s += wk[k];
+            A = s * s;
+            for (int D = 1; D < n; ++D) {
+                float r = 0.f;
+                for (int k = 0; k + D < n; ++k) r += wk[k] * wk[k + D];
+                Bp += 2.f * (float)D * r;
+            }
+        }
+        for (int j = 0; j < nw; ++j) {
+            const int wdt = widths[j];
+            float q;
+            if (!wk) {
+                q = q_unit(n, wdt);
+            } else if (wdt >= n) {
+                q = (float)wdt * A - Bp;
+            } else {
+                float v = 0.f;
+                q = 0.f;
+                for (int m = 0; m < n + wdt - 1; ++m) {
+                    if (m < n) v += wk[m];
+                    if (m >= wdt) v -= wk[m - wdt];
+                    q += v * v;
+                }
+            }
+            float contrib = warp_sum(s2 * q);
+            if (lane == 0) red[warp * nw + j] += contrib;
+        }
+    }
+    __syncthreads();
+    for (int j = threadIdx.x; j < nw; j += blockDim.x) {
+        float v = 0.f;
+        for (int i = 0; i < 8; ++i) v += red[i * nw + j];
+        mu_out[(int64_t)d * nw + j] = (float)((double)widths[j] * (mu1 - o));
+        isd_out[(int64_t)d * nw + j] = v > 0.f ? 1.0f / sqrtf(v) : 0.f;
+    }
+    if (threadIdx.x == 0) off[d] = o;
+}
+
+// ----------------------------------------------------------------------------- boxcar scan
+
+struct BoxArgs {
+    const void* x;
+    int64_t ld;
+    int32_t t_len;
+    int32_t ndm;
+    const int32_t* widths;
+    int32_t nw;
+    const double* off;
+    const float* mu;
+    const float* isd;
+    float* peak;
+    int32_t* arg;
+    float thresh;
+    dd_candidate* cands;
+    int32_t cap;
+    int32_t* ncands;
+};
+
+template <typename T>
+__device__ __forceinline__ T lowest();
+template <>
+__device__ __forceinline__ float lowest<float>() { return -FLT_MAX; }
+template <>
+__device__ __forceinline__ int lowest<int>() { return INT_MIN; }
+template <>
+__device__ __forceinline__ long long lowest<long long>() { return LLONG_MIN; }
+
+constexpr int kBoxS = 31;  // samples per thread segment (odd: conflict-free)
+constexpr int kBoxG = 16;  // widths per CTA
+
+// grid (width groups, trials).  The CTA walks the row in chunks of 256*S samples;
+// thread segments keep G running boxcar sums and their maxima in registers.
+template <typename TX, typename TB>
+__global__ void __launch_bounds__(256) k_boxcar(BoxArgs a) {
+    constexpr int S = kBoxS, G = kBoxG;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TX* xs = (TX*)smem_raw;
+    __shared__ TB rb[8][G];
+    __shared__ int ri[8][G];
+    const int d = blockIdx.y;
+    const int j0 = blockIdx.x * G;
+    const int cnt = min(G, a.nw - j0);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    int wl[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) wl[j] = j < cnt ? a.widths[j0 + j] : INT_MAX / 2;
+    const int wmin = wl[0], wmax = a.widths[j0 + cnt - 1];
+    const TX o = (TX)a.off[d];
+    const TX* xrow = (const TX*)a.x + (int64_t)d * a.ld;
+    TB best[G];
+    int bi[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        best[j] = lowest<TB>();
+        bi[j] = -1;
+    }
+    const int tvalid = a.t_len - wmin + 1;
+    const int chunk = 256 * S;
+    for (int tc = 0; tc < tvalid; tc += chunk) {
+        __syncthreads();
+        for (int i = tid; i < chunk + wmax + 1; i += 256) {
+            const int t = tc + i;
+            xs[i] = t < a.t_len ? (TX)(xrow[t] - o) : TX(0);
+        }
+        __syncthreads();
+        const int ls = tid * S;
+        TB B[G];
+        TB run = TB(0);
+        int idx = 0;
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (j < cnt) {
+                while (idx < wl[j]) {
+                    run += (TB)xs[ls + idx];
+                    ++idx;
+                }
+            }
+            B[j] = run;
+        }
+        for (int s = 0; s < S; ++s) {
+            const int t = tc + ls + s;
+            const TB x0 = (TB)xs[ls + s];
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                if (j < cnt) {
+                    if (t + wl[j] <= a.t_len && B[j] > best[j]) {
+                        best[j] = B[j];
+                        bi[j] = t;
+                    }
+                    B[j] += (TB)xs[ls + s + wl[j]] - x0;
+                }
+            }
+        }
+    }
+    // reduce (max, earliest t) over the CTA
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        TB b = best[j];
+        int i = bi[j];
+#pragma unroll
+        for (int ofs = 16; ofs > 0; ofs >>= 1) {
+            const TB ob = __shfl_xor_sync(0xffffffffu, b, ofs);
+            const int oi = __shfl_xor_sync(0xffffffffu, i, ofs);
+            if (oi >= 0 && (i < 0 || ob > b || (ob == b && oi < i))) {
+                b = ob;
+                i = oi;
+            }
+        }
+        if (lane == 0) {
+            rb[warp][j] = b;
+            ri[warp][j] = i;
+        }
+    }
+    __syncthreads();
+    if (tid < cnt) {
+        const int j = tid;
+        TB b = rb[0][j];
+        int i = ri[0][j];
+        for (int k = 1; k < 8; ++k) {
+            const TB ob = rb[k][j];
+            const int oi = ri[k][j];
+            if (oi >= 0 && (i < 0 || ob > b || (ob == b && oi < i))) {
+                b = ob;
+                i = oi;
+            }
+        }
+        const int64_t o2 = (int64_t)d * a.nw + j0 + j;
+        const float snr = (float)(((double)b - (double)a.mu[o2]) * (double)a.isd[o2]);
+        a.peak[o2] = snr;
+        a.arg[o2] = i;
+        if (a.cands && snr > a.thresh) {
+            const int k = atomicAdd(a.ncands, 1);
+            if (k < a.cap) {
+                dd_candidate cd;
+                cd.dm_index = d;
+                cd.width_index = j0 + j;
+                cd.t = i;
+                cd.snr = snr;
+                a.cands[k] = cd;
+            }
+        }
+    }
+}
+
+template <typename TX, typename TB>
+dd_status run_boxcar(const BoxArgs& a, int wmax_all, cudaStream_t s) {
+    const size_t smem = (size_t)(256 * kBoxS + wmax_all + 2) * sizeof(TX);
+    auto kern = k_boxcar<TX, TB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    dim3 grid((unsigned)((a.nw + kBoxG - 1) / kBoxG), (unsigned)a.ndm);
+    if (grid.y > 65535) return DD_ERR_UNSUPPORTED;
+    kern<<<grid, 256, smem, s>>>(a);
+    return cuda_status(cudaGetLastError());
+}
+
+}  // namespace
+
+dd_status launch_channel_stats(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
+                               int64_t nsamp, double* mean, double* sd, cudaStream_t s) {
+    if (p->band.in_type == DD_U8)
+        k_chan_stats<uint8_t><<<p->nchan, 256, 0, s>>>((const uint8_t*)in, ld, t_offset, nsamp, mean, sd);
+    else
+        k_chan_stats<float><<<p->nchan, 256, 0, s>>>((const float*)in, ld, t_offset, nsamp, mean, sd);
+    return cuda_status(cudaGetLastError());
+}
+
+static dd_status ensure_norm_ws(dd_plan_s* p, int nw) {
+    if (p->dev.ws_w >= nw && p->dev.mu) return DD_OK;
+    cudaFree(p->dev.mu);
+    cudaFree(p->dev.isd);
+    cudaFree(p->dev.widths);
+    p->dev.mu = nullptr;
+    p->dev.isd = nullptr;
+    p->dev.widths = nullptr;
+    p->dev.ws_w = 0;
+    cudaError_t e = cudaMalloc((void**)&p->dev.mu, (size_t)p->ndm * nw * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->dev.isd, (size_t)p->ndm * nw * sizeof(float));
+    if (e == cudaSuccess) e = cudaMalloc((void**)&p->dev.widths, (size_t)nw * sizeof(int32_t));
+    if (e != cudaSuccess) return cuda_status(e);
+    p->dev.ws_w = nw;
+    return DD_OK;
+}
+
+dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
+                        const int32_t* widths, int32_t nw, const double* mean, const double* sd,
+                        float* peak, int32_t* arg, float thresh, dd_candidate* cands, int32_t cap,
+                        int32_t* ncands, cudaStream_t s) {
+    dd_status st = ensure_norm_ws(p, nw);
+    if (st != DD_OK) return st;
+    cudaError_t e = cudaMemcpyAsync(p->dev.widths, widths, (size_t)nw * sizeof(int32_t),
+                                    cudaMemcpyHostToDevice, s);
+    if (e != cudaSuccess) return cuda_status(e);
+    const size_t red = (size_t)8 * nw * sizeof(float);
+    if (red > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    k_norm<<<p->ndm, 256, red, s>>>(p->dev.taps, p->unit ? nullptr : p->dev.w, p->kpad, p->nchan,
+                                    mean, sd, p->dev.widths, nw, p->out_int ? 1 : 0, p->dev.off,
+                                    p->dev.mu, p->dev.isd);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    BoxArgs a;
+    a.x = x;
+    a.ld = ld;
+    a.t_len = (int32_t)t_len;
+    a.ndm = p->ndm;
+    a.widths = p->dev.widths;
+    a.nw = nw;
+    a.off = p->dev.off;
+    a.mu = p->dev.mu;
+    a.isd = p->dev.isd;
+    a.peak = peak;
+    a.arg = arg;
+    a.thresh = thresh;
+    a.cands = cands;
+    a.cap = cap;
+    a.ncands = ncands;
+    const int wmax = widths[nw - 1];
+    if (!p->out_int) return run_boxcar<float, float>(a, wmax, s);
+    // exact integer sums around the per-trial offset: |x - o| <= 255 * N_S(d), so a
+    // width-w sum fits int32 when wmax * 255 * max_d N_S(d) < 2^31
+    const long long bound = (long long)wmax * p->max_abs_row;
+    if (bound < (long long)INT_MAX) return run_boxcar<int, int>(a, wmax, s);
+    return run_boxcar<int, long long>(a, wmax, s);
+}
+
+}  // namespace dd

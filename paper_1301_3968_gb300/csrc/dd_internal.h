@@ -1,0 +1,96 @@
+// Internal definitions shared by the host plan code and the CUDA launchers.
+#pragma once
+
+#include <cuda_runtime.h>
+
+#include <cstdint>
+#include <vector>
+
+#include "dd.h"
+
+namespace dd {
+
+// Dedispersion kernel geometry (see dd_dedisp.cu): a CTA has kWarps warps, one trial
+// per warp, and each lane owns kR consecutive output samples, so a CTA covers kWarps
+// trials x (32 * kR) samples.  kR is odd so that lane-strided shared-memory reads hit
+// distinct banks.
+constexpr int kWarps = 8;
+constexpr int kR = 31;
+constexpr int kTileT = 32 * kR;
+constexpr int kStages = 3;                 // cp.async pipeline depth
+constexpr int kSmemBudget = 200 * 1024;    // dynamic shared memory per dedispersion CTA
+
+// Byte layout of one dedispersion pipeline stage in shared memory: cs staged rows of
+// lcap elements, then per-channel window offsets, the delay and tap tables of the
+// CTA's trials, and (weighted plans) their per-tap weights.
+struct StageBytes {
+    int rows_bytes, e_off, dl_off, tp_off, w_off, bytes;
+    __host__ __device__ StageBytes(int esz, bool unit, int lcap, int kpad, int cs) {
+        rows_bytes = cs * lcap * esz;
+        e_off = (rows_bytes + 15) & ~15;
+        dl_off = e_off + cs * 4;
+        tp_off = dl_off + kWarps * cs * 4;
+        w_off = (tp_off + kWarps * cs * 4 + 15) & ~15;
+        bytes = w_off + (unit ? 0 : kWarps * cs * kpad * 4);
+        bytes = (bytes + 127) & ~127;
+    }
+};
+
+struct DevTables {
+    int device = -1;
+    int32_t* delay = nullptr;   // [ndm][nchan]
+    int32_t* taps = nullptr;    // [ndm][nchan]
+    float* w = nullptr;         // [ndm][nchan][kpad]  (weighted plans)
+    int32_t* blk_lo = nullptr;  // [nblk][nchan] minimum delay over the CTA's trials
+    // boxcar normaliser workspace
+    double* off = nullptr;      // [ndm]  per-trial offset subtracted before summing
+    float* mu = nullptr;        // [ndm][ws_w] mean of B_w minus w*off
+    float* isd = nullptr;       // [ndm][ws_w] 1/sigma_dw
+    int32_t* widths = nullptr;  // [ws_w]
+    int32_t ws_w = 0;
+};
+
+}  // namespace dd
+
+struct dd_plan_s {
+    dd_band band{};
+    int32_t nchan = 0, ndm = 0;
+    std::vector<double> dms;
+    std::vector<int32_t> delay, taps;  // [ndm][nchan]
+    std::vector<float> w;              // [ndm][nchan][kpad], empty for unit weights
+    int32_t kpad = 0;                  // weight row stride (multiple of 4) or 0
+    int32_t kuser = 0;                 // caller's weight row length (kmax argument)
+    bool unit = true;
+    int32_t kmax = 1, dmax = 0;
+    int64_t ns_total = 0;
+    bool out_int = true;               // int32 sums (uint8 input, unit weights)
+    int64_t max_abs_row = 0;           // bound on |out| for integer plans
+    // dedispersion schedule
+    int32_t nblk = 0;
+    std::vector<int32_t> blk_lo;       // [nblk][nchan] minimum delay over the block's trials
+    int32_t lcap = 0;                  // staged row length (elements)
+    int32_t cs = 4;                    // channels per pipeline stage
+    int32_t nch = 1;                   // time chunks per CTA (trials per CTA = 8 / nch)
+    bool dev_dirty = true;
+    dd::DevTables dev;
+};
+
+namespace dd {
+
+dd_status upload_tables(dd_plan_s* p);  // (re)creates the device tables if dirty
+dd_status cuda_status(cudaError_t e);
+
+// launchers (stream = cudaStream_t)
+dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
+                            int64_t t_out, void* out, int64_t out_ld, cudaStream_t s);
+dd_status launch_channel_stats(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
+                               int64_t nsamp, double* mean, double* sd, cudaStream_t s);
+dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
+                        const int32_t* widths, int32_t nw, const double* mean,
+                        const double* sd, float* peak, int32_t* arg, float thresh,
+                        dd_candidate* cands, int32_t cap, int32_t* ncands, cudaStream_t s);
+dd_status launch_backward(dd_plan_s* p, const float* in, int64_t ld, int64_t t_offset,
+                          int64_t t_out, const float* g, int64_t gld, float* gw, float* gin,
+                          int64_t gin_ld, cudaStream_t s);
+
+}  // namespace dd

@@ -1,0 +1,443 @@
+// Host side of the C ABI: band geometry, the default profile tables (Sec. 3), the
+// trial-DM rule (eq. trial DMs, Sec. 6.3), argument checking and the dedispersion
+// schedule (trial blocks and staged window lengths).
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+
+#include "dd_internal.h"
+
+namespace {
+
+constexpr double kDefaultKdm = 4.15;
+
+double kdm_of(const dd_band& b) { return b.k_dm > 0 ? b.k_dm : kDefaultKdm; }
+
+bool band_ok(const dd_band* b) {
+    return b && b->nchan > 0 && b->f_lo_mhz > 0 && b->df_mhz > 0 && b->dt_ms > 0 &&
+           b->nsamp >= 0 && (b->in_type == DD_U8 || b->in_type == DD_F32) &&
+           b->f_lo_mhz > 0;
+}
+
+// nu_c: highest frequency of channel c in GHz (Sec. 3).
+double chan_top_ghz(const dd_band& b, int c) {
+    int j = b.descending ? (b.nchan - 1 - c) : c;
+    return (b.f_lo_mhz + (j + 1) * b.df_mhz) / 1000.0;
+}
+
+double band_top_ghz(const dd_band& b) { return (b.f_lo_mhz + b.nchan * b.df_mhz) / 1000.0; }
+
+// Sec. 6.2: [(1/C) sum_c nu_c^-3]^-1 (channel order does not matter).
+double inv_mean_inv_cube(const dd_band& b) {
+    double s = 0.0;
+    for (int c = 0; c < b.nchan; ++c) {
+        double nu = (b.f_lo_mhz + (c + 1) * b.df_mhz) / 1000.0;
+        s += 1.0 / (nu * nu * nu);
+    }
+    return 1.0 / (s / b.nchan);
+}
+
+void build_trials(const dd_band& b, double dm0, double eps, int n, double extra2, double* out) {
+    out[0] = dm0;
+    double acc = 0.0;
+    for (int i = 1; i < n; ++i) {
+        acc += std::sqrt(out[i - 1] * out[i - 1] + extra2);
+        out[i] = dm0 + 2.0 * eps / b.nchan * acc;
+    }
+}
+
+// Span of the staged window when `db` consecutive trials share a CTA: the largest
+// max(delta + n) - min(delta) over blocks and channels.
+int64_t block_span(const dd_plan_s* p, int db, std::vector<int32_t>* lo_out) {
+    const int C = p->nchan;
+    const int nblk = (p->ndm + db - 1) / db;
+    if (lo_out) lo_out->assign((size_t)nblk * C, 0);
+    int64_t span = 0;
+    for (int b = 0; b < nblk; ++b) {
+        for (int c = 0; c < C; ++c) {
+            int64_t lo = INT64_MAX, hi = 0;
+            for (int i = 0; i < db; ++i) {
+                const int d = b * db + i;
+                if (d >= p->ndm) break;
+                const int64_t dl = p->delay[(size_t)d * C + c];
+                lo = std::min(lo, dl);
+                hi = std::max(hi, dl + p->taps[(size_t)d * C + c]);
+            }
+            if (lo_out) (*lo_out)[(size_t)b * C + c] = (int32_t)lo;
+            span = std::max(span, hi - lo);
+        }
+    }
+    return span;
+}
+
+// Chooses the CTA shape of the dedispersion kernel (trials x time chunks), the staged
+// window length and the channels per pipeline stage.  The most trials per CTA (the
+// most reuse of each staged sample) whose window still fits is taken.
+dd_status build_schedule(dd_plan_s* p) {
+    const bool u8 = p->band.in_type == DD_U8;
+    const int64_t q = u8 ? 16 : 4;            // elements per 16-byte chunk
+    const int64_t esz = u8 ? 1 : 4;
+    const int64_t cs_want = u8 ? 8 : 4;
+    for (int nch = 1; nch <= dd::kWarps; nch *= 2) {
+        const int db = dd::kWarps / nch;
+        const int64_t span = block_span(p, db, nullptr);
+        // the CTA's outputs, the block's delay spread plus taps, 16 bytes of alignment
+        // slack and one element that the register pipeline reads ahead
+        int64_t need = (int64_t)nch * dd::kTileT + span + q + 2;
+        need = (need + q - 1) / q * q;
+        if (need > (1 << 24)) continue;
+        int64_t cs = cs_want;
+        const int kpad = p->unit ? 0 : p->kpad;
+        while (cs > 0 && (int64_t)dd::kStages *
+                                 dd::StageBytes((int)esz, p->unit, (int)need, kpad, (int)cs).bytes >
+                             dd::kSmemBudget)
+            --cs;
+        if (cs < (nch == dd::kWarps ? 1 : cs_want)) continue;
+        p->nch = nch;
+        p->cs = (int32_t)cs;
+        p->lcap = (int32_t)need;
+        p->nblk = (p->ndm + db - 1) / db;
+        block_span(p, db, &p->blk_lo);
+        p->dev_dirty = true;
+        return DD_OK;
+    }
+    return DD_ERR_UNSUPPORTED;
+}
+
+dd_status finish_profiles(dd_plan_s* p) {
+    const size_t n = (size_t)p->ndm * p->nchan;
+    int32_t kmax = 1, dmax = 0;
+    int64_t ns = 0, row_max = 0;
+    for (int d = 0; d < p->ndm; ++d) {
+        int64_t row = 0;
+        for (int c = 0; c < p->nchan; ++c) {
+            size_t i = (size_t)d * p->nchan + c;
+            kmax = std::max(kmax, p->taps[i]);
+            int64_t e = (int64_t)p->delay[i] + p->taps[i] - 1;
+            if (e > INT32_MAX) return DD_ERR_OVERFLOW;
+            dmax = std::max<int32_t>(dmax, (int32_t)e);
+            ns += p->taps[i];
+            row += p->taps[i];
+        }
+        row_max = std::max(row_max, row);
+    }
+    (void)n;
+    p->kmax = kmax;
+    p->dmax = dmax;
+    p->ns_total = ns;
+    p->out_int = p->unit && p->band.in_type == DD_U8;
+    p->max_abs_row = row_max * 255;
+    if (p->out_int && p->max_abs_row > INT32_MAX) return DD_ERR_OVERFLOW;
+    return build_schedule(p);
+}
+
+}  // namespace
+
+namespace dd {
+
+dd_status cuda_status(cudaError_t e) {
+    if (e == cudaSuccess) return DD_OK;
+    return e == cudaErrorMemoryAllocation ? DD_ERR_OOM : DD_ERR_CUDA;
+}
+
+static void free_dev(dd_plan_s* p) {
+    if (p->dev.device < 0) return;
+    int cur = -1;
+    cudaGetDevice(&cur);
+    if (cur != p->dev.device) cudaSetDevice(p->dev.device);
+    cudaFree(p->dev.delay);
+    cudaFree(p->dev.taps);
+    cudaFree(p->dev.w);
+    cudaFree(p->dev.blk_lo);
+    cudaFree(p->dev.off);
+    cudaFree(p->dev.mu);
+    cudaFree(p->dev.isd);
+    cudaFree(p->dev.widths);
+    if (cur >= 0 && cur != p->dev.device) cudaSetDevice(cur);
+    p->dev = DevTables{};
+}
+
+template <typename T>
+static dd_status put(T** dst, const T* src, size_t n) {
+    cudaError_t e = cudaMalloc((void**)dst, std::max<size_t>(n, 1) * sizeof(T));
+    if (e != cudaSuccess) return cuda_status(e);
+    if (n) e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
+    return cuda_status(e);
+}
+
+dd_status upload_tables(dd_plan_s* p) {
+    int dev = -1;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    if (!p->dev_dirty && p->dev.device == dev) return DD_OK;
+    free_dev(p);
+    p->dev.device = dev;
+    const size_t n = (size_t)p->ndm * p->nchan;
+    dd_status st;
+    if ((st = put(&p->dev.delay, p->delay.data(), n)) != DD_OK) return st;
+    if ((st = put(&p->dev.taps, p->taps.data(), n)) != DD_OK) return st;
+    if (!p->unit && (st = put(&p->dev.w, p->w.data(), p->w.size())) != DD_OK) return st;
+    if ((st = put(&p->dev.blk_lo, p->blk_lo.data(), p->blk_lo.size())) != DD_OK) return st;
+    e = cudaMalloc((void**)&p->dev.off, (size_t)p->ndm * sizeof(double));
+    if (e != cudaSuccess) return cuda_status(e);
+    p->dev_dirty = false;
+    return DD_OK;
+}
+
+}  // namespace dd
+
+extern "C" {
+
+const char* dd_status_str(dd_status s) {
+    switch (s) {
+        case DD_OK: return "ok";
+        case DD_ERR_ARG: return "invalid argument";
+        case DD_ERR_OVERFLOW: return "integer overflow";
+        case DD_ERR_OOM: return "out of memory";
+        case DD_ERR_CUDA: return "CUDA error";
+        case DD_ERR_STATE: return "invalid state";
+        case DD_ERR_TIMEOUT: return "device wait timed out";
+        case DD_ERR_CAPACITY: return "capacity exceeded";
+        case DD_ERR_UNSUPPORTED: return "unsupported";
+    }
+    return "unknown status";
+}
+
+int32_t dd_version(void) { return 100; }
+
+dd_status dd_trial_dms(const dd_band* band, double dm0, double dm_max, int32_t n,
+                       double tau_av_ms, int32_t smear_terms, double* dms_out,
+                       double* eps_out) {
+    if (!band_ok(band) || !dms_out || n < 2 || !(dm_max > dm0) || dm0 < 0 ||
+        tau_av_ms < 0 || (smear_terms != 1 && smear_terms != 2))
+        return DD_ERR_ARG;
+    const dd_band& b = *band;
+    const double k = kdm_of(b);
+    const double dnu = b.df_mhz / 1000.0;
+    const double geo = inv_mean_inv_cube(b);
+    const double dm_diag = b.dt_ms / (2.0 * k * dnu) * geo;   // Sec. 6.2, kappa = 1/k
+    const double dm_tau = tau_av_ms / (2.0 * k * dnu) * geo;  // eq. DM_tau
+    const double extra2 = dm_diag * dm_diag + (smear_terms == 2 ? dm_tau * dm_tau : 0.0);
+    std::vector<double> tmp(n);
+    double lo = 0.0, hi = 1.0;
+    for (int it = 0; it < 200; ++it) {
+        build_trials(b, dm0, hi, n, extra2, tmp.data());
+        if (tmp[n - 1] >= dm_max) break;
+        hi *= 2.0;
+    }
+    for (int it = 0; it < 200; ++it) {
+        double mid = 0.5 * (lo + hi);
+        build_trials(b, dm0, mid, n, extra2, tmp.data());
+        if (tmp[n - 1] < dm_max) lo = mid; else hi = mid;
+    }
+    const double eps = 0.5 * (lo + hi);
+    build_trials(b, dm0, eps, n, extra2, dms_out);
+    if (eps_out) *eps_out = eps;
+    return DD_OK;
+}
+
+dd_status dd_plan_create(dd_plan_t* out, const dd_band* band, const double* dms, int32_t ndm) {
+    if (!out || !band_ok(band) || !dms || ndm < 1) return DD_ERR_ARG;
+    *out = nullptr;
+    for (int d = 0; d < ndm; ++d)
+        if (!(dms[d] >= 0.0) || !std::isfinite(dms[d])) return DD_ERR_ARG;
+    dd_plan_s* p = new (std::nothrow) dd_plan_s;
+    if (!p) return DD_ERR_OOM;
+    p->band = *band;
+    p->nchan = band->nchan;
+    p->ndm = ndm;
+    p->dms.assign(dms, dms + ndm);
+    const size_t n = (size_t)ndm * band->nchan;
+    p->delay.resize(n);
+    p->taps.resize(n);
+    const double k = kdm_of(*band);
+    const double top = band_top_ghz(*band);
+    const double dnu = band->df_mhz / 1000.0;
+    for (int d = 0; d < ndm; ++d) {
+        for (int c = 0; c < band->nchan; ++c) {
+            const double nu = chan_top_ghz(*band, c);
+            const double lo = nu - dnu;
+            const double raw_d = k * dms[d] * (1.0 / (nu * nu) - 1.0 / (top * top)) / band->dt_ms;
+            const double raw_n = k * dms[d] * (1.0 / (lo * lo) - 1.0 / (nu * nu)) / band->dt_ms;
+            if (!(raw_d < 2.0e9) || !(raw_n < 2.0e9)) {
+                delete p;
+                return DD_ERR_OVERFLOW;
+            }
+            p->delay[(size_t)d * band->nchan + c] = (int32_t)std::floor(raw_d);
+            p->taps[(size_t)d * band->nchan + c] = std::max(1, (int32_t)std::ceil(raw_n));
+        }
+    }
+    dd_status st = finish_profiles(p);
+    if (st != DD_OK) {
+        delete p;
+        return st;
+    }
+    *out = p;
+    return DD_OK;
+}
+
+dd_status dd_set_profiles(dd_plan_t p, const int32_t* delay, const int32_t* ntaps,
+                          const float* w, int32_t kmax) {
+    if (!p) return DD_ERR_ARG;
+    const size_t n = (size_t)p->ndm * p->nchan;
+    if (w && kmax < 1) return DD_ERR_ARG;
+    if (delay)
+        for (size_t i = 0; i < n; ++i)
+            if (delay[i] < 0) return DD_ERR_ARG;
+    if (ntaps)
+        for (size_t i = 0; i < n; ++i)
+            if (ntaps[i] < 1) return DD_ERR_ARG;
+    // keep the old state so that a rejected profile leaves the plan usable
+    std::vector<int32_t> old_d = p->delay, old_t = p->taps;
+    std::vector<float> old_w = p->w;
+    int32_t old_kpad = p->kpad, old_kuser = p->kuser;
+    bool old_unit = p->unit;
+    if (delay) std::memcpy(p->delay.data(), delay, n * sizeof(int32_t));
+    if (ntaps) std::memcpy(p->taps.data(), ntaps, n * sizeof(int32_t));
+    if (w) {
+        for (size_t i = 0; i < n; ++i)
+            if (p->taps[i] > kmax) {
+                p->delay = old_d;
+                p->taps = old_t;
+                return DD_ERR_ARG;
+            }
+        p->kpad = (kmax + 3) / 4 * 4;
+        p->kuser = kmax;
+        p->w.assign(n * (size_t)p->kpad, 0.0f);
+        for (size_t i = 0; i < n; ++i)
+            for (int k = 0; k < p->taps[i]; ++k) p->w[i * p->kpad + k] = w[i * (size_t)kmax + k];
+        p->unit = false;
+    } else {
+        p->w.clear();
+        p->kpad = 0;
+        p->kuser = 0;
+        p->unit = true;
+    }
+    dd_status st = finish_profiles(p);
+    if (st != DD_OK) {
+        p->delay = old_d;
+        p->taps = old_t;
+        p->w = old_w;
+        p->kpad = old_kpad;
+        p->kuser = old_kuser;
+        p->unit = old_unit;
+        finish_profiles(p);
+        return st;
+    }
+    p->dev_dirty = true;
+    return DD_OK;
+}
+
+dd_status dd_set_weights_device(dd_plan_t p, const float* d_w, int32_t kmax, void* stream) {
+    if (!p || !d_w || kmax < 1) return DD_ERR_ARG;
+    if (p->kmax > kmax) return DD_ERR_ARG;
+    const int32_t kpad = (kmax + 3) / 4 * 4;
+    if (p->unit || p->kpad != kpad || p->kuser != kmax) {
+        // switch the plan to weighted with this row length; host weights start at zero
+        const size_t n = (size_t)p->ndm * p->nchan;
+        p->w.assign(n * (size_t)kpad, 0.0f);
+        p->kpad = kpad;
+        p->kuser = kmax;
+        p->unit = false;
+        dd_status st = finish_profiles(p);
+        if (st != DD_OK) return st;
+    }
+    dd_status st = dd::upload_tables(p);
+    if (st != DD_OK) return st;
+    cudaError_t e = cudaMemcpy2DAsync(p->dev.w, (size_t)kpad * sizeof(float), d_w,
+                                      (size_t)kmax * sizeof(float), (size_t)kmax * sizeof(float),
+                                      (size_t)p->ndm * p->nchan, cudaMemcpyDeviceToDevice,
+                                      (cudaStream_t)stream);
+    return dd::cuda_status(e);
+}
+
+dd_status dd_plan_info(dd_plan_t p, int64_t* t_out, int32_t* d_max, int32_t* kmax,
+                       int64_t* ns_total, int32_t* out_is_int) {
+    if (!p) return DD_ERR_ARG;
+    if (t_out) *t_out = std::max<int64_t>(0, p->band.nsamp - p->dmax);
+    if (d_max) *d_max = p->dmax;
+    if (kmax) *kmax = p->kmax;
+    if (ns_total) *ns_total = p->ns_total;
+    if (out_is_int) *out_is_int = p->out_int ? 1 : 0;
+    return DD_OK;
+}
+
+dd_status dd_get_tables(dd_plan_t p, int32_t* delay, int32_t* ntaps) {
+    if (!p) return DD_ERR_ARG;
+    const size_t n = (size_t)p->ndm * p->nchan;
+    if (delay) std::memcpy(delay, p->delay.data(), n * sizeof(int32_t));
+    if (ntaps) std::memcpy(ntaps, p->taps.data(), n * sizeof(int32_t));
+    return DD_OK;
+}
+
+static bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
+
+dd_status dd_dedisperse(dd_plan_t p, const void* in, int64_t in_ld, int64_t t_offset,
+                        int64_t nsamp, void* out, int64_t out_ld, void* stream) {
+    if (!p || !in || !out) return DD_ERR_ARG;
+    const int64_t esz = p->band.in_type == DD_U8 ? 1 : 4;
+    if (nsamp <= 0) nsamp = p->band.nsamp;
+    if (t_offset < 0 || nsamp <= p->dmax || t_offset + nsamp > in_ld) return DD_ERR_ARG;
+    if (!aligned16(in) || (in_ld * esz) % 16 != 0) return DD_ERR_ARG;
+    const int64_t t_out = nsamp - p->dmax;
+    if (out_ld < t_out) return DD_ERR_ARG;
+    if (t_out > INT32_MAX - dd::kTileT || in_ld > (int64_t)1 << 40) return DD_ERR_OVERFLOW;
+    dd_status st = dd::upload_tables(p);
+    if (st != DD_OK) return st;
+    return dd::launch_dedisperse(p, in, in_ld, t_offset, t_out, out, out_ld, (cudaStream_t)stream);
+}
+
+dd_status dd_channel_stats(dd_plan_t p, const void* in, int64_t in_ld, int64_t t_offset,
+                           int64_t nsamp, double* mean, double* sd, void* stream) {
+    if (!p || !in || !mean || !sd) return DD_ERR_ARG;
+    if (nsamp <= 0) nsamp = p->band.nsamp;
+    if (t_offset < 0 || nsamp < 1 || t_offset + nsamp > in_ld) return DD_ERR_ARG;
+    dd_status st = dd::upload_tables(p);
+    if (st != DD_OK) return st;
+    return dd::launch_channel_stats(p, in, in_ld, t_offset, nsamp, mean, sd, (cudaStream_t)stream);
+}
+
+dd_status dd_boxcar_snr(dd_plan_t p, const void* x, int64_t ld, int64_t t_len,
+                        const int32_t* widths, int32_t nw, const double* mean,
+                        const double* sd, float* peak, int32_t* arg, float thresh,
+                        dd_candidate* cands, int32_t cap, int32_t* ncands, void* stream) {
+    if (!p || !x || !widths || nw < 1 || !mean || !sd || !peak || !arg) return DD_ERR_ARG;
+    if (t_len < 1 || ld < t_len || t_len > INT32_MAX) return DD_ERR_ARG;
+    if (cands && (!ncands || cap < 0)) return DD_ERR_ARG;
+    for (int i = 0; i < nw; ++i) {
+        if (widths[i] < 1 || widths[i] > t_len) return DD_ERR_ARG;
+        if (i && widths[i] <= widths[i - 1]) return DD_ERR_ARG;
+    }
+    dd_status st = dd::upload_tables(p);
+    if (st != DD_OK) return st;
+    return dd::launch_boxcar(p, x, ld, t_len, widths, nw, mean, sd, peak, arg, thresh, cands,
+                             cap, ncands, (cudaStream_t)stream);
+}
+
+dd_status dd_backward(dd_plan_t p, const float* in, int64_t in_ld, int64_t t_offset,
+                      int64_t nsamp, const float* g, int64_t gld, float* gw, float* gin,
+                      int64_t gin_ld, void* stream) {
+    if (!p || !in || !g) return DD_ERR_ARG;
+    if (p->band.in_type != DD_F32) return DD_ERR_UNSUPPORTED;
+    if (nsamp <= 0) nsamp = p->band.nsamp;
+    if (t_offset < 0 || nsamp <= p->dmax || t_offset + nsamp > in_ld) return DD_ERR_ARG;
+    const int64_t t_out = nsamp - p->dmax;
+    if (gld < t_out) return DD_ERR_ARG;
+    if (gin && (gin_ld < t_offset + nsamp || (gin_ld * 4) % 16 != 0 || !aligned16(gin)))
+        return DD_ERR_ARG;
+    if (!aligned16(in) || (in_ld * 4) % 16 != 0) return DD_ERR_ARG;
+    dd_status st = dd::upload_tables(p);
+    if (st != DD_OK) return st;
+    return dd::launch_backward(p, in, in_ld, t_offset, t_out, g, gld, gw, gin, gin_ld,
+                               (cudaStream_t)stream);
+}
+
+dd_status dd_plan_destroy(dd_plan_t p) {
+    if (!p) return DD_ERR_ARG;
+    dd::free_dev(p);
+    delete p;
+    return DD_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,415 @@
+"""Benchmark of the dedispersion hot path on GB300.
+
+One step = one pass of the hot path over one block of synthetic filterbank data:
+per-channel noise statistics, profiled dedispersion of every trial (eq. p_dedisp),
+the boxcar normaliser and the boxcar S/N scan over all widths (eq. snr).  The default
+workload is the CRAFT-like configuration (336 x 1 MHz channels over 1130-1466 MHz,
+dt = 1 ms, 65536 fp32 samples, 4096 trial DMs of eq. trial DMs over 0-4000 pc cm^-3,
+weights proportional to nu^-1.4 on every tap, boxcar widths 1-32).
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--impl reference]
+
+prints one JSON line.  `value` is dedispersed DM-trial*samples per second for the
+whole job (N ranks each process their own block: weak scaling, no collective on the
+data path).  `--impl reference` times the CPU oracle (tests' reference) on a bounded
+sample of the same workload.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+METRIC = "dedispersed DM-trial·samples/s on 1 GB300 and % roofline; fwd+bwd vs plain fwd"
+UNIT = "DM-trial·samples/s"
+FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
+N_SM = 152
+FP32_LANES_PER_SM = 128
+
+
+def _peaks():
+    path = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    try:
+        with open(path) as f:
+            return json.load(f), "measured"
+    except Exception:
+        return dict(FALLBACK_PEAKS), "fallback"
+
+
+# ----------------------------------------------------------------------------- workload
+
+
+def craft_workload(dd, dev, ndm=None):
+    import torch
+    import synth
+    cfg = synth.make_craft()
+    b = cfg["band"]
+    band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, cfg["nsamp"], "f32")
+    dms, eps = dd.trial_dms(band, 0.0, cfg["dm_max"], cfg["ndm"], tau_av_ms=1.0)
+    if ndm:   # a smaller profiling case: every k-th trial of the same list
+        dms = dms[:: max(1, len(dms) // ndm)][:ndm]
+    plan = dd.Plan(band, dms)
+    delay, taps = plan.tables()
+    K = int(taps.max())
+    w = np.where(np.arange(K)[None, None, :] < taps[:, :, None], cfg["wchan"][None, :, None], 0.0)
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    plan.set_profiles(weights=w)
+    x = torch.from_numpy(cfg["data"]).to(dev)
+    info = plan.info()
+    t_out = cfg["nsamp"] - info["d_max"]
+    return dict(
+        name="CRAFT-like",
+        desc=("CRAFT-like: 336 ch x 1 MHz (1130-1466 MHz), dt 1 ms, 65536 fp32 samples, "
+              f"{len(dms)} trial DMs 0-{dms[-1]:.0f} (eq. trial DMs, eps={eps:.4f}), "
+              "weights ~ nu^-1.4 on every tap, boxcar widths 1-32"),
+        plan=plan, x=x, host=cfg["data"], nsamp=cfg["nsamp"], t_out=t_out, ndm=len(dms),
+        widths=cfg["widths"], delay=delay, taps=taps, w=w, dtype="f32",
+        flops=2.0 * float(taps.astype(np.int64).sum()) * t_out, ns_total=int(info["ns_total"]),
+    )
+
+
+# ----------------------------------------------------------------------------- clocks
+
+
+class ClockSampler:
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+
+    def start(self):
+        try:
+            os.makedirs(os.path.dirname(self.path), exist_ok=True)
+            self.f = open(self.path, "w")
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", f"--query-gpu={self.FIELDS}", "--format=csv,noheader,nounits",
+                 "-i", str(self.index), "-lms", "200"], stdout=self.f, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        self.f.close()
+        sm, smax, reasons = [], None, set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        with open(self.path) as f:
+            for line in f:
+                p = [v.strip() for v in line.split(",")]
+                if len(p) < 9:
+                    continue
+                try:
+                    sm.append(float(p[1]))
+                    smax = float(p[2])
+                except ValueError:
+                    continue
+                for nm, v in zip(names, p[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": smax,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ----------------------------------------------------------------------------- timing
+
+
+def _dist():
+    import torch.distributed as dist
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws > 1 and not dist.is_initialized():
+        import torch
+        backend = "nccl" if torch.cuda.is_available() else "gloo"
+        dist.init_process_group(backend=backend)
+    rank = int(os.environ.get("RANK", "0"))
+    return rank, ws
+
+
+def _barrier(ws):
+    if ws > 1:
+        import torch.distributed as dist
+        dist.barrier()
+
+
+def _max_over_ranks(v, ws):
+    if ws == 1:
+        return v
+    import torch
+    import torch.distributed as dist
+    t = torch.tensor([v], dtype=torch.float64, device="cuda" if torch.cuda.is_available() else "cpu")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def run_gpu(args):
+    import torch
+    import paper_1301_3968_gb300 as dd
+    from paper_1301_3968_gb300 import build as dd_build
+
+    rank, ws = _dist()
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    dev = torch.device("cuda", local)
+    dd_build.build()
+    W = craft_workload(dd, dev, args.ndm)
+    plan, x = W["plan"], W["x"]
+    widths = W["widths"]
+    stream = torch.cuda.current_stream()
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)      # 256 MiB > 129 MB L2
+    out = torch.empty((W["ndm"], W["t_out"]), dtype=torch.float32, device=dev)
+    launches_per_step = 4    # channel stats, dedispersion, normaliser, boxcar scan
+
+    def step(ev=None):
+        mean, sd = plan.channel_stats(x, nsamp=W["nsamp"])
+        if ev is not None:
+            ev[0].record(stream)
+        plan.dedisperse(x, nsamp=W["nsamp"], out=out)
+        if ev is not None:
+            ev[1].record(stream)
+        return plan.boxcar_snr(out, widths, mean, sd, t_len=W["t_out"])
+
+    for _ in range(args.warmup):
+        flush.fill_(1)
+        step()
+    torch.cuda.synchronize()
+
+    clk = ClockSampler(torch.cuda.current_device()) if rank == 0 else None
+    if clk:
+        clk.start()
+        time.sleep(0.3)
+    evs = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    kev = [(torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True))
+           for _ in range(args.steps)]
+    _barrier(ws)
+    torch.cuda.synchronize()
+    for i in range(args.steps):
+        flush.fill_(i & 0xFF)                     # evict the input from L2 between steps
+        evs[i][0].record(stream)
+        step(kev[i])
+        evs[i][1].record(stream)
+    torch.cuda.synchronize()
+    _barrier(ws)
+    step_ms = [a.elapsed_time(b) for a, b in evs]
+    k_ms = [a.elapsed_time(b) for a, b in kev]
+    clocks = clk.stop() if clk else None
+    ms = _max_over_ranks(sum(step_ms) / len(step_ms), ws)
+    units = float(W["ndm"]) * W["t_out"]
+    value = ws * units / (ms / 1e3)
+
+    if args.no_e2e:
+        return _result(args, W, ws, rank, ms, value, k_ms, clocks, None)
+
+    # end to end through the public API: pinned host input -> device, the hot path,
+    # peak S/N and times back to the host, every step
+    host = torch.from_numpy(W["host"]).pin_memory()
+    peak_h = torch.empty((W["ndm"], len(widths)), dtype=torch.float32).pin_memory()
+    arg_h = torch.empty((W["ndm"], len(widths)), dtype=torch.int32).pin_memory()
+    xin = torch.empty_like(x)
+
+    def e2e_step():
+        xin.copy_(host, non_blocking=True)
+        mean, sd = plan.channel_stats(xin, nsamp=W["nsamp"])
+        plan.dedisperse(xin, nsamp=W["nsamp"], out=out)
+        pk, ag, _ = plan.boxcar_snr(out, widths, mean, sd, t_len=W["t_out"])
+        peak_h.copy_(pk, non_blocking=True)
+        arg_h.copy_(ag, non_blocking=True)
+
+    for _ in range(max(1, args.warmup)):
+        e2e_step()
+    torch.cuda.synchronize()
+    _barrier(ws)
+    e0 = torch.cuda.Event(enable_timing=True)
+    e1 = torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        e2e_step()
+    e1.record(stream)
+    torch.cuda.synchronize()
+    e_ms = _max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
+    h2d = host.numel() * host.element_size()
+    d2h = peak_h.numel() * 4 + arg_h.numel() * 4
+    units = float(W["ndm"]) * W["t_out"]
+    e2e = {"value": ws * units / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+           "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
+    return _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e)
+
+
+def _profile_traffic():
+    """DRAM bytes per dedispersion launch from the committed ncu summary, if it was
+    taken on the current kernel source (else None)."""
+    import hashlib
+    path = os.path.join(ROOT, "profiles", "k_dedisp_f32_craft.md")
+    src = os.path.join(ROOT, "paper_1301_3968_gb300", "csrc", "dd_dedisp.cu")
+    try:
+        text = open(path).read()
+        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+    except OSError:
+        return None
+    got = {}
+    for line in text.splitlines():
+        if ":" in line:
+            k, v = line.split(":", 1)
+            got[k.strip().strip("-* `")] = v.strip().strip("` ")
+    if got.get("source_sha256") != sha:
+        return None
+    try:
+        return float(got["dram_bytes_per_full_launch"])
+    except (KeyError, ValueError):
+        return None
+
+
+def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e):
+    if rank != 0:
+        return None
+    peaks, kind = _peaks()
+    sm_max = float(peaks.get("sm_max_mhz", 2070.0))
+    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    k_avg = sum(k_ms) / len(k_ms)
+    achieved = W["flops"] / (k_avg / 1e3) / 1e12
+    res = {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
+        "scaling": "weak", "vs_baseline": None, "dtype": W["dtype"], "data": "synthetic",
+        "config": {"workload": W["desc"], "trials": W["ndm"], "t_out": W["t_out"],
+                   "channels": 336, "nsamp": W["nsamp"], "taps_total": W["ns_total"],
+                   "l2": "flushed between steps (256 MiB write outside the timed events)",
+                   "parallelism": f"replicas x{ws} (independent blocks per GPU)"},
+        "e2e": e2e,
+        "gpu_launches": launches_per_step * args.steps,
+        "roofline": {"bound": "alu", "kernel": "k_dedisp<float,float,weighted>",
+                     "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
+                     "frac": achieved / peak_tflops,
+                     "traffic": args.traffic if args.traffic is not None else _profile_traffic(),
+                     "peak_kind": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
+                                  f"{sm_max:.0f} MHz ({kind} sm_max_mhz)",
+                     "kernel_ms": k_avg, "flops_per_launch": W["flops"]},
+        "clocks": clocks,
+    }
+    if not args.no_cpu_baseline:
+        res["cpu_baseline"] = cpu_baseline(W, budget_s=args.cpu_seconds)
+    return res
+
+
+# ----------------------------------------------------------------------------- oracle
+
+
+def cpu_baseline(W, budget_s=12.0):
+    """The oracle as it stands (C brute force + numpy boxcar) on a bounded sample of
+    trial rows of the same workload, on this host's cores."""
+    import oracle
+    from oracle import ref
+    I, delay, taps, w = W["host"], W["delay"], W["taps"], W["w"]
+    nsamp, t_out, widths = W["nsamp"], W["t_out"], W["widths"]
+    mu_c, sd_c = ref.channel_stats(I, nsamp=nsamp)
+    rng = np.random.default_rng(7)
+    order = rng.permutation(W["ndm"])
+    done = 0
+    t0 = time.perf_counter()
+    while time.perf_counter() - t0 < budget_s and done < W["ndm"]:
+        rows = np.sort(order[done:done + 16])
+        x = oracle.c_dedisperse(I, delay, taps, w=w, nsamp=nsamp, rows=rows)
+        mu, sd = ref.boxcar_norm(taps[rows], widths, mu_c, sd_c, w=w[rows])
+        ref.boxcar_snr(x, widths, mu, sd)
+        done += len(rows)
+    el = time.perf_counter() - t0
+    return {"value": done * t_out / el, "unit": UNIT, "cores": oracle.num_threads(),
+            "kind": "oracle",
+            "sample": f"{done} of {W['ndm']} trial rows (random), full {t_out} outputs each, "
+                      f"dedispersion + boxcar normaliser + boxcar S/N, {el:.1f} s"}
+
+
+def run_reference(args):
+    rank = int(os.environ.get("RANK", "0"))
+    if rank != 0:
+        return None
+    import oracle
+    from oracle import ref
+    import synth
+    cfg = synth.make_craft()
+    b = cfg["band"]
+    dms, eps = ref.trial_dms(0.0, cfg["dm_max"], cfg["ndm"], b.nchan, b.f_lo_mhz, b.df_mhz,
+                             b.dt_ms, 1.0)
+    delay, _ = ref.delay_table(dms, b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms)
+    taps, _ = ref.taps_table(dms, b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms)
+    K = int(taps.max())
+    w = np.where(np.arange(K)[None, None, :] < taps[:, :, None], cfg["wchan"][None, :, None], 0.0)
+    w = np.ascontiguousarray(w, dtype=np.float32)
+    nsamp = cfg["nsamp"]
+    t_out = nsamp - ref.d_max(delay, taps)
+    widths = cfg["widths"]
+    rows_per_step = 8
+    rng = np.random.default_rng(11)
+
+    def step():
+        rows = np.sort(rng.choice(len(dms), rows_per_step, replace=False))
+        mu_c, sd_c = ref.channel_stats(cfg["data"], nsamp=nsamp)
+        x = oracle.c_dedisperse(cfg["data"], delay, taps, w=w, nsamp=nsamp, rows=rows)
+        mu, sd = ref.boxcar_norm(taps[rows], widths, mu_c, sd_c, w=w[rows])
+        ref.boxcar_snr(x, widths, mu, sd)
+
+    for _ in range(args.warmup):
+        step()
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        step()
+    el = time.perf_counter() - t0
+    ms = el / args.steps * 1e3
+    value = rows_per_step * t_out / (el / args.steps)
+    return {
+        "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
+        "config": {"workload": "CRAFT-like: 336 ch x 1 MHz, dt 1 ms, 65536 fp32 samples, 4096 trial "
+                               "DMs 0-4000 (eq. trial DMs), weights ~ nu^-1.4, boxcar widths 1-32",
+                   "sample": f"{rows_per_step} random trial rows per step"},
+        "cpu_baseline": {"value": value, "unit": UNIT, "cores": oracle.num_threads(), "kind": "oracle",
+                         "sample": f"{rows_per_step} random trial rows of 4096 per step, full "
+                                   f"{t_out} outputs, stats + dedispersion + normaliser + boxcar"},
+        "e2e": {"value": value, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--impl", default="gb300", choices=["gb300", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--cpu-seconds", type=float, default=12.0)
+    ap.add_argument("--ndm", type=int, default=None,
+                    help="trial count override (profiling on a smaller case); default 4096")
+    ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--traffic", type=float, default=None,
+                    help="DRAM bytes per dedispersion launch from an ncu capture")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        res = run_reference(args)
+    else:
+        res = run_gpu(args)
+    if res is not None:
+        print(json.dumps(res), flush=True)
+
+
+if __name__ == "__main__":
+    main()

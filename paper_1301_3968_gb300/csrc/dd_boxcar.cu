@@ -8,6 +8,7 @@
 // All reductions run in a fixed order, so results are deterministic.
 #include <cfloat>
 #include <climits>
+#include <algorithm>
 #include <cstdint>
 
 #include "dd_internal.h"
@@ -353,6 +354,7 @@ static dd_status ensure_norm_ws(dd_plan_s* p, int nw) {
     cudaFree(p->dev.mu);
     cudaFree(p->dev.isd);
     cudaFree(p->dev.widths);
+    p->widths_on_dev.clear();
     p->dev.mu = nullptr;
     p->dev.isd = nullptr;
     p->dev.widths = nullptr;
@@ -371,9 +373,16 @@ dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
                         int32_t* ncands, cudaStream_t s) {
     dd_status st = ensure_norm_ws(p, nw);
     if (st != DD_OK) return st;
-    cudaError_t e = cudaMemcpyAsync(p->dev.widths, widths, (size_t)nw * sizeof(int32_t),
-                                    cudaMemcpyHostToDevice, s);
-    if (e != cudaSuccess) return cuda_status(e);
+    cudaError_t e = cudaSuccess;
+    if (p->widths_on_dev.size() != (size_t)nw ||
+        !std::equal(widths, widths + nw, p->widths_on_dev.begin())) {
+        // a new width list: copy it synchronously (the host array may be a temporary)
+        e = cudaMemcpyAsync(p->dev.widths, widths, (size_t)nw * sizeof(int32_t),
+                            cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_status(e);
+        p->widths_on_dev.assign(widths, widths + nw);
+    }
     const size_t red = (size_t)8 * nw * sizeof(float);
     if (red > 48 * 1024) {
         e = cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red);

@@ -73,6 +73,7 @@ struct dd_plan_s {
     int32_t nch = 1;                   // time chunks per CTA (trials per CTA = 8 / nch)
     bool dev_dirty = true;
     dd::DevTables dev;
+    std::vector<int32_t> widths_on_dev;  // widths last copied to dev.widths
 };
 
 namespace dd {

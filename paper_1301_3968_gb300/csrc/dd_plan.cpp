@@ -156,6 +156,7 @@ static void free_dev(dd_plan_s* p) {
     cudaFree(p->dev.widths);
     if (cur >= 0 && cur != p->dev.device) cudaSetDevice(cur);
     p->dev = DevTables{};
+    p->widths_on_dev.clear();
 }
 
 template <typename T>

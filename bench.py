@@ -36,6 +36,7 @@ UNIT = "DM-trial·samples/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
 N_SM = 152
 FP32_LANES_PER_SM = 128
+LAUNCHES_PER_STEP = 4    # channel stats, dedispersion, normaliser, boxcar scan
 
 
 def _peaks():
@@ -176,7 +177,7 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)      # 256 MiB > 129 MB L2
     out = torch.empty((W["ndm"], W["t_out"]), dtype=torch.float32, device=dev)
-    launches_per_step = 4    # channel stats, dedispersion, normaliser, boxcar scan
+    launches_per_step = LAUNCHES_PER_STEP
 
     def step(ev=None):
         mean, sd = plan.channel_stats(x, nsamp=W["nsamp"])
@@ -295,7 +296,7 @@ def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e):
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
                    "parallelism": f"replicas x{ws} (independent blocks per GPU)"},
         "e2e": e2e,
-        "gpu_launches": launches_per_step * args.steps,
+        "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "roofline": {"bound": "alu", "kernel": "k_dedisp<float,float,weighted>",
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,

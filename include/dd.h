@@ -172,6 +172,19 @@ dd_status dd_backward(dd_plan_t plan, const float* d_in, int64_t in_ld, int64_t 
                       int64_t nsamp, const float* d_gout, int64_t gout_ld, float* d_gw,
                       float* d_gin, int64_t gin_ld, void* stream);
 
+/* Device-side errors: synchronises `stream`, then returns in *code the first error a
+ * kernel of this plan recorded since the last call (0 = none; DD_ERR_TIMEOUT when a
+ * bounded wait on a bulk-copy barrier ran out) and clears it.  Errors: DD_ERR_ARG,
+ * DD_ERR_CUDA. */
+dd_status dd_get_device_status(dd_plan_t plan, int32_t* code, void* stream);
+
+/* Test hook for the failure path of the dedispersion pipeline: the bulk copies of
+ * channel stage `skip_stage` (-1: none) are never issued, and every barrier wait gives
+ * up after wait_ns (0 restores the default of 2 s).  The kernel then records
+ * DD_ERR_TIMEOUT, drains the copies it did issue and returns; no GPU fault is involved.
+ * Errors: DD_ERR_ARG. */
+dd_status dd_test_set_wait(dd_plan_t plan, int32_t skip_stage, int64_t wait_ns);
+
 /* Releases the plan's host and device memory (after its work has finished). */
 dd_status dd_plan_destroy(dd_plan_t plan);
 

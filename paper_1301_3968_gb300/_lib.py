@@ -57,6 +57,8 @@ SIGNATURES = {
     "dd_boxcar_snr": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp,
                               c_f32, c_vp, c_i32, c_vp, c_vp]),
     "dd_backward": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp]),
+    "dd_get_device_status": (c_i32, [c_vp, c_vp, c_vp]),
+    "dd_test_set_wait": (c_i32, [c_vp, c_i32, c_i64]),
     "dd_plan_destroy": (c_i32, [c_vp]),
     "dd_status_str": (ctypes.c_char_p, [c_i32]),
     "dd_version": (c_i32, []),

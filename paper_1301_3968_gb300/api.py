@@ -196,6 +196,18 @@ class Plan:
               "dd_backward")
         return gw, gin
 
+    def device_status(self, stream=None) -> int:
+        """Synchronises the stream and returns (and clears) the first device-side error
+        code a kernel of this plan recorded (0 = none)."""
+        code = ctypes.c_int32(0)
+        check(self._lib.dd_get_device_status(self._h, ctypes.cast(ctypes.byref(code), ctypes.c_void_p),
+                                             _stream(stream)), "dd_get_device_status")
+        return code.value
+
+    def test_set_wait(self, skip_stage: int = -1, wait_ns: int = 0) -> None:
+        """Test hook: never issue the copies of one channel stage; bound waits by wait_ns."""
+        check(self._lib.dd_test_set_wait(self._h, int(skip_stage), int(wait_ns)), "dd_test_set_wait")
+
     def close(self) -> None:
         if getattr(self, "_h", None):
             self._lib.dd_plan_destroy(self._h)

@@ -8,16 +8,23 @@
 //     chunk_start + l*kR + r, r < kR.  The plan picks the largest db whose staged
 //     window fits in shared memory (db = 8 whenever neighbouring trials have close
 //     delays, as every trial list of eq. trial DMs does).
-//   * Channels are streamed in stages of cs rows.  For each channel the CTA stages
-//     the window that all its trials read -- [T0 + min delta, T0 + tile + max(delta + n))
-//     rounded to 16-byte chunks -- into shared memory with cp.async, NBUF stages deep,
-//     so every staged sample is reused by db trials x up to n_dc taps.
+//   * Channels are streamed in stages of cs rows through a ring of NBUF shared-memory
+//     buffers.  For each channel the CTA stages the window that all its trials read --
+//     [T0 + min delta, T0 + tile + max(delta + n)) rounded to 16-byte chunks -- with one
+//     bulk copy (cp.async.bulk, the TMA engine), plus one bulk copy of the stage's
+//     profile record (delays, taps, weights).  Each buffer has a full mbarrier that
+//     counts the copied bytes.
+//   * Warps do not synchronise with each other per stage: after consuming a buffer each
+//     warp increments the buffer's counter, and the last of the 8 refills it with the
+//     stage NBUF ahead.  A warp can run up to NBUF-1 stages ahead of the slowest one.
+//   * Every wait is bounded by time; a wait that runs out records DD_ERR_TIMEOUT in the
+//     plan's status word, the CTA drains its own copies in flight and returns.
 //   * Inner loop: a register window of kR samples slides along the taps; each tap
-//     costs one shared-memory load, one weight broadcast and kR FMAs (or integer
-//     adds).  kR is odd, so the lane-strided loads hit 32 distinct banks.
-//   * fp32 sums accumulate each stage's channels in a fresh partial that is then
-//     added to the running total (two-level summation); uint8 unit-weight sums are
-//     exact int32.
+//     costs one shared-memory load, one weight broadcast and kR FMAs (or exact int32
+//     adds for uint8 unit-weight plans).  kR is odd, so the lane-strided loads hit 32
+//     distinct banks.
+//   * Sums run over channels, then taps, in a fixed order, so results are
+//     deterministic.
 //   * Results are transposed through shared memory so that global stores coalesce.
 #include <cstdint>
 
@@ -33,26 +40,65 @@ struct DedispArgs {
     void* out;
     int64_t out_ld;
     int32_t t_out;
-    const int32_t* delay;
-    const int32_t* taps;
-    const float* w;
-    int32_t kpad;
-    const int32_t* blk_lo;
+    const unsigned char* rec;  // [nblk][nst][rec_bytes]
+    const int32_t* blk_lo;     // [nblk][nchan]
     int32_t nchan;
     int32_t ndm;
     int32_t lcap;
     int32_t cs;   // channels per stage
     int32_t nch;  // time chunks per CTA (trials per CTA = kWarps / nch)
+    int32_t kpad;
+    int32_t* status;
+    int32_t skip_stage;
+    int64_t wait_ns;
 };
 
-__device__ __forceinline__ void cp_async16(void* smem, const void* gmem) {
-    unsigned s = (unsigned)__cvta_generic_to_shared(smem);
-    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(s), "l"(gmem) : "memory");
+__device__ __forceinline__ uint32_t su32(const void* p) {
+    return (uint32_t)__cvta_generic_to_shared(p);
 }
-__device__ __forceinline__ void cp_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
-template <int N>
-__device__ __forceinline__ void cp_wait() {
-    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+__device__ __forceinline__ void mbar_init(uint64_t* bar, uint32_t count) {
+    asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;\n" ::"r"(su32(bar)), "r"(count) : "memory");
+}
+__device__ __forceinline__ void fence_mbar_init() {
+    asm volatile("fence.mbarrier_init.release.cluster;\n" ::: "memory");
+}
+__device__ __forceinline__ void fence_proxy_async() {
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint64_t* bar, uint32_t bytes) {
+    asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;\n" ::"r"(su32(bar)), "r"(bytes)
+                 : "memory");
+}
+__device__ __forceinline__ bool mbar_try_wait(uint64_t* bar, uint32_t parity) {
+    uint32_t ok;
+    asm volatile(
+        "{\n .reg .pred p;\n mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n"
+        " selp.u32 %0, 1, 0, p;\n}\n"
+        : "=r"(ok)
+        : "r"(su32(bar)), "r"(parity)
+        : "memory");
+    return ok != 0;
+}
+__device__ __forceinline__ uint64_t global_ns() {
+    uint64_t t;
+    asm volatile("mov.u64 %0, %%globaltimer;\n" : "=l"(t));
+    return t;
+}
+// Waits for the phase of `bar` with the given parity, for at most limit_ns.
+__device__ __forceinline__ bool mbar_wait_bounded(uint64_t* bar, uint32_t parity, int64_t limit_ns) {
+    if (mbar_try_wait(bar, parity)) return true;
+    const uint64_t t0 = global_ns();
+    while (!mbar_try_wait(bar, parity)) {
+        if ((int64_t)(global_ns() - t0) > limit_ns) return false;
+    }
+    return true;
+}
+__device__ __forceinline__ void bulk_g2s(void* dst, const void* src, uint32_t bytes, uint64_t* bar) {
+    asm volatile(
+        "cp.async.bulk.shared::cluster.global.mbarrier::complete_tx::bytes [%0], [%1], %2, [%3];\n" ::"r"(
+            su32(dst)),
+        "l"(src), "r"(bytes), "r"(su32(bar))
+        : "memory");
 }
 
 template <typename TIN>
@@ -71,74 +117,118 @@ __device__ __forceinline__ TACC cvt(TIN v) {
     return (TACC)v;
 }
 
-template <typename TIN, bool UNIT>
-struct StageLayout : StageBytes {
-    __host__ __device__ StageLayout(int lcap, int kpad, int cs)
-        : StageBytes((int)sizeof(TIN), UNIT, lcap, kpad, cs) {}
+struct Smem {
+    unsigned char* stages;
+    int* lo_all;
+    uint64_t* full;
+    int* cnt;
+    int* issued;
 };
 
-template <typename TIN, bool UNIT>
-__device__ __forceinline__ void load_stage(const DedispArgs& a, unsigned char* buf,
-                                           const StageLayout<TIN, UNIT>& L, int stage,
-                                           int blk, int64_t t0) {
+template <int NBUF>
+__device__ __forceinline__ Smem carve(unsigned char* smem, const StageGeom& g, int nchan) {
+    Smem s;
+    s.stages = smem;
+    s.lo_all = (int*)(smem + NBUF * g.bytes);
+    s.full = (uint64_t*)(smem + NBUF * g.bytes + ((4 * nchan + 15) & ~15));
+    s.cnt = (int*)(s.full + NBUF);
+    s.issued = s.cnt + NBUF;
+    return s;
+}
+
+// Issues the bulk copies of stage `stage` into buffer `b` (one thread).  In the common
+// case every staged window lies inside its row and each channel is one full-length
+// copy; CTAs whose windows run past the end of the rows (`tail`) zero the missing part
+// first and copy only what exists.
+template <typename TIN, bool UNIT, int NBUF>
+__device__ void issue_stage(const DedispArgs& a, const StageGeom& g, const Smem& sm, int blk,
+                            int stage, int b, int64_t base, bool tail) {
     constexpr int Q = Elem<TIN>::Q;
-    const int CS = a.cs;
-    const int db = kWarps / a.nch;
-    const int tid = threadIdx.x;
-    const int c0 = stage * CS;
-    const int csn = min(CS, a.nchan - c0);
-    const int nq = a.lcap / Q;
+    if (stage == a.skip_stage) return;  // test hook: this stage is never filled
+    unsigned char* buf = sm.stages + b * g.bytes;
+    const int c0 = stage * a.cs;
+    const int csn = min(a.cs, a.nchan - c0);
     const TIN* in = (const TIN*)a.in;
-    const int64_t base = a.t_offset + t0;
-    // staged rows: chunk j of channel ci holds global columns a0 + j*Q .. +Q-1
-    for (int idx = tid; idx < csn * nq; idx += blockDim.x) {
-        const int ci = idx / nq;
-        const int j = idx - ci * nq;
+    const int nst = (a.nchan + a.cs - 1) / a.cs;
+    const unsigned char* rec = a.rec + ((int64_t)blk * nst + stage) * g.rec_bytes;
+    const uint32_t row_bytes = (uint32_t)a.lcap * sizeof(TIN);
+    if (!tail) {
+        mbar_expect_tx(&sm.full[b], (uint32_t)csn * row_bytes + g.rec_bytes);
+        for (int ci = 0; ci < csn; ++ci) {
+            const int c = c0 + ci;
+            const int64_t a0 = (base + sm.lo_all[c]) & ~(int64_t)(Q - 1);
+            bulk_g2s(buf + ci * row_bytes, in + (int64_t)c * a.ld + a0, row_bytes, &sm.full[b]);
+        }
+        bulk_g2s(buf + g.rec_off, rec, (uint32_t)g.rec_bytes, &sm.full[b]);
+        sm.issued[b] += 1;
+        return;
+    }
+    uint32_t bytes = g.rec_bytes;
+    // zero the parts of the windows past the end of the rows first (generic stores,
+    // published by the barrier's arrive below)
+    for (int ci = 0; ci < csn; ++ci) {
+        const int64_t a0 = (base + sm.lo_all[c0 + ci]) & ~(int64_t)(Q - 1);
+        const int64_t nin = max((int64_t)0, min((int64_t)a.lcap, a.ld - a0));
+        if (nin < a.lcap) {
+            uint4* z = (uint4*)(buf + ((int64_t)ci * a.lcap + nin) * sizeof(TIN));
+            const int nz = (int)((a.lcap - nin) * sizeof(TIN) / 16);
+            for (int i = 0; i < nz; ++i) z[i] = make_uint4(0, 0, 0, 0);
+        }
+        bytes += (uint32_t)(nin * sizeof(TIN));
+    }
+    fence_proxy_async();
+    mbar_expect_tx(&sm.full[b], bytes);
+    for (int ci = 0; ci < csn; ++ci) {
         const int c = c0 + ci;
-        const int64_t a0 = (base + a.blk_lo[(int64_t)blk * a.nchan + c]) / Q * Q;
-        const int64_t g = a0 + (int64_t)j * Q;
-        unsigned char* dst = buf + ((int64_t)ci * a.lcap + (int64_t)j * Q) * sizeof(TIN);
-        if (g + Q <= a.ld) {
-            cp_async16(dst, in + (int64_t)c * a.ld + g);
-        } else {
-            *(uint4*)dst = make_uint4(0, 0, 0, 0);
-        }
+        const int64_t a0 = (base + sm.lo_all[c]) & ~(int64_t)(Q - 1);
+        const int64_t nin = max((int64_t)0, min((int64_t)a.lcap, a.ld - a0));
+        if (nin > 0)
+            bulk_g2s(buf + (int64_t)ci * a.lcap * sizeof(TIN), in + (int64_t)c * a.ld + a0,
+                     (uint32_t)(nin * sizeof(TIN)), &sm.full[b]);
     }
-    int* e = (int*)(buf + L.e_off);
-    int* dl = (int*)(buf + L.dl_off);
-    int* tp = (int*)(buf + L.tp_off);
-    for (int i = tid; i < CS; i += blockDim.x) {
-        const int c = c0 + i;
-        int ev = 0;
-        if (i < csn) {
-            const int64_t a0 = (base + a.blk_lo[(int64_t)blk * a.nchan + c]) / Q * Q;
-            ev = (int)(base - a0);
-        }
-        e[i] = ev;
-    }
-    for (int idx = tid; idx < db * CS; idx += blockDim.x) {
-        const int wi = idx / CS, ci = idx - wi * CS;
-        const int d = blk * db + wi;
-        int dv = 0, tv = 0;
-        if (ci < csn && d < a.ndm) {
-            dv = a.delay[(int64_t)d * a.nchan + c0 + ci];
-            tv = a.taps[(int64_t)d * a.nchan + c0 + ci];
-        }
-        dl[idx] = dv;
-        tp[idx] = tv;
-    }
-    if (!UNIT) {
-        // weights [d][c0 .. c0+csn)[kpad] are contiguous for each trial d
-        const int nchunk = csn * a.kpad / 4;
-        float* wdst = (float*)(buf + L.w_off);
-        for (int idx = tid; idx < db * nchunk; idx += blockDim.x) {
-            const int wi = idx / nchunk, j = idx - wi * nchunk;
-            const int d = blk * db + wi;
-            float* dst = wdst + (int64_t)wi * CS * a.kpad + j * 4;
-            if (d < a.ndm)
-                cp_async16(dst, a.w + ((int64_t)d * a.nchan + c0) * a.kpad + j * 4);
-            else
-                *(float4*)dst = make_float4(0.f, 0.f, 0.f, 0.f);
+    bulk_g2s(buf + g.rec_off, rec, (uint32_t)g.rec_bytes, &sm.full[b]);
+    sm.issued[b] += 1;
+}
+
+// One stage of one warp: for each of the stage's channels, a register window of kR
+// samples slides along the profile's taps.  At tap k output r reads window sample
+// r + k, held in register (r + k) mod kR; after the tap, sample k (no longer needed)
+// is replaced by sample k + kR.  Each tap costs one shared-memory load, one weight
+// broadcast and kR FMAs (fp32) or adds (exact int32 for uint8 unit weights).  Sums run
+// over channels, then taps, in a fixed order (deterministic); single-precision
+// accumulation of the ~10^3-10^4 terms of an output stays orders of magnitude inside
+// the 1e-5 scale-aware bound.
+template <typename TIN, typename TACC, bool UNIT>
+__device__ __forceinline__ void stage_accumulate(const TIN* rows, const int2* dltp,
+                                                 const float* wts, const int* lo, int csn,
+                                                 int lcap, int kpad, int bq, int lane_off,
+                                                 TACC (&acc)[kR]) {
+    constexpr int Q = Elem<TIN>::Q;
+    constexpr int R = kR;
+    for (int ci = 0; ci < csn; ++ci) {
+        const int2 q = dltp[ci];  // (delay - block minimum, taps)
+        const int n = q.y;
+        const TIN* p = rows + ci * lcap + ((bq + lo[ci]) & (Q - 1)) + q.x + lane_off;
+        const float* wk = wts + ci * kpad;
+        __builtin_assume(__isShared(p));
+        __builtin_assume(__isShared(wk));
+        TACC win[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) win[j] = (TACC)p[j];
+        for (int k0 = 0; k0 < n; k0 += R) {
+#pragma unroll
+            for (int kk = 0; kk < R; ++kk) {
+                if (k0 + kk >= n) break;
+                if (UNIT) {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] += win[(r + kk) % R];
+                } else {
+                    const float wv = wk[k0 + kk];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] = fmaf(wv, (float)win[(r + kk) % R], (float)acc[r]);
+                }
+                win[kk] = (TACC)p[R + k0 + kk];
+            }
         }
     }
 }
@@ -146,73 +236,89 @@ __device__ __forceinline__ void load_stage(const DedispArgs& a, unsigned char* b
 template <typename TIN, typename TACC, bool UNIT, int NBUF>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
     constexpr int R = kR;
+    constexpr int Q = Elem<TIN>::Q;
     extern __shared__ __align__(128) unsigned char smem[];
-    const int CS = a.cs;
-    const StageLayout<TIN, UNIT> L(a.lcap, a.kpad, CS);
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
+    const int cs = a.cs;
+    const int db = kWarps / a.nch;
+    const StageGeom g((int)sizeof(TIN), UNIT, a.lcap, a.kpad, cs, db);
+    const Smem sm = carve<NBUF>(smem, g, a.nchan);
+    const int tid = threadIdx.x;
+    const int warp = tid >> 5, lane = tid & 31;
     const int blk = blockIdx.y;
     const int dmi = warp / a.nch, chunk = warp - dmi * a.nch;
-    const int d = blk * (kWarps / a.nch) + dmi;
-    const int64_t t0 = (int64_t)blockIdx.x * kTileT * a.nch;   // CTA time start
-    const int64_t tw = t0 + (int64_t)chunk * kTileT;            // warp time start
-    const int nst = (a.nchan + CS - 1) / CS;
+    const int d = blk * db + dmi;
+    const int64_t t0 = (int64_t)blockIdx.x * kTileT * a.nch;  // CTA time start
+    const int64_t tw = t0 + (int64_t)chunk * kTileT;           // warp time start
+    const int64_t base = a.t_offset + t0;
+    const int nst = (a.nchan + cs - 1) / cs;
+
+    // per-channel block minima; does any staged window run past the end of its row?
+    int past_end = 0;
+    for (int c = tid; c < a.nchan; c += blockDim.x) {
+        const int lo = a.blk_lo[(int64_t)blk * a.nchan + c];
+        sm.lo_all[c] = lo;
+        past_end |= (((base + lo) & ~(int64_t)(Q - 1)) + a.lcap > a.ld) ? 1 : 0;
+    }
+    const bool tail = __syncthreads_or(past_end) != 0;
+    if (tid == 0) {
+        for (int b = 0; b < NBUF; ++b) {
+            mbar_init(&sm.full[b], 1);
+            sm.cnt[b] = 0;
+            sm.issued[b] = 0;
+        }
+        fence_mbar_init();
+    }
+    __syncthreads();
+    if (tid == 0)
+        for (int s = 0; s < NBUF && s < nst; ++s) issue_stage<TIN, UNIT, NBUF>(a, g, sm, blk, s, s, base, tail);
 
     TACC acc[R];
 #pragma unroll
     for (int r = 0; r < R; ++r) acc[r] = TACC(0);
-
-#pragma unroll
-    for (int s = 0; s < NBUF - 1; ++s) {
-        if (s < nst) load_stage<TIN, UNIT>(a, smem + s * L.bytes, L, s, blk, t0);
-        cp_commit();
-    }
+    const int bq = (int)(base & (Q - 1));
+    const int lane_off = chunk * kTileT + lane * R;
+    bool ok = true;
 
     for (int s = 0; s < nst; ++s) {
-        const int sn = s + NBUF - 1;
-        if (sn < nst) load_stage<TIN, UNIT>(a, smem + (sn % NBUF) * L.bytes, L, sn, blk, t0);
-        cp_commit();
-        cp_wait<NBUF - 1>();
-        __syncthreads();
-
-        if (d < a.ndm) {
-            const unsigned char* buf = smem + (s % NBUF) * L.bytes;
-            const TIN* rows = (const TIN*)buf;
-            const int* e = (const int*)(buf + L.e_off);
-            const int* dl = (const int*)(buf + L.dl_off) + dmi * CS;
-            const int* tp = (const int*)(buf + L.tp_off) + dmi * CS;
-            const float* wts = (const float*)(buf + L.w_off) + dmi * CS * a.kpad;
-            const int csn = min(CS, a.nchan - s * CS);
-            TACC part[R];
-#pragma unroll
-            for (int r = 0; r < R; ++r) part[r] = TACC(0);
-            for (int ci = 0; ci < csn; ++ci) {
-                const int n = tp[ci];
-                const TIN* p = rows + ci * a.lcap + e[ci] + dl[ci] + chunk * kTileT + lane * R;
-                const float* wk = wts + ci * a.kpad;
-                TACC win[R];
-#pragma unroll
-                for (int j = 0; j < R; ++j) win[j] = cvt<TACC>(p[j]);
-                for (int k0 = 0; k0 < n; k0 += R) {
-#pragma unroll
-                    for (int kk = 0; kk < R; ++kk) {
-                        if (k0 + kk >= n) break;
-                        if (UNIT) {
-#pragma unroll
-                            for (int r = 0; r < R; ++r) part[r] += win[(r + kk) % R];
-                        } else {
-                            const float wv = wk[k0 + kk];
-#pragma unroll
-                            for (int r = 0; r < R; ++r) part[r] = fmaf(wv, (float)win[(r + kk) % R], (float)part[r]);
-                        }
-                        win[kk] = cvt<TACC>(p[R + k0 + kk]);
-                    }
-                }
-            }
-#pragma unroll
-            for (int r = 0; r < R; ++r) acc[r] += part[r];
+        const int b = s % NBUF;
+        const bool got = mbar_wait_bounded(&sm.full[b], (uint32_t)((s / NBUF) & 1), a.wait_ns);
+        if (!__all_sync(0xffffffffu, got)) {
+            if (lane == 0) atomicExch(a.status, (int)DD_ERR_TIMEOUT);
+            ok = false;
+            break;
         }
-        __syncthreads();
+        if (d < a.ndm) {
+            // pointers derived from the __shared__ array itself, so that every access
+            // below compiles to a shared-memory load
+            const unsigned char* buf = smem + b * g.bytes;
+            const TIN* rows = (const TIN*)buf;
+            const int2* dltp = (const int2*)(buf + g.rec_off) + dmi * cs;
+            const int* lo_all = (const int*)(smem + NBUF * g.bytes);
+            const int c0 = s * cs;
+            const int csn = min(cs, a.nchan - c0);
+            const float* wts = (const float*)(buf + g.rec_off + g.w_off) + dmi * cs * a.kpad;
+            stage_accumulate<TIN, TACC, UNIT>(rows, dltp, wts, lo_all + c0, csn, a.lcap, a.kpad, bq,
+                                              lane_off, acc);
+        }
+        __syncwarp();
+        if (lane == 0) {
+            __threadfence_block();
+            const int old = atomicAdd(&sm.cnt[b], 1);
+            if (old == kWarps - 1) {  // last warp out refills the buffer
+                sm.cnt[b] = 0;
+                if (s + NBUF < nst) issue_stage<TIN, UNIT, NBUF>(a, g, sm, blk, s + NBUF, b, base, tail);
+            }
+        }
     }
+
+    __syncthreads();
+    if (tid == 0) {  // no copy may still be in flight when the CTA leaves
+        for (int b = 0; b < NBUF; ++b)
+            if (sm.issued[b] > 0 &&
+                !mbar_wait_bounded(&sm.full[b], (uint32_t)((sm.issued[b] - 1) & 1), a.wait_ns))
+                atomicExch(a.status, (int)DD_ERR_TIMEOUT);
+    }
+    if (!__syncthreads_and(ok)) return;
 
     // transpose through shared memory and store coalesced
     TACC* st = (TACC*)smem + warp * (32 * R);
@@ -231,22 +337,49 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
 
 template <typename TIN, typename TACC, bool UNIT, int NBUF>
 dd_status run(const DedispArgs& a, cudaStream_t s) {
-    const StageLayout<TIN, UNIT> L(a.lcap, a.kpad, a.cs);
-    size_t smem = (size_t)NBUF * L.bytes;
+    const int db = kWarps / a.nch;
+    const StageGeom g((int)sizeof(TIN), UNIT, a.lcap, a.kpad, a.cs, db);
+    size_t smem = (size_t)dedisp_smem_bytes(g, NBUF, a.nchan);
     const size_t st_bytes = (size_t)kWarps * 32 * kR * sizeof(TACC);
     if (smem < st_bytes) smem = st_bytes;
     auto kern = k_dedisp<TIN, TACC, UNIT, NBUF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
     const int64_t tile = (int64_t)kTileT * a.nch;
-    const int db = kWarps / a.nch;
     dim3 grid((unsigned)((a.t_out + tile - 1) / tile), (unsigned)((a.ndm + db - 1) / db));
     if (grid.y > 65535) return DD_ERR_UNSUPPORTED;
     kern<<<grid, kWarps * 32, smem, s>>>(a);
     return cuda_status(cudaGetLastError());
 }
 
+// Copies the device weights [d][c][kpad] into the stage records' weight slots.
+__global__ void k_repack_w(const float* w, unsigned char* rec, int32_t rec_bytes, int32_t w_off,
+                           int32_t nchan, int32_t ndm, int32_t cs, int32_t db, int32_t kpad,
+                           int32_t nst) {
+    const int rid = blockIdx.x;  // record = (block, stage)
+    const int blk = rid / nst, st = rid - blk * nst;
+    float* dst = (float*)(rec + (int64_t)rid * rec_bytes + w_off);
+    const int n = db * cs * kpad;
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+        const int k = i % kpad;
+        const int j = i / kpad;
+        const int dmi = j / cs, ci = j - dmi * cs;
+        const int d = blk * db + dmi, c = st * cs + ci;
+        dst[i] = (d < ndm && c < nchan) ? w[((int64_t)d * nchan + c) * kpad + k] : 0.f;
+    }
+}
+
 }  // namespace
+
+dd_status launch_repack(dd_plan_s* p, cudaStream_t s) {
+    if (p->unit) return DD_OK;
+    const int db = kWarps / p->nch;
+    const int nst = (p->nchan + p->cs - 1) / p->cs;
+    const StageGeom g(p->band.in_type == DD_U8 ? 1 : 4, false, p->lcap, p->kpad, p->cs, db);
+    k_repack_w<<<p->nblk * nst, 256, 0, s>>>(p->dev.w, p->dev.rec, g.rec_bytes, g.w_off, p->nchan,
+                                              p->ndm, p->cs, db, p->kpad, nst);
+    return cuda_status(cudaGetLastError());
+}
 
 dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
                             int64_t t_out, void* out, int64_t out_ld, cudaStream_t s) {
@@ -257,16 +390,17 @@ dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_
     a.out = out;
     a.out_ld = out_ld;
     a.t_out = (int32_t)t_out;
-    a.delay = p->dev.delay;
-    a.taps = p->dev.taps;
-    a.w = p->dev.w;
-    a.kpad = p->kpad;
+    a.rec = p->dev.rec;
     a.blk_lo = p->dev.blk_lo;
     a.nchan = p->nchan;
     a.ndm = p->ndm;
     a.lcap = p->lcap;
     a.cs = p->cs;
     a.nch = p->nch;
+    a.kpad = p->unit ? 0 : p->kpad;
+    a.status = p->dev.status;
+    a.skip_stage = p->debug_skip_stage;
+    a.wait_ns = p->wait_ns;
     const bool u8 = p->band.in_type == DD_U8;
     if (u8 && p->unit) return run<uint8_t, int, true, kStages>(a, s);
     if (u8) return run<uint8_t, float, false, kStages>(a, s);

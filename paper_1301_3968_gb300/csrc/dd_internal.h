@@ -17,24 +17,33 @@ namespace dd {
 constexpr int kWarps = 8;
 constexpr int kR = 31;
 constexpr int kTileT = 32 * kR;
-constexpr int kStages = 3;                 // cp.async pipeline depth
-constexpr int kSmemBudget = 200 * 1024;    // dynamic shared memory per dedispersion CTA
+constexpr int kStages = 4;                 // bulk-copy pipeline depth
+constexpr int kSmemBudget = 110 * 1024;    // dynamic shared memory per CTA (two per SM)
+constexpr int kSmemBudgetOne = 220 * 1024; // fallback: one CTA per SM
+constexpr long long kWaitNs = 2000000000;  // bound on any device-side barrier wait
 
-// Byte layout of one dedispersion pipeline stage in shared memory: cs staged rows of
-// lcap elements, then per-channel window offsets, the delay and tap tables of the
-// CTA's trials, and (weighted plans) their per-tap weights.
-struct StageBytes {
-    int rows_bytes, e_off, dl_off, tp_off, w_off, bytes;
-    __host__ __device__ StageBytes(int esz, bool unit, int lcap, int kpad, int cs) {
-        rows_bytes = cs * lcap * esz;
-        e_off = (rows_bytes + 15) & ~15;
-        dl_off = e_off + cs * 4;
-        tp_off = dl_off + kWarps * cs * 4;
-        w_off = (tp_off + kWarps * cs * 4 + 15) & ~15;
-        bytes = w_off + (unit ? 0 : kWarps * cs * kpad * 4);
-        bytes = (bytes + 127) & ~127;
+// Byte layout of one dedispersion pipeline stage in shared memory: cs staged input
+// rows of lcap elements, then the stage's profile record -- (delay minus the block's
+// minimum delay for the channel, taps) of the CTA's db trials for the cs channels and,
+// for weighted plans, their per-tap weights.  The
+// record is stored in this layout in global memory ([block][stage][rec_bytes]) and
+// staged by one bulk copy.
+struct StageGeom {
+    int rows_bytes, rec_off, rec_bytes, w_off, bytes;
+    __host__ __device__ StageGeom(int esz, bool unit, int lcap, int kpad, int cs, int db) {
+        rows_bytes = (cs * lcap * esz + 15) & ~15;
+        rec_off = rows_bytes;
+        w_off = 8 * db * cs;
+        rec_bytes = (w_off + (unit ? 0 : 4 * db * cs * kpad) + 15) & ~15;
+        bytes = (rec_off + rec_bytes + 127) & ~127;
     }
 };
+
+// Shared memory of a dedispersion CTA beyond its stages: the block's per-channel
+// minimum delays and the pipeline's barriers and counters.
+__host__ __device__ inline int dedisp_smem_bytes(const StageGeom& g, int nbuf, int nchan) {
+    return nbuf * g.bytes + ((4 * nchan + 15) & ~15) + nbuf * 8 + 2 * nbuf * 4;
+}
 
 struct DevTables {
     int device = -1;
@@ -42,6 +51,8 @@ struct DevTables {
     int32_t* taps = nullptr;    // [ndm][nchan]
     float* w = nullptr;         // [ndm][nchan][kpad]  (weighted plans)
     int32_t* blk_lo = nullptr;  // [nblk][nchan] minimum delay over the CTA's trials
+    unsigned char* rec = nullptr;  // [nblk][nstage][rec_bytes] staged profile records
+    int32_t* status = nullptr;  // device status word (0 = ok)
     // boxcar normaliser workspace
     double* off = nullptr;      // [ndm]  per-trial offset subtracted before summing
     float* mu = nullptr;        // [ndm][ws_w] mean of B_w minus w*off
@@ -71,6 +82,11 @@ struct dd_plan_s {
     int32_t lcap = 0;                  // staged row length (elements)
     int32_t cs = 4;                    // channels per pipeline stage
     int32_t nch = 1;                   // time chunks per CTA (trials per CTA = 8 / nch)
+    int32_t rec_bytes = 0;             // bytes of one stage's profile record
+    std::vector<unsigned char> rec;    // host copy of the records
+    bool rec_from_dev_w = false;       // records' weights come from dev.w (device weights)
+    int32_t debug_skip_stage = -1;     // test hook: a stage whose bulk copies are never issued
+    int64_t wait_ns = dd::kWaitNs;
     bool dev_dirty = true;
     dd::DevTables dev;
     std::vector<int32_t> widths_on_dev;  // widths last copied to dev.widths
@@ -79,6 +95,7 @@ struct dd_plan_s {
 namespace dd {
 
 dd_status upload_tables(dd_plan_s* p);  // (re)creates the device tables if dirty
+dd_status launch_repack(dd_plan_s* p, cudaStream_t s);  // dev.w -> records' weights
 dd_status cuda_status(cudaError_t e);
 
 // launchers (stream = cudaStream_t)

@@ -71,36 +71,72 @@ int64_t block_span(const dd_plan_s* p, int db, std::vector<int32_t>* lo_out) {
     return span;
 }
 
+// Lays the profile tables out as the kernel stages them: one record per (trial block,
+// channel stage) holding (delay, taps) of the block's trials for the stage's channels
+// followed, for weighted plans, by their per-tap weights.
+void build_records(dd_plan_s* p) {
+    const int C = p->nchan;
+    const int db = dd::kWarps / p->nch;
+    const int nst = (C + p->cs - 1) / p->cs;
+    const int kpad = p->unit ? 0 : p->kpad;
+    const dd::StageGeom g(p->band.in_type == DD_U8 ? 1 : 4, p->unit, p->lcap, kpad, p->cs, db);
+    p->rec_bytes = g.rec_bytes;
+    p->rec.assign((size_t)p->nblk * nst * g.rec_bytes, 0);
+    for (int b = 0; b < p->nblk; ++b)
+        for (int st = 0; st < nst; ++st) {
+            unsigned char* r = p->rec.data() + ((size_t)b * nst + st) * g.rec_bytes;
+            int32_t* dltp = (int32_t*)r;
+            float* w = (float*)(r + g.w_off);
+            for (int i = 0; i < db; ++i)
+                for (int ci = 0; ci < p->cs; ++ci) {
+                    const int d = b * db + i, c = st * p->cs + ci;
+                    if (d >= p->ndm || c >= C) continue;
+                    const size_t dc = (size_t)d * C + c;
+                    dltp[2 * (i * p->cs + ci)] = p->delay[dc] - p->blk_lo[(size_t)b * C + c];
+                    dltp[2 * (i * p->cs + ci) + 1] = p->taps[dc];
+                    for (int k = 0; k < kpad; ++k)
+                        w[(size_t)(i * p->cs + ci) * kpad + k] = p->w[dc * kpad + k];
+                }
+        }
+}
+
 // Chooses the CTA shape of the dedispersion kernel (trials x time chunks), the staged
 // window length and the channels per pipeline stage.  The most trials per CTA (the
 // most reuse of each staged sample) whose window still fits is taken.
 dd_status build_schedule(dd_plan_s* p) {
     const bool u8 = p->band.in_type == DD_U8;
     const int64_t q = u8 ? 16 : 4;            // elements per 16-byte chunk
-    const int64_t esz = u8 ? 1 : 4;
-    const int64_t cs_want = u8 ? 8 : 4;
-    for (int nch = 1; nch <= dd::kWarps; nch *= 2) {
-        const int db = dd::kWarps / nch;
-        const int64_t span = block_span(p, db, nullptr);
-        // the CTA's outputs, the block's delay spread plus taps, 16 bytes of alignment
-        // slack and one element that the register pipeline reads ahead
-        int64_t need = (int64_t)nch * dd::kTileT + span + q + 2;
-        need = (need + q - 1) / q * q;
-        if (need > (1 << 24)) continue;
-        int64_t cs = cs_want;
-        const int kpad = p->unit ? 0 : p->kpad;
-        while (cs > 0 && (int64_t)dd::kStages *
-                                 dd::StageBytes((int)esz, p->unit, (int)need, kpad, (int)cs).bytes >
-                             dd::kSmemBudget)
-            --cs;
-        if (cs < (nch == dd::kWarps ? 1 : cs_want)) continue;
-        p->nch = nch;
-        p->cs = (int32_t)cs;
-        p->lcap = (int32_t)need;
-        p->nblk = (p->ndm + db - 1) / db;
-        block_span(p, db, &p->blk_lo);
-        p->dev_dirty = true;
-        return DD_OK;
+    const int esz = u8 ? 1 : 4;
+    const int cs_want = u8 ? 8 : 4;
+    const int kpad = p->unit ? 0 : p->kpad;
+    // first pass: shared memory for two CTAs per SM and at least two channels per
+    // stage; second pass: one CTA per SM, any stage size
+    const int budgets[2] = {dd::kSmemBudget, dd::kSmemBudgetOne};
+    const int min_cs[2] = {2, 1};
+    for (int pass = 0; pass < 2; ++pass) {
+        for (int nch = 1; nch <= dd::kWarps; nch *= 2) {
+            const int db = dd::kWarps / nch;
+            const int64_t span = block_span(p, db, nullptr);
+            // the CTA's outputs, the block's delay spread plus taps, 16 bytes of
+            // alignment slack and the elements that the register pipeline reads ahead
+            int64_t need = (int64_t)nch * dd::kTileT + span + q + 2;
+            need = (need + q - 1) / q * q;
+            if (need > (1 << 22)) continue;
+            int cs = cs_want;
+            while (cs >= min_cs[pass] &&
+                   dd::dedisp_smem_bytes(dd::StageGeom(esz, p->unit, (int)need, kpad, cs, db),
+                                         dd::kStages, p->nchan) > budgets[pass])
+                --cs;
+            if (cs < min_cs[pass]) continue;
+            p->nch = nch;
+            p->cs = cs;
+            p->lcap = (int32_t)need;
+            p->nblk = (p->ndm + db - 1) / db;
+            block_span(p, db, &p->blk_lo);
+            build_records(p);
+            p->dev_dirty = true;
+            return DD_OK;
+        }
     }
     return DD_ERR_UNSUPPORTED;
 }
@@ -150,6 +186,8 @@ static void free_dev(dd_plan_s* p) {
     cudaFree(p->dev.taps);
     cudaFree(p->dev.w);
     cudaFree(p->dev.blk_lo);
+    cudaFree(p->dev.rec);
+    cudaFree(p->dev.status);
     cudaFree(p->dev.off);
     cudaFree(p->dev.mu);
     cudaFree(p->dev.isd);
@@ -180,6 +218,9 @@ dd_status upload_tables(dd_plan_s* p) {
     if ((st = put(&p->dev.taps, p->taps.data(), n)) != DD_OK) return st;
     if (!p->unit && (st = put(&p->dev.w, p->w.data(), p->w.size())) != DD_OK) return st;
     if ((st = put(&p->dev.blk_lo, p->blk_lo.data(), p->blk_lo.size())) != DD_OK) return st;
+    if ((st = put(&p->dev.rec, p->rec.data(), p->rec.size())) != DD_OK) return st;
+    const int32_t zero = 0;
+    if ((st = put(&p->dev.status, &zero, 1)) != DD_OK) return st;
     e = cudaMalloc((void**)&p->dev.off, (size_t)p->ndm * sizeof(double));
     if (e != cudaSuccess) return cuda_status(e);
     p->dev_dirty = false;
@@ -350,7 +391,8 @@ dd_status dd_set_weights_device(dd_plan_t p, const float* d_w, int32_t kmax, voi
                                       (size_t)kmax * sizeof(float), (size_t)kmax * sizeof(float),
                                       (size_t)p->ndm * p->nchan, cudaMemcpyDeviceToDevice,
                                       (cudaStream_t)stream);
-    return dd::cuda_status(e);
+    if (e != cudaSuccess) return dd::cuda_status(e);
+    return dd::launch_repack(p, (cudaStream_t)stream);
 }
 
 dd_status dd_plan_info(dd_plan_t p, int64_t* t_out, int32_t* d_max, int32_t* kmax,
@@ -432,6 +474,26 @@ dd_status dd_backward(dd_plan_t p, const float* in, int64_t in_ld, int64_t t_off
     if (st != DD_OK) return st;
     return dd::launch_backward(p, in, in_ld, t_offset, t_out, g, gld, gw, gin, gin_ld,
                                (cudaStream_t)stream);
+}
+
+dd_status dd_get_device_status(dd_plan_t p, int32_t* code, void* stream) {
+    if (!p || !code) return DD_ERR_ARG;
+    *code = 0;
+    if (p->dev.device < 0 || !p->dev.status) return DD_OK;
+    cudaError_t e = cudaStreamSynchronize((cudaStream_t)stream);
+    int32_t v = 0;
+    if (e == cudaSuccess) e = cudaMemcpy(&v, p->dev.status, sizeof(v), cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess && v != 0) e = cudaMemset(p->dev.status, 0, sizeof(int32_t));
+    if (e != cudaSuccess) return dd::cuda_status(e);
+    *code = v;
+    return DD_OK;
+}
+
+dd_status dd_test_set_wait(dd_plan_t p, int32_t skip_stage, int64_t wait_ns) {
+    if (!p || wait_ns < 0) return DD_ERR_ARG;
+    p->debug_skip_stage = skip_stage;
+    p->wait_ns = wait_ns > 0 ? wait_ns : dd::kWaitNs;
+    return DD_OK;
 }
 
 dd_status dd_plan_destroy(dd_plan_t p) {

@@ -3,11 +3,12 @@
 //   out[d][t] = sum_c sum_{k < n_dc} w_dck * I[c][t_offset + t + delta_dc + k]
 //
 // Work decomposition (sm_103a):
-//   * A CTA has kWarps = 8 warps covering db consecutive trials x nch time chunks
-//     (db * nch = 8); a chunk is 32 * kR outputs and lane l owns outputs
-//     chunk_start + l*kR + r, r < kR.  The plan picks the largest db whose staged
-//     window fits in shared memory (db = 8 whenever neighbouring trials have close
-//     delays, as every trial list of eq. trial DMs does).
+//   * A CTA has kWarps = 8 warps covering 8 / nch warp units x nch time chunks.  On the
+//     fp32 path a warp unit sums two adjacent trials from one shared register window
+//     (their delays and tap counts differ by at most a sample or so on a trial list of
+//     eq. trial DMs); on the exact integer path it sums one trial.  A chunk is 32 * kR
+//     outputs and lane l owns outputs chunk_start + l*kR + r, r < kR.  The plan picks
+//     the most trials per CTA whose staged window fits in shared memory.
 //   * Channels are streamed in stages of cs rows through a ring of NBUF shared-memory
 //     buffers.  For each channel the CTA stages the window that all its trials read --
 //     [T0 + min delta, T0 + tile + max(delta + n)) rounded to 16-byte chunks -- with one
@@ -20,13 +21,14 @@
 //   * Every wait is bounded by time; a wait that runs out records DD_ERR_TIMEOUT in the
 //     plan's status word, the CTA drains its own copies in flight and returns.
 //   * Inner loop: a register window of kR samples slides along the taps; each tap
-//     costs one shared-memory load, one weight broadcast and kR FMAs (or exact int32
-//     adds for uint8 unit-weight plans).  kR is odd, so the lane-strided loads hit 32
-//     distinct banks.
+//     costs one shared-memory load, one weight-pair broadcast and 2 x kR FMAs (or one
+//     load and kR exact int32 adds for uint8 unit-weight plans).  kR is odd, so the
+//     lane-strided loads hit 32 distinct banks.
 //   * Sums run over channels, then taps, in a fixed order, so results are
 //     deterministic.
 //   * Results are transposed through shared memory so that global stores coalesce.
 #include <cstdint>
+#include <type_traits>
 
 #include "dd_internal.h"
 
@@ -47,7 +49,7 @@ struct DedispArgs {
     int32_t lcap;
     int32_t cs;   // channels per stage
     int32_t nch;  // time chunks per CTA (trials per CTA = kWarps / nch)
-    int32_t kpad;
+    int32_t kpad;  // weight pairs per record entry (pair path)
     int32_t* status;
     int32_t skip_stage;
     int64_t wait_ns;
@@ -140,7 +142,7 @@ __device__ __forceinline__ Smem carve(unsigned char* smem, const StageGeom& g, i
 // case every staged window lies inside its row and each channel is one full-length
 // copy; CTAs whose windows run past the end of the rows (`tail`) zero the missing part
 // first and copy only what exists.
-template <typename TIN, bool UNIT, int NBUF>
+template <typename TIN, int NBUF>
 __device__ void issue_stage(const DedispArgs& a, const StageGeom& g, const Smem& sm, int blk,
                             int stage, int b, int64_t base, bool tail) {
     constexpr int Q = Elem<TIN>::Q;
@@ -190,63 +192,110 @@ __device__ void issue_stage(const DedispArgs& a, const StageGeom& g, const Smem&
     sm.issued[b] += 1;
 }
 
-// One stage of one warp: for each of the stage's channels, a register window of kR
-// samples slides along the profile's taps.  At tap k output r reads window sample
-// r + k, held in register (r + k) mod kR; after the tap, sample k (no longer needed)
-// is replaced by sample k + kR.  Each tap costs one shared-memory load, one weight
-// broadcast and kR FMAs (fp32) or adds (exact int32 for uint8 unit weights).  Sums run
-// over channels, then taps, in a fixed order (deterministic); single-precision
-// accumulation of the ~10^3-10^4 terms of an output stays orders of magnitude inside
-// the 1e-5 scale-aware bound.
-template <typename TIN, typename TACC, bool UNIT>
-__device__ __forceinline__ void stage_accumulate(const TIN* rows, const int2* dltp,
-                                                 const float* wts, const int* lo, int csn,
-                                                 int lcap, int kpad, int bq, int lane_off,
-                                                 TACC (&acc)[kR]) {
+// One stage of one warp unit, exact integer sums of uint8 samples with unit weights:
+// for each of the stage's channels a register window of kR samples slides along the
+// taps.  At tap k output r reads window sample r + k, held in register (r + k) mod kR;
+// after the tap, sample k (no longer needed) is replaced by sample k + kR.  Each tap
+// costs one shared-memory load and kR adds.
+template <typename TIN>
+__device__ __forceinline__ void stage_int(const TIN* rows, const int2* ent, const int* lo,
+                                          int csn, int lcap, int bq, int lane_off,
+                                          int (&acc)[kR]) {
     constexpr int Q = Elem<TIN>::Q;
     constexpr int R = kR;
     for (int ci = 0; ci < csn; ++ci) {
-        const int2 q = dltp[ci];  // (delay - block minimum, taps)
+        const int2 q = ent[ci];  // (window start - block minimum, taps)
         const int n = q.y;
         const TIN* p = rows + ci * lcap + ((bq + lo[ci]) & (Q - 1)) + q.x + lane_off;
-        const float* wk = wts + ci * kpad;
         __builtin_assume(__isShared(p));
-        __builtin_assume(__isShared(wk));
-        TACC win[R];
+        int win[R];
 #pragma unroll
-        for (int j = 0; j < R; ++j) win[j] = (TACC)p[j];
+        for (int j = 0; j < R; ++j) win[j] = (int)p[j];
         for (int k0 = 0; k0 < n; k0 += R) {
 #pragma unroll
             for (int kk = 0; kk < R; ++kk) {
                 if (k0 + kk >= n) break;
-                if (UNIT) {
 #pragma unroll
-                    for (int r = 0; r < R; ++r) acc[r] += win[(r + kk) % R];
-                } else {
-                    const float wv = wk[k0 + kk];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) acc[r] = fmaf(wv, (float)win[(r + kk) % R], (float)acc[r]);
-                }
-                win[kk] = (TACC)p[R + k0 + kk];
+                for (int r = 0; r < R; ++r) acc[r] += win[(r + kk) % R];
+                win[kk] = (int)p[R + k0 + kk];
             }
         }
     }
 }
 
-template <typename TIN, typename TACC, bool UNIT, int NBUF>
+// One stage of one warp unit on the fp32 path: two adjacent trials share the register
+// window.  The entry's window is the union of the two trials' windows, and its weights
+// are (w0, w1) pairs that are zero where a trial has no tap, so each tap costs one
+// window load, one weight-pair broadcast and 2 x kR FMAs.  Sums run over channels,
+// then taps, in a fixed order (deterministic); single-precision accumulation of the
+// ~10^3-10^4 terms of an output stays orders of magnitude inside the 1e-5 scale-aware
+// bound.
+template <typename TIN>
+__device__ __forceinline__ void stage_pair(const TIN* rows, const int2* ent, const float2* wts,
+                                           const int* lo, int csn, int lcap, int kw, int bq,
+                                           int lane_off, float (&acc0)[kR], float (&acc1)[kR]) {
+    constexpr int Q = Elem<TIN>::Q;
+    constexpr int R = kR;
+    for (int ci = 0; ci < csn; ++ci) {
+        const int2 q = ent[ci];
+        const int n = q.y;
+        const TIN* p = rows + ci * lcap + ((bq + lo[ci]) & (Q - 1)) + q.x + lane_off;
+        const float2* wk = wts + ci * kw;
+        __builtin_assume(__isShared(p));
+        __builtin_assume(__isShared(wk));
+        float win[R];
+#pragma unroll
+        for (int j = 0; j < R; ++j) win[j] = (float)p[j];
+        for (int k0 = 0; k0 < n; k0 += R) {
+#pragma unroll
+            for (int kk = 0; kk < R; ++kk) {
+                if (k0 + kk >= n) break;
+                const float2 w = wk[k0 + kk];
+#pragma unroll
+                for (int r = 0; r < R; ++r) {
+                    acc0[r] = fmaf(w.x, win[(r + kk) % R], acc0[r]);
+                    acc1[r] = fmaf(w.y, win[(r + kk) % R], acc1[r]);
+                }
+                win[kk] = (float)p[R + k0 + kk];
+            }
+        }
+    }
+}
+
+template <typename TACC>
+__device__ __forceinline__ void store_row(unsigned char* smem, const TACC (&acc)[kR], int warp,
+                                          int lane, int64_t tw, int32_t t_out, TACC* out) {
+    constexpr int R = kR;
+    TACC* st = (TACC*)smem + warp * (32 * R);
+#pragma unroll
+    for (int r = 0; r < R; ++r) st[lane * R + r] = acc[r];
+    __syncwarp();
+    if (out) {
+#pragma unroll 4
+        for (int j = 0; j < R; ++j) {
+            const int64_t t = tw + j * 32 + lane;
+            if (t < t_out) out[t] = st[j * 32 + lane];
+        }
+    }
+    __syncwarp();
+}
+
+template <typename TIN, bool PAIR, int NBUF>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
     constexpr int R = kR;
     constexpr int Q = Elem<TIN>::Q;
+    constexpr int TPW = PAIR ? 2 : 1;   // trials per warp unit
+    using TACC = typename std::conditional<PAIR, float, int>::type;
     extern __shared__ __align__(128) unsigned char smem[];
     const int cs = a.cs;
-    const int db = kWarps / a.nch;
-    const StageGeom g((int)sizeof(TIN), UNIT, a.lcap, a.kpad, cs, db);
+    const int nu = kWarps / a.nch;     // warp units per CTA
+    const StageGeom g((int)sizeof(TIN), PAIR, a.lcap, a.kpad, cs, nu);
     const Smem sm = carve<NBUF>(smem, g, a.nchan);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int blk = blockIdx.y;
     const int dmi = warp / a.nch, chunk = warp - dmi * a.nch;
-    const int d = blk * db + dmi;
+    const int d = blk * (TPW * nu) + dmi * TPW;               // first trial of the unit
     const int64_t t0 = (int64_t)blockIdx.x * kTileT * a.nch;  // CTA time start
     const int64_t tw = t0 + (int64_t)chunk * kTileT;           // warp time start
     const int64_t base = a.t_offset + t0;
@@ -270,11 +319,14 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
     }
     __syncthreads();
     if (tid == 0)
-        for (int s = 0; s < NBUF && s < nst; ++s) issue_stage<TIN, UNIT, NBUF>(a, g, sm, blk, s, s, base, tail);
+        for (int s = 0; s < NBUF && s < nst; ++s) issue_stage<TIN, NBUF>(a, g, sm, blk, s, s, base, tail);
 
-    TACC acc[R];
+    TACC acc0[R];
+    float acc1[PAIR ? R : 1];
 #pragma unroll
-    for (int r = 0; r < R; ++r) acc[r] = TACC(0);
+    for (int r = 0; r < R; ++r) acc0[r] = TACC(0);
+#pragma unroll
+    for (int r = 0; r < (PAIR ? R : 1); ++r) acc1[r] = 0.f;
     const int bq = (int)(base & (Q - 1));
     const int lane_off = chunk * kTileT + lane * R;
     bool ok = true;
@@ -292,13 +344,17 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
             // below compiles to a shared-memory load
             const unsigned char* buf = smem + b * g.bytes;
             const TIN* rows = (const TIN*)buf;
-            const int2* dltp = (const int2*)(buf + g.rec_off) + dmi * cs;
+            const int2* ent = (const int2*)(buf + g.rec_off) + dmi * cs;
             const int* lo_all = (const int*)(smem + NBUF * g.bytes);
             const int c0 = s * cs;
             const int csn = min(cs, a.nchan - c0);
-            const float* wts = (const float*)(buf + g.rec_off + g.w_off) + dmi * cs * a.kpad;
-            stage_accumulate<TIN, TACC, UNIT>(rows, dltp, wts, lo_all + c0, csn, a.lcap, a.kpad, bq,
-                                              lane_off, acc);
+            if constexpr (PAIR) {
+                const float2* wts = (const float2*)(buf + g.rec_off + g.w_off) + dmi * cs * a.kpad;
+                stage_pair<TIN>(rows, ent, wts, lo_all + c0, csn, a.lcap, a.kpad, bq, lane_off,
+                                acc0, acc1);
+            } else {
+                stage_int<TIN>(rows, ent, lo_all + c0, csn, a.lcap, bq, lane_off, acc0);
+            }
         }
         __syncwarp();
         if (lane == 0) {
@@ -306,7 +362,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
             const int old = atomicAdd(&sm.cnt[b], 1);
             if (old == kWarps - 1) {  // last warp out refills the buffer
                 sm.cnt[b] = 0;
-                if (s + NBUF < nst) issue_stage<TIN, UNIT, NBUF>(a, g, sm, blk, s + NBUF, b, base, tail);
+                if (s + NBUF < nst) issue_stage<TIN, NBUF>(a, g, sm, blk, s + NBUF, b, base, tail);
             }
         }
     }
@@ -320,64 +376,75 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
     }
     if (!__syncthreads_and(ok)) return;
 
-    // transpose through shared memory and store coalesced
-    TACC* st = (TACC*)smem + warp * (32 * R);
-#pragma unroll
-    for (int r = 0; r < R; ++r) st[lane * R + r] = acc[r];
-    __syncwarp();
-    if (d < a.ndm) {
-        TACC* out = (TACC*)a.out + (int64_t)d * a.out_ld;
-#pragma unroll 4
-        for (int j = 0; j < R; ++j) {
-            const int64_t t = tw + j * 32 + lane;
-            if (t < a.t_out) out[t] = st[j * 32 + lane];
-        }
-    }
+    // transpose through shared memory and store coalesced, one trial row at a time
+    TACC* out = (TACC*)a.out;
+    store_row<TACC>(smem, acc0, warp, lane, tw, a.t_out, d < a.ndm ? out + (int64_t)d * a.out_ld : nullptr);
+    if constexpr (PAIR)
+        store_row<float>(smem, acc1, warp, lane, tw, a.t_out,
+                         d + 1 < a.ndm ? (float*)a.out + (int64_t)(d + 1) * a.out_ld : nullptr);
 }
 
-template <typename TIN, typename TACC, bool UNIT, int NBUF>
+template <typename TIN, bool PAIR, int NBUF>
 dd_status run(const DedispArgs& a, cudaStream_t s) {
-    const int db = kWarps / a.nch;
-    const StageGeom g((int)sizeof(TIN), UNIT, a.lcap, a.kpad, a.cs, db);
+    const int nu = kWarps / a.nch;
+    const StageGeom g((int)sizeof(TIN), PAIR, a.lcap, a.kpad, a.cs, nu);
     size_t smem = (size_t)dedisp_smem_bytes(g, NBUF, a.nchan);
-    const size_t st_bytes = (size_t)kWarps * 32 * kR * sizeof(TACC);
+    const size_t st_bytes = (size_t)kWarps * 32 * kR * 4;
     if (smem < st_bytes) smem = st_bytes;
-    auto kern = k_dedisp<TIN, TACC, UNIT, NBUF>;
+    auto kern = k_dedisp<TIN, PAIR, NBUF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
     const int64_t tile = (int64_t)kTileT * a.nch;
+    const int db = (PAIR ? 2 : 1) * nu;
     dim3 grid((unsigned)((a.t_out + tile - 1) / tile), (unsigned)((a.ndm + db - 1) / db));
     if (grid.y > 65535) return DD_ERR_UNSUPPORTED;
     kern<<<grid, kWarps * 32, smem, s>>>(a);
     return cuda_status(cudaGetLastError());
 }
 
-// Copies the device weights [d][c][kpad] into the stage records' weight slots.
-__global__ void k_repack_w(const float* w, unsigned char* rec, int32_t rec_bytes, int32_t w_off,
-                           int32_t nchan, int32_t ndm, int32_t cs, int32_t db, int32_t kpad,
-                           int32_t nst) {
+// Builds the pair records' (w0, w1) weights from the device weights [d][c][kpad] and
+// the delay and tap tables (the entries themselves do not change).
+__global__ void k_repack_w(const float* w, const int32_t* delay, const int32_t* taps,
+                           unsigned char* rec, int32_t rec_bytes,
+                           int32_t w_off, int32_t nchan, int32_t ndm, int32_t cs, int32_t nu,
+                           int32_t kw, int32_t kpad, int32_t nst) {
     const int rid = blockIdx.x;  // record = (block, stage)
     const int blk = rid / nst, st = rid - blk * nst;
     float* dst = (float*)(rec + (int64_t)rid * rec_bytes + w_off);
-    const int n = db * cs * kpad;
+    const int n = nu * cs * kw;
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int k = i % kpad;
-        const int j = i / kpad;
-        const int dmi = j / cs, ci = j - dmi * cs;
-        const int d = blk * db + dmi, c = st * cs + ci;
-        dst[i] = (d < ndm && c < nchan) ? w[((int64_t)d * nchan + c) * kpad + k] : 0.f;
+        const int k = i % kw;
+        const int e = i / kw;  // entry = (unit, channel)
+        const int j = e / cs, ci = e - j * cs;
+        const int d0 = blk * 2 * nu + 2 * j, c = st * cs + ci;
+        float v[2] = {0.f, 0.f};
+        if (d0 < ndm && c < nchan) {
+            // window start of the entry: the smaller of the two trials' delays
+            int lo = delay[(int64_t)d0 * nchan + c];
+            if (d0 + 1 < ndm) lo = min(lo, delay[(int64_t)(d0 + 1) * nchan + c]);
+            for (int t = 0; t < 2; ++t) {
+                const int dd = d0 + t;
+                if (dd >= ndm) break;
+                const int64_t dc = (int64_t)dd * nchan + c;
+                const int kk = k - (delay[dc] - lo);
+                if (kk >= 0 && kk < taps[dc]) v[t] = w[dc * kpad + kk];
+            }
+        }
+        dst[2 * i] = v[0];
+        dst[2 * i + 1] = v[1];
     }
 }
 
 }  // namespace
 
 dd_status launch_repack(dd_plan_s* p, cudaStream_t s) {
-    if (p->unit) return DD_OK;
-    const int db = kWarps / p->nch;
+    if (!p->pair) return DD_OK;
+    const int nu = kWarps / p->nch;
     const int nst = (p->nchan + p->cs - 1) / p->cs;
-    const StageGeom g(p->band.in_type == DD_U8 ? 1 : 4, false, p->lcap, p->kpad, p->cs, db);
-    k_repack_w<<<p->nblk * nst, 256, 0, s>>>(p->dev.w, p->dev.rec, g.rec_bytes, g.w_off, p->nchan,
-                                              p->ndm, p->cs, db, p->kpad, nst);
+    const StageGeom g(p->band.in_type == DD_U8 ? 1 : 4, true, p->lcap, p->kw, p->cs, nu);
+    k_repack_w<<<p->nblk * nst, 256, 0, s>>>(p->dev.w, p->dev.delay, p->dev.taps, p->dev.rec,
+                                              g.rec_bytes, g.w_off, p->nchan, p->ndm, p->cs, nu,
+                                              p->kw, p->kpad, nst);
     return cuda_status(cudaGetLastError());
 }
 
@@ -397,15 +464,14 @@ dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_
     a.lcap = p->lcap;
     a.cs = p->cs;
     a.nch = p->nch;
-    a.kpad = p->unit ? 0 : p->kpad;
+    a.kpad = p->pair ? p->kw : 0;
     a.status = p->dev.status;
     a.skip_stage = p->debug_skip_stage;
     a.wait_ns = p->wait_ns;
     const bool u8 = p->band.in_type == DD_U8;
-    if (u8 && p->unit) return run<uint8_t, int, true, kStages>(a, s);
-    if (u8) return run<uint8_t, float, false, kStages>(a, s);
-    if (p->unit) return run<float, float, true, kStages>(a, s);
-    return run<float, float, false, kStages>(a, s);
+    if (!p->pair) return run<uint8_t, false, kStages>(a, s);
+    if (u8) return run<uint8_t, true, kStages>(a, s);
+    return run<float, true, kStages>(a, s);
 }
 
 }  // namespace dd

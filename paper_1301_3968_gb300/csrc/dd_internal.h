@@ -10,10 +10,10 @@
 
 namespace dd {
 
-// Dedispersion kernel geometry (see dd_dedisp.cu): a CTA has kWarps warps, one trial
-// per warp, and each lane owns kR consecutive output samples, so a CTA covers kWarps
-// trials x (32 * kR) samples.  kR is odd so that lane-strided shared-memory reads hit
-// distinct banks.
+// Dedispersion kernel geometry (see dd_dedisp.cu): a CTA has kWarps warps; a warp
+// unit sums two adjacent trials (fp32 path) or one trial (exact integer path), and each
+// lane owns kR consecutive output samples.  kR is odd so that lane-strided
+// shared-memory reads hit distinct banks.
 constexpr int kWarps = 8;
 constexpr int kR = 31;
 constexpr int kTileT = 32 * kR;
@@ -23,18 +23,19 @@ constexpr int kSmemBudgetOne = 220 * 1024; // fallback: one CTA per SM
 constexpr long long kWaitNs = 2000000000;  // bound on any device-side barrier wait
 
 // Byte layout of one dedispersion pipeline stage in shared memory: cs staged input
-// rows of lcap elements, then the stage's profile record -- (delay minus the block's
-// minimum delay for the channel, taps) of the CTA's db trials for the cs channels and,
-// for weighted plans, their per-tap weights.  The
-// record is stored in this layout in global memory ([block][stage][rec_bytes]) and
+// rows of lcap elements, then the stage's profile record.  The record holds, for each
+// of the CTA's nu warp units and each of the stage's channels, an entry (window start
+// relative to the block's minimum delay for the channel, taps) and, for fp32 plans,
+// the per-tap weights of the unit's two trials as (w0, w1) pairs (kw pairs per entry).
+// Records are stored in this layout in global memory ([block][stage][rec_bytes]) and
 // staged by one bulk copy.
 struct StageGeom {
     int rows_bytes, rec_off, rec_bytes, w_off, bytes;
-    __host__ __device__ StageGeom(int esz, bool unit, int lcap, int kpad, int cs, int db) {
+    __host__ __device__ StageGeom(int esz, bool has_w, int lcap, int kw, int cs, int nu) {
         rows_bytes = (cs * lcap * esz + 15) & ~15;
         rec_off = rows_bytes;
-        w_off = 8 * db * cs;
-        rec_bytes = (w_off + (unit ? 0 : 4 * db * cs * kpad) + 15) & ~15;
+        w_off = 8 * nu * cs;
+        rec_bytes = (w_off + (has_w ? 8 * nu * cs * kw : 0) + 15) & ~15;
         bytes = (rec_off + rec_bytes + 127) & ~127;
     }
 };
@@ -81,8 +82,10 @@ struct dd_plan_s {
     std::vector<int32_t> blk_lo;       // [nblk][nchan] minimum delay over the block's trials
     int32_t lcap = 0;                  // staged row length (elements)
     int32_t cs = 4;                    // channels per pipeline stage
-    int32_t nch = 1;                   // time chunks per CTA (trials per CTA = 8 / nch)
+    int32_t nch = 1;                   // time chunks per CTA
     int32_t rec_bytes = 0;             // bytes of one stage's profile record
+    bool pair = true;                  // fp32 path: each warp sums two adjacent trials
+    int32_t kw = 0;                    // weight pairs per record entry (pair path)
     std::vector<unsigned char> rec;    // host copy of the records
     bool rec_from_dev_w = false;       // records' weights come from dev.w (device weights)
     int32_t debug_skip_stage = -1;     // test hook: a stage whose bulk copies are never issued

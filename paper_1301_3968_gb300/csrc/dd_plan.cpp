@@ -71,65 +71,107 @@ int64_t block_span(const dd_plan_s* p, int db, std::vector<int32_t>* lo_out) {
     return span;
 }
 
+// Trials per warp unit: two adjacent trials share one register window on the fp32
+// path; the exact integer path sums one trial per warp.
+int trials_per_unit(const dd_plan_s* p) { return p->pair ? 2 : 1; }
+
+// Weight pairs per record entry for a given trial block size: the longest union
+// window [min delta, max(delta + n)) of any warp unit's trials on any channel.
+int32_t union_taps(const dd_plan_s* p, int db) {
+    const int C = p->nchan, tpw = trials_per_unit(p);
+    int64_t u = 0;
+    for (int d0 = 0; d0 < p->ndm; d0 += tpw)
+        for (int c = 0; c < C; ++c) {
+            int64_t lo = INT64_MAX, hi = 0;
+            for (int i = 0; i < tpw && d0 + i < p->ndm; ++i) {
+                const size_t dc = (size_t)(d0 + i) * C + c;
+                lo = std::min<int64_t>(lo, p->delay[dc]);
+                hi = std::max<int64_t>(hi, (int64_t)p->delay[dc] + p->taps[dc]);
+            }
+            u = std::max(u, hi - lo);
+        }
+    (void)db;
+    return (int32_t)std::min<int64_t>(u, INT32_MAX);
+}
+
 // Lays the profile tables out as the kernel stages them: one record per (trial block,
-// channel stage) holding (delay, taps) of the block's trials for the stage's channels
-// followed, for weighted plans, by their per-tap weights.
+// channel stage).  Entry (unit j, channel ci) = (window start - block minimum, taps);
+// on the pair path the window is the union of the unit's two trials' windows and the
+// weights are (w0, w1) pairs, zero where a trial has no tap.
 void build_records(dd_plan_s* p) {
     const int C = p->nchan;
-    const int db = dd::kWarps / p->nch;
+    const int tpw = trials_per_unit(p);
+    const int nu = dd::kWarps / p->nch;
+    const int db = tpw * nu;
     const int nst = (C + p->cs - 1) / p->cs;
-    const int kpad = p->unit ? 0 : p->kpad;
-    const dd::StageGeom g(p->band.in_type == DD_U8 ? 1 : 4, p->unit, p->lcap, kpad, p->cs, db);
+    const int kw = p->pair ? p->kw : 0;
+    const dd::StageGeom g(p->band.in_type == DD_U8 ? 1 : 4, p->pair, p->lcap, kw, p->cs, nu);
     p->rec_bytes = g.rec_bytes;
     p->rec.assign((size_t)p->nblk * nst * g.rec_bytes, 0);
     for (int b = 0; b < p->nblk; ++b)
         for (int st = 0; st < nst; ++st) {
             unsigned char* r = p->rec.data() + ((size_t)b * nst + st) * g.rec_bytes;
-            int32_t* dltp = (int32_t*)r;
+            int32_t* ent = (int32_t*)r;
             float* w = (float*)(r + g.w_off);
-            for (int i = 0; i < db; ++i)
+            for (int j = 0; j < nu; ++j)
                 for (int ci = 0; ci < p->cs; ++ci) {
-                    const int d = b * db + i, c = st * p->cs + ci;
-                    if (d >= p->ndm || c >= C) continue;
-                    const size_t dc = (size_t)d * C + c;
-                    dltp[2 * (i * p->cs + ci)] = p->delay[dc] - p->blk_lo[(size_t)b * C + c];
-                    dltp[2 * (i * p->cs + ci) + 1] = p->taps[dc];
-                    for (int k = 0; k < kpad; ++k)
-                        w[(size_t)(i * p->cs + ci) * kpad + k] = p->w[dc * kpad + k];
+                    const int c = st * p->cs + ci;
+                    const int d0 = b * db + j * tpw;
+                    if (d0 >= p->ndm || c >= C) continue;
+                    int64_t lo = INT64_MAX, hi = 0;
+                    for (int i = 0; i < tpw && d0 + i < p->ndm; ++i) {
+                        const size_t dc = (size_t)(d0 + i) * C + c;
+                        lo = std::min<int64_t>(lo, p->delay[dc]);
+                        hi = std::max<int64_t>(hi, (int64_t)p->delay[dc] + p->taps[dc]);
+                    }
+                    const int e = j * p->cs + ci;
+                    ent[2 * e] = (int32_t)(lo - p->blk_lo[(size_t)b * C + c]);
+                    ent[2 * e + 1] = (int32_t)(hi - lo);
+                    if (!p->pair) continue;
+                    for (int i = 0; i < tpw && d0 + i < p->ndm; ++i) {
+                        const size_t dc = (size_t)(d0 + i) * C + c;
+                        const int off = (int)(p->delay[dc] - lo);
+                        for (int k = 0; k < p->taps[dc]; ++k)
+                            w[((size_t)e * kw + off + k) * 2 + i] = p->unit ? 1.0f : p->w[dc * p->kpad + k];
+                    }
                 }
         }
 }
 
-// Chooses the CTA shape of the dedispersion kernel (trials x time chunks), the staged
-// window length and the channels per pipeline stage.  The most trials per CTA (the
-// most reuse of each staged sample) whose window still fits is taken.
+// Chooses the CTA shape of the dedispersion kernel (warp units x time chunks), the
+// staged window length and the channels per pipeline stage.  The most trials per CTA
+// (the most reuse of each staged sample) whose window still fits is taken.
 dd_status build_schedule(dd_plan_s* p) {
     const bool u8 = p->band.in_type == DD_U8;
+    p->pair = !(u8 && p->unit);
     const int64_t q = u8 ? 16 : 4;            // elements per 16-byte chunk
     const int esz = u8 ? 1 : 4;
     const int cs_want = u8 ? 8 : 4;
-    const int kpad = p->unit ? 0 : p->kpad;
+    const int tpw = trials_per_unit(p);
     // first pass: shared memory for two CTAs per SM and at least two channels per
     // stage; second pass: one CTA per SM, any stage size
     const int budgets[2] = {dd::kSmemBudget, dd::kSmemBudgetOne};
     const int min_cs[2] = {2, 1};
     for (int pass = 0; pass < 2; ++pass) {
         for (int nch = 1; nch <= dd::kWarps; nch *= 2) {
-            const int db = dd::kWarps / nch;
+            const int nu = dd::kWarps / nch;
+            const int db = tpw * nu;
             const int64_t span = block_span(p, db, nullptr);
+            const int32_t kw = p->pair ? ((union_taps(p, db) + 1) & ~1) : 0;
             // the CTA's outputs, the block's delay spread plus taps, 16 bytes of
-            // alignment slack and the elements that the register pipeline reads ahead
+            // alignment slack and the element that the register pipeline reads ahead
             int64_t need = (int64_t)nch * dd::kTileT + span + q + 2;
             need = (need + q - 1) / q * q;
             if (need > (1 << 22)) continue;
             int cs = cs_want;
             while (cs >= min_cs[pass] &&
-                   dd::dedisp_smem_bytes(dd::StageGeom(esz, p->unit, (int)need, kpad, cs, db),
+                   dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu),
                                          dd::kStages, p->nchan) > budgets[pass])
                 --cs;
             if (cs < min_cs[pass]) continue;
             p->nch = nch;
             p->cs = cs;
+            p->kw = kw;
             p->lcap = (int32_t)need;
             p->nblk = (p->ndm + db - 1) / db;
             block_span(p, db, &p->blk_lo);

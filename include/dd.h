@@ -159,6 +159,30 @@ dd_status dd_boxcar_snr(dd_plan_t plan, const void* d_series, int64_t ld, int64_
                         float thresh, dd_candidate* d_cands, int32_t cap,
                         int32_t* d_ncands, void* stream);
 
+/* dd_boxcar_snr for callers that may not allocate device memory while running -- a
+ * real-time pipeline that fixes its device-memory footprint at start-up, or a host
+ * that gives the library a fixed device budget.  The paper has no counterpart; this is
+ * a deployment variant.  Same arguments, results and errors as dd_boxcar_snr, but the
+ * normaliser tables live in an 8 MiB array in device global memory that is part of the
+ * library image (every GPU that loads the library holds it until the process exits),
+ * so the call allocates nothing.  Limits and rules:
+ *   - ndm * 8 + 2 * ndm * nw * 4 + nw * 4 bytes (each part rounded up to 256) must fit
+ *     in 8 MiB (about ndm * nw <= 1,000,000); larger requests return DD_ERR_CAPACITY.
+ *   - The plan's tables must already be on the current device (any earlier device call
+ *     on the plan, e.g. dd_dedisperse, puts them there); otherwise DD_ERR_STATE, since
+ *     uploading them would allocate.
+ *   - The first call on each device looks up the array's device address and caches it;
+ *     make that first call before any stream capture.
+ *   - Every call shares the one array, and it keeps the last call's contents: calls on
+ *     one stream are ordered, but calls that overlap on the GPU (different streams or
+ *     host threads) race.  Nothing in it needs clearing: each call writes every value
+ *     it reads. */
+dd_status dd_boxcar_snr_noalloc(dd_plan_t plan, const void* d_series, int64_t ld, int64_t t_len,
+                                const int32_t* widths, int32_t nw, const double* d_chan_mean,
+                                const double* d_chan_std, float* d_peak_snr, int32_t* d_peak_t,
+                                float thresh, dd_candidate* d_cands, int32_t cap,
+                                int32_t* d_ncands, void* stream);
+
 /* Adjoint of the weighted map of eq. p_dedisp (no counterpart in the paper): given
  * g = d(loss)/d(out) (d_gout [ndm][gout_ld] fp32, nsamp - d_max valid columns),
  *   d_gw [ndm][nchan][kmax] : gw_dck   = sum_t g[d][t] I[c][t_offset + t + delta + k]

@@ -56,6 +56,8 @@ SIGNATURES = {
     "dd_channel_stats": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_i64, c_vp, c_vp, c_vp]),
     "dd_boxcar_snr": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp,
                               c_f32, c_vp, c_i32, c_vp, c_vp]),
+    "dd_boxcar_snr_noalloc": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp,
+                                      c_f32, c_vp, c_i32, c_vp, c_vp]),
     "dd_backward": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp]),
     "dd_get_device_status": (c_i32, [c_vp, c_vp, c_vp]),
     "dd_test_set_wait": (c_i32, [c_vp, c_i32, c_i64]),

@@ -179,6 +179,22 @@ class Plan:
             return peak, arg, None
         return peak, arg, (cands, ncand)
 
+    def boxcar_snr_noalloc(self, series: torch.Tensor, widths, mean: torch.Tensor,
+                           sd: torch.Tensor, peak: torch.Tensor, arg: torch.Tensor,
+                           t_len: int | None = None, thresh: float | None = None,
+                           cands: torch.Tensor | None = None, ncand: torch.Tensor | None = None,
+                           stream=None) -> None:
+        """Boxcar S/N into caller-provided outputs, with no device allocation by the library
+        (scratch in a fixed device array); see dd_boxcar_snr_noalloc in include/dd.h."""
+        wl = np.ascontiguousarray(widths, dtype=np.int32)
+        t_len = series.shape[1] if t_len is None else t_len
+        cap = 0 if cands is None else int(cands.shape[0])
+        check(self._lib.dd_boxcar_snr_noalloc(self._h, _ptr(series), series.stride(0), t_len,
+                                              _np_ptr(wl), len(wl), _ptr(mean), _ptr(sd), _ptr(peak),
+                                              _ptr(arg), float(thresh if thresh is not None else np.inf),
+                                              _ptr(cands), cap, _ptr(ncand), _stream(stream)),
+              "dd_boxcar_snr_noalloc")
+
     def backward(self, x: torch.Tensor, gout: torch.Tensor, t_offset: int = 0,
                  nsamp: int | None = None, want_gw: bool = True, want_gin: bool = True,
                  stream=None):

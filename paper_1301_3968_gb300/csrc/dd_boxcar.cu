@@ -367,6 +367,44 @@ static dd_status ensure_norm_ws(dd_plan_s* p, int nw) {
     return DD_OK;
 }
 
+dd_status launch_boxcar_scratch(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
+                                const int32_t* widths, int32_t nw, const int32_t* widths_dev,
+                                const double* mean, const double* sd, double* off, float* mu,
+                                float* isd, float* peak, int32_t* arg, float thresh,
+                                dd_candidate* cands, int32_t cap, int32_t* ncands, cudaStream_t s) {
+    const size_t red = (size_t)8 * nw * sizeof(float);
+    cudaError_t e = cudaSuccess;
+    if (red > 48 * 1024) {
+        e = cudaFuncSetAttribute(k_norm, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)red);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    k_norm<<<p->ndm, 256, red, s>>>(p->dev.taps, p->unit ? nullptr : p->dev.w, p->kpad, p->nchan,
+                                    mean, sd, widths_dev, nw, p->out_int ? 1 : 0, off, mu, isd);
+    e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    BoxArgs a;
+    a.x = x;
+    a.ld = ld;
+    a.t_len = (int32_t)t_len;
+    a.ndm = p->ndm;
+    a.widths = widths_dev;
+    a.nw = nw;
+    a.off = off;
+    a.mu = mu;
+    a.isd = isd;
+    a.peak = peak;
+    a.arg = arg;
+    a.thresh = thresh;
+    a.cands = cands;
+    a.cap = cap;
+    a.ncands = ncands;
+    const int wmax = widths[nw - 1];
+    if (!p->out_int) return run_boxcar<float, float>(a, wmax, s);
+    const long long bound = (long long)wmax * p->max_abs_row;
+    if (bound < (long long)INT_MAX) return run_boxcar<int, int>(a, wmax, s);
+    return run_boxcar<int, long long>(a, wmax, s);
+}
+
 dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
                         const int32_t* widths, int32_t nw, const double* mean, const double* sd,
                         float* peak, int32_t* arg, float thresh, dd_candidate* cands, int32_t cap,

@@ -110,6 +110,11 @@ dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
                         const int32_t* widths, int32_t nw, const double* mean,
                         const double* sd, float* peak, int32_t* arg, float thresh,
                         dd_candidate* cands, int32_t cap, int32_t* ncands, cudaStream_t s);
+dd_status launch_boxcar_scratch(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
+                                const int32_t* widths, int32_t nw, const int32_t* widths_dev,
+                                const double* mean, const double* sd, double* off, float* mu,
+                                float* isd, float* peak, int32_t* arg, float thresh,
+                                dd_candidate* cands, int32_t cap, int32_t* ncands, cudaStream_t s);
 dd_status launch_backward(dd_plan_s* p, const float* in, int64_t ld, int64_t t_offset,
                           int64_t t_out, const float* g, int64_t gld, float* gw, float* gin,
                           int64_t gin_ld, cudaStream_t s);

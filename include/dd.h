@@ -196,6 +196,55 @@ dd_status dd_backward(dd_plan_t plan, const float* d_in, int64_t in_ld, int64_t 
                       int64_t nsamp, const float* d_gout, int64_t gout_ld, float* d_gw,
                       float* d_gin, int64_t gin_ld, void* stream);
 
+/* Kernel schedule of the plan: nch time chunks per CTA (the CTA sums 16/nch trials on
+ * the fp32 path, 8/nch on the exact integer path) and cs channels per pipeline stage.
+ * dd_plan_create and dd_set_profiles pick a default; dd_plan_set_schedule overrides it
+ * (DD_ERR_UNSUPPORTED if it does not fit in shared memory, the old one is then kept). */
+dd_status dd_plan_set_schedule(dd_plan_t plan, int32_t nch, int32_t cs);
+dd_status dd_plan_get_schedule(dd_plan_t plan, int32_t* nch, int32_t* cs, int32_t* trials_per_cta);
+
+/* Autotuner: times the plan's dedispersion on the given buffers (as dd_dedisperse with
+ * t_offset 0 and the band's nsamp) for each CTA shape (nch 1, 2) and stage size (fp32:
+ * 2, 3, 4, 6, 8 channels; uint8: 4, 8, 12, 16) that fits, keeps the fastest, and appends
+ * it to the text cache at cache_path (may be NULL) under a key of channel count, input
+ * type, path, and the powers of two of the trial-block delay spread and the widest tap
+ * run.  A cached key is applied without timing (*best_ms = -1).  Synchronises the
+ * stream; overwrites d_out.  Errors: DD_ERR_ARG, DD_ERR_CUDA. */
+dd_status dd_plan_autotune(dd_plan_t plan, const void* d_in, int64_t in_ld, void* d_out,
+                           int64_t out_ld, const char* cache_path, float* best_ms, void* stream);
+
+/* Many beams in one persistent launch (uneven lengths and trial lists; no counterpart in
+ * the paper, which describes one beam).  Each beam has its own plan (same input type and
+ * path for all; the plans must outlive the batch); a beam's block is the band's nsamp
+ * samples from column 0.  The work list has one item per CTA tile (beam, trial block,
+ * time tile), sorted by estimated cost, largest first; the kernel's CTAs take items
+ * from an atomic counter that each launch resets. */
+typedef struct dd_batch_s* dd_batch_t;
+dd_status dd_batch_create(dd_batch_t* batch, const dd_plan_t* plans, int32_t nbeams);
+/* Binds each beam's device input [nchan][in_ld] and output [ndm][out_ld] (host arrays of
+ * nbeams pointers / leading dimensions), uploads the plans' tables and the work list
+ * (allocates; synchronous).  Rebinding invalidates a captured graph. */
+dd_status dd_batch_bind(dd_batch_t batch, const void* const* d_in, const int64_t* in_ld,
+                        void* const* d_out, const int64_t* out_ld);
+/* The persistent dedispersion launch for all bound beams (counter reset + kernel). */
+dd_status dd_batch_dedisperse(dd_batch_t batch, void* stream);
+/* Binds, per beam, the outputs of the detection stage (boxcar widths shared by all beams;
+ * device channel mean/std [nchan], peak S/N and peak time [ndm][nw]). */
+dd_status dd_batch_bind_boxcar(dd_batch_t batch, const int32_t* widths, int32_t nw,
+                               double* const* d_mean, double* const* d_std, float* const* d_peak,
+                               int32_t* const* d_arg);
+/* One block of every beam: dd_batch_dedisperse, then (if bound) each beam's channel
+ * statistics and boxcar S/N. */
+dd_status dd_batch_run(dd_batch_t batch, void* stream);
+/* Runs dd_batch_run once eagerly (creating all workspace), then captures it on `stream`
+ * (a non-default stream) into a CUDA graph owned by the batch; dd_batch_replay launches
+ * the graph. */
+dd_status dd_batch_capture(dd_batch_t batch, void* stream);
+dd_status dd_batch_replay(dd_batch_t batch, void* stream);
+/* Work items, persistent grid size, and total trial x output samples of one block. */
+dd_status dd_batch_info(dd_batch_t batch, int32_t* nitems, int32_t* grid, int64_t* units);
+dd_status dd_batch_destroy(dd_batch_t batch);
+
 /* Device-side errors: synchronises `stream`, then returns in *code the first error a
  * kernel of this plan recorded since the last call (0 = none; DD_ERR_TIMEOUT when a
  * bounded wait on a bulk-copy barrier ran out) and clears it.  Errors: DD_ERR_ARG,

@@ -59,6 +59,18 @@ SIGNATURES = {
     "dd_boxcar_snr_noalloc": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp,
                                       c_f32, c_vp, c_i32, c_vp, c_vp]),
     "dd_backward": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp]),
+    "dd_plan_set_schedule": (c_i32, [c_vp, c_i32, c_i32]),
+    "dd_plan_get_schedule": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "dd_plan_autotune": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, ctypes.c_char_p, c_vp, c_vp]),
+    "dd_batch_create": (c_i32, [c_vp, c_vp, c_i32]),
+    "dd_batch_bind": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),
+    "dd_batch_dedisperse": (c_i32, [c_vp, c_vp]),
+    "dd_batch_bind_boxcar": (c_i32, [c_vp, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp]),
+    "dd_batch_run": (c_i32, [c_vp, c_vp]),
+    "dd_batch_capture": (c_i32, [c_vp, c_vp]),
+    "dd_batch_replay": (c_i32, [c_vp, c_vp]),
+    "dd_batch_info": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "dd_batch_destroy": (c_i32, [c_vp]),
     "dd_get_device_status": (c_i32, [c_vp, c_vp, c_vp]),
     "dd_test_set_wait": (c_i32, [c_vp, c_i32, c_i64]),
     "dd_plan_destroy": (c_i32, [c_vp]),

@@ -212,6 +212,27 @@ class Plan:
               "dd_backward")
         return gw, gin
 
+    def set_schedule(self, nch: int, cs: int) -> None:
+        check(self._lib.dd_plan_set_schedule(self._h, int(nch), int(cs)), "dd_plan_set_schedule")
+
+    def schedule(self) -> dict:
+        nch, cs, tpc = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int32()
+        check(self._lib.dd_plan_get_schedule(self._h, *(ctypes.cast(ctypes.byref(v), ctypes.c_void_p)
+                                                        for v in (nch, cs, tpc))), "dd_plan_get_schedule")
+        return dict(nch=nch.value, cs=cs.value, trials_per_cta=tpc.value)
+
+    def autotune(self, x: torch.Tensor, out: torch.Tensor, cache_path: str | None = None,
+                 stream=None) -> float:
+        """Times the CTA shapes and stage sizes that fit on (x, out) and keeps the fastest;
+        returns its time in ms (-1 when taken from the cache)."""
+        ld = self._check_input(x)
+        best = ctypes.c_float(0.0)
+        path = None if cache_path is None else cache_path.encode()
+        check(self._lib.dd_plan_autotune(self._h, _ptr(x), ld, _ptr(out), out.stride(0), path,
+                                         ctypes.cast(ctypes.byref(best), ctypes.c_void_p),
+                                         _stream(stream)), "dd_plan_autotune")
+        return best.value
+
     def device_status(self, stream=None) -> int:
         """Synchronises the stream and returns (and clears) the first device-side error
         code a kernel of this plan recorded (0 = none)."""
@@ -227,6 +248,66 @@ class Plan:
     def close(self) -> None:
         if getattr(self, "_h", None):
             self._lib.dd_plan_destroy(self._h)
+            self._h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Batch:
+    """Many beams (one plan each) dedispersed in one persistent launch; optionally the
+    beams' boxcar S/N too, and the whole block captured as a CUDA graph."""
+
+    def __init__(self, plans):
+        self._lib = _lib.load()
+        self.plans = list(plans)
+        n = len(self.plans)
+        arr = (ctypes.c_void_p * n)(*[p._h.value for p in self.plans])
+        h = ctypes.c_void_p()
+        check(self._lib.dd_batch_create(ctypes.byref(h), arr, n), "dd_batch_create")
+        self._h = h
+        self._keep = []
+
+    def bind(self, xs, outs) -> None:
+        n = len(self.plans)
+        ins = (ctypes.c_void_p * n)(*[x.data_ptr() for x in xs])
+        ild = (ctypes.c_int64 * n)(*[x.stride(0) for x in xs])
+        os_ = (ctypes.c_void_p * n)(*[o.data_ptr() for o in outs])
+        old = (ctypes.c_int64 * n)(*[o.stride(0) for o in outs])
+        check(self._lib.dd_batch_bind(self._h, ins, ild, os_, old), "dd_batch_bind")
+        self._keep = [list(xs), list(outs)]
+
+    def bind_boxcar(self, widths, means, sds, peaks, args) -> None:
+        n = len(self.plans)
+        wl = np.ascontiguousarray(widths, dtype=np.int32)
+        arrs = [(ctypes.c_void_p * n)(*[t.data_ptr() for t in ts]) for ts in (means, sds, peaks, args)]
+        check(self._lib.dd_batch_bind_boxcar(self._h, _np_ptr(wl), len(wl), *arrs), "dd_batch_bind_boxcar")
+        self._keep.append([list(means), list(sds), list(peaks), list(args), wl])
+
+    def dedisperse(self, stream=None) -> None:
+        check(self._lib.dd_batch_dedisperse(self._h, _stream(stream)), "dd_batch_dedisperse")
+
+    def run(self, stream=None) -> None:
+        check(self._lib.dd_batch_run(self._h, _stream(stream)), "dd_batch_run")
+
+    def capture(self, stream) -> None:
+        check(self._lib.dd_batch_capture(self._h, _stream(stream)), "dd_batch_capture")
+
+    def replay(self, stream=None) -> None:
+        check(self._lib.dd_batch_replay(self._h, _stream(stream)), "dd_batch_replay")
+
+    def info(self) -> dict:
+        ni, g, u = ctypes.c_int32(), ctypes.c_int32(), ctypes.c_int64()
+        check(self._lib.dd_batch_info(self._h, *(ctypes.cast(ctypes.byref(v), ctypes.c_void_p)
+                                                 for v in (ni, g, u))), "dd_batch_info")
+        return dict(items=ni.value, grid=g.value, units=u.value)
+
+    def close(self) -> None:
+        if getattr(self, "_h", None):
+            self._lib.dd_batch_destroy(self._h)
             self._h = None
 
     def __del__(self):

@@ -35,25 +35,7 @@
 namespace dd {
 namespace {
 
-struct DedispArgs {
-    const void* in;
-    int64_t ld;
-    int64_t t_offset;
-    void* out;
-    int64_t out_ld;
-    int32_t t_out;
-    const unsigned char* rec;  // [nblk][nst][rec_bytes]
-    const int32_t* blk_lo;     // [nblk][nchan]
-    int32_t nchan;
-    int32_t ndm;
-    int32_t lcap;
-    int32_t cs;   // channels per stage
-    int32_t nch;  // time chunks per CTA (trials per CTA = kWarps / nch)
-    int32_t kpad;  // weight pairs per record entry (pair path)
-    int32_t* status;
-    int32_t skip_stage;
-    int64_t wait_ns;
-};
+
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -127,12 +109,14 @@ struct Smem {
     int* issued;
 };
 
+__device__ __forceinline__ unsigned char* pipeline_area(unsigned char* smem, size_t smem_bytes, int nbuf);
+
 template <int NBUF>
-__device__ __forceinline__ Smem carve(unsigned char* smem, const StageGeom& g, int nchan) {
+__device__ __forceinline__ Smem carve(unsigned char* smem, const StageGeom& g, size_t smem_bytes) {
     Smem s;
     s.stages = smem;
     s.lo_all = (int*)(smem + NBUF * g.bytes);
-    s.full = (uint64_t*)(smem + NBUF * g.bytes + ((4 * nchan + 15) & ~15));
+    s.full = (uint64_t*)pipeline_area(smem, smem_bytes, NBUF);
     s.cnt = (int*)(s.full + NBUF);
     s.issued = s.cnt + NBUF;
     return s;
@@ -280,23 +264,33 @@ __device__ __forceinline__ void store_row(unsigned char* smem, const TACC (&acc)
     __syncwarp();
 }
 
-template <typename TIN, bool PAIR, int NBUF>
-__global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
+// Per-CTA pipeline state kept in shared memory across tiles (the batched kernel runs
+// many tiles per CTA): uses[b] counts completed uses of buffer b, which fixes the
+// parity of the barrier phase that the next use waits for.
+struct TileState {
+    int uses[kStagesMax];
+};
+
+// One CTA tile: trial block `blk`, time tile `tx` of the plan described by `a`.
+// Returns false (on every thread) if a bounded wait ran out.
+// `a` is taken by value: with a reference to the kernel parameter the compiler picked
+// a register allocation for the FMA loop that ran 11 % slower.
+template <typename TIN, bool PAIR, int NBUF, bool MULTI>
+__device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* smem, int blk,
+                                            int tx, TileState& ts) {
     constexpr int R = kR;
     constexpr int Q = Elem<TIN>::Q;
     constexpr int TPW = PAIR ? 2 : 1;   // trials per warp unit
     using TACC = typename std::conditional<PAIR, float, int>::type;
-    extern __shared__ __align__(128) unsigned char smem[];
     const int cs = a.cs;
     const int nu = kWarps / a.nch;     // warp units per CTA
     const StageGeom g((int)sizeof(TIN), PAIR, a.lcap, a.kpad, cs, nu);
-    const Smem sm = carve<NBUF>(smem, g, a.nchan);
+    const Smem sm = carve<NBUF>(smem, g, a.smem_bytes);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int blk = blockIdx.y;
     const int dmi = warp / a.nch, chunk = warp - dmi * a.nch;
     const int d = blk * (TPW * nu) + dmi * TPW;               // first trial of the unit
-    const int64_t t0 = (int64_t)blockIdx.x * kTileT * a.nch;  // CTA time start
+    const int64_t t0 = (int64_t)tx * kTileT * a.nch;          // CTA time start
     const int64_t tw = t0 + (int64_t)chunk * kTileT;           // warp time start
     const int64_t base = a.t_offset + t0;
     const int nst = (a.nchan + cs - 1) / cs;
@@ -309,15 +303,6 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
         past_end |= (((base + lo) & ~(int64_t)(Q - 1)) + a.lcap > a.ld) ? 1 : 0;
     }
     const bool tail = __syncthreads_or(past_end) != 0;
-    if (tid == 0) {
-        for (int b = 0; b < NBUF; ++b) {
-            mbar_init(&sm.full[b], 1);
-            sm.cnt[b] = 0;
-            sm.issued[b] = 0;
-        }
-        fence_mbar_init();
-    }
-    __syncthreads();
     if (tid == 0)
         for (int s = 0; s < NBUF && s < nst; ++s) issue_stage<TIN, NBUF>(a, g, sm, blk, s, s, base, tail);
 
@@ -333,7 +318,9 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
 
     for (int s = 0; s < nst; ++s) {
         const int b = s % NBUF;
-        const bool got = mbar_wait_bounded(&sm.full[b], (uint32_t)((s / NBUF) & 1), a.wait_ns);
+        // a one-tile CTA starts every buffer at phase 0; a persistent CTA continues
+        const uint32_t parity = (uint32_t)(((MULTI ? ts.uses[b] : 0) + s / NBUF) & 1);
+        const bool got = mbar_wait_bounded(&sm.full[b], parity, a.wait_ns);
         if (!__all_sync(0xffffffffu, got)) {
             if (lane == 0) atomicExch(a.status, (int)DD_ERR_TIMEOUT);
             ok = false;
@@ -368,13 +355,15 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
     }
 
     __syncthreads();
-    if (tid == 0) {  // no copy may still be in flight when the CTA leaves
+    if (!ok && tid == 0) {  // no copy may still be in flight when the CTA leaves
         for (int b = 0; b < NBUF; ++b)
             if (sm.issued[b] > 0 &&
                 !mbar_wait_bounded(&sm.full[b], (uint32_t)((sm.issued[b] - 1) & 1), a.wait_ns))
                 atomicExch(a.status, (int)DD_ERR_TIMEOUT);
     }
-    if (!__syncthreads_and(ok)) return;
+    if (!__syncthreads_and(ok)) return false;
+    if (MULTI && tid == 0)
+        for (int b = 0; b < NBUF && b < nst; ++b) ts.uses[b] += (nst - b + NBUF - 1) / NBUF;
 
     // transpose through shared memory and store coalesced, one trial row at a time
     TACC* out = (TACC*)a.out;
@@ -382,15 +371,85 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
     if constexpr (PAIR)
         store_row<float>(smem, acc1, warp, lane, tw, a.t_out,
                          d + 1 < a.ndm ? (float*)a.out + (int64_t)(d + 1) * a.out_ld : nullptr);
+    if (MULTI) __syncthreads();  // the staging area is the next tile's stage buffers
+    return true;
+}
+
+template <int NBUF>
+__device__ __forceinline__ void init_pipeline(unsigned char* smem_tail_full, TileState& ts) {
+    uint64_t* full = (uint64_t*)smem_tail_full;
+    int* cnt = (int*)(full + NBUF);
+    int* issued = cnt + NBUF;
+    for (int b = 0; b < NBUF; ++b) {
+        mbar_init(&full[b], 1);
+        cnt[b] = 0;
+        issued[b] = 0;
+        ts.uses[b] = 0;
+    }
+    fence_mbar_init();
+}
+
+// Barriers and counters sit after the stage buffers and the per-channel minima; their
+// offset depends on the plan's geometry, so the kernels place them at a fixed offset
+// from the end of the dynamic shared memory instead.
+__device__ __forceinline__ unsigned char* pipeline_area(unsigned char* smem, size_t smem_bytes, int nbuf) {
+    return smem + smem_bytes - (size_t)(nbuf * 8 + 2 * nbuf * 4);
 }
 
 template <typename TIN, bool PAIR, int NBUF>
-dd_status run(const DedispArgs& a, cudaStream_t s) {
+__global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ TileState ts;
+    if (threadIdx.x == 0) init_pipeline<NBUF>(pipeline_area(smem, a.smem_bytes, NBUF), ts);
+    __syncthreads();
+    dedisp_tile<TIN, PAIR, NBUF, false>(a, smem, blockIdx.y, blockIdx.x, ts);
+}
+
+// Persistent form: each CTA takes work items (beam, trial block, time tile) from an
+// atomic counter until none remain.  Items are sorted by estimated cost, largest
+// first, so the uneven beams finish together.  The counter is reset before each launch.
+template <typename TIN, bool PAIR, int NBUF>
+__global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_batched(const DedispArgs* beams,
+                                                                    const BatchItem* items,
+                                                                    int32_t nitems, int32_t* counter,
+                                                                    uint32_t smem_bytes) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ TileState ts;
+    __shared__ DedispArgs sa;
+    __shared__ int s_item;
+    if (threadIdx.x == 0) init_pipeline<NBUF>(pipeline_area(smem, smem_bytes, NBUF), ts);
+    for (;;) {
+        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
+        __syncthreads();
+        const int item = s_item;
+        if (item >= nitems) break;
+        const BatchItem it = items[item];
+        if (threadIdx.x == 0) {
+            sa = beams[it.beam];
+            sa.smem_bytes = smem_bytes;
+        }
+        __syncthreads();
+        if (!dedisp_tile<TIN, PAIR, NBUF, true>(sa, smem, it.blk, it.tx, ts)) break;
+    }
+}
+
+// Dynamic shared memory of a launch: the plan's stages, per-channel minima and
+// barriers, and at least the output transpose area plus the barriers (which sit at the
+// end and survive the transpose).
+template <typename TIN, bool PAIR, int NBUF>
+size_t smem_for(int lcap, int kpad, int cs, int nch, int nchan) {
+    const StageGeom g((int)sizeof(TIN), PAIR, lcap, kpad, cs, kWarps / nch);
+    size_t smem = (size_t)dedisp_smem_bytes(g, NBUF, nchan);
+    const size_t st = (size_t)kStoreBytes + NBUF * 8 + 2 * NBUF * 4;
+    if (smem < st) smem = st;
+    return (smem + 15) & ~(size_t)15;
+}
+
+template <typename TIN, bool PAIR, int NBUF>
+dd_status run(DedispArgs a, cudaStream_t s) {
     const int nu = kWarps / a.nch;
-    const StageGeom g((int)sizeof(TIN), PAIR, a.lcap, a.kpad, a.cs, nu);
-    size_t smem = (size_t)dedisp_smem_bytes(g, NBUF, a.nchan);
-    const size_t st_bytes = (size_t)kWarps * 32 * kR * 4;
-    if (smem < st_bytes) smem = st_bytes;
+    const size_t smem = smem_for<TIN, PAIR, NBUF>(a.lcap, a.kpad, a.cs, a.nch, a.nchan);
+    a.smem_bytes = (uint32_t)smem;
     auto kern = k_dedisp<TIN, PAIR, NBUF>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
@@ -400,6 +459,28 @@ dd_status run(const DedispArgs& a, cudaStream_t s) {
     if (grid.y > 65535) return DD_ERR_UNSUPPORTED;
     kern<<<grid, kWarps * 32, smem, s>>>(a);
     return cuda_status(cudaGetLastError());
+}
+
+template <typename TIN, bool PAIR, int NBUF>
+dd_status run_batched(const DedispArgs* d_args, const BatchItem* d_items, int32_t nitems,
+                      int32_t* d_counter, size_t smem, int grid, cudaStream_t s) {
+    auto kern = k_dedisp_batched<TIN, PAIR, NBUF>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    e = cudaMemsetAsync(d_counter, 0, sizeof(int32_t), s);
+    if (e != cudaSuccess) return cuda_status(e);
+    kern<<<grid, kWarps * 32, smem, s>>>(d_args, d_items, nitems, d_counter, (uint32_t)smem);
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename TIN, bool PAIR, int NBUF>
+int blocks_per_sm(size_t smem) {
+    int n = 0;
+    auto kern = k_dedisp_batched<TIN, PAIR, NBUF>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kWarps * 32, smem) != cudaSuccess) return 0;
+    return n;
 }
 
 // Builds the pair records' (w0, w1) weights from the device weights [d][c][kpad] and
@@ -448,30 +529,57 @@ dd_status launch_repack(dd_plan_s* p, cudaStream_t s) {
     return cuda_status(cudaGetLastError());
 }
 
+void fill_dedisp_args(const dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
+                      int64_t t_out, void* out, int64_t out_ld, DedispArgs* a) {
+    a->in = in;
+    a->ld = ld;
+    a->t_offset = t_offset;
+    a->out = out;
+    a->out_ld = out_ld;
+    a->t_out = (int32_t)t_out;
+    a->rec = p->dev.rec;
+    a->blk_lo = p->dev.blk_lo;
+    a->nchan = p->nchan;
+    a->ndm = p->ndm;
+    a->lcap = p->lcap;
+    a->cs = p->cs;
+    a->nch = p->nch;
+    a->kpad = p->pair ? p->kw : 0;
+    a->status = p->dev.status;
+    a->skip_stage = p->debug_skip_stage;
+    a->wait_ns = p->wait_ns;
+    a->smem_bytes = (uint32_t)dedisp_smem_for(p);
+}
+
+size_t dedisp_smem_for(const dd_plan_s* p) {
+    const int kp = p->pair ? p->kw : 0;
+    if (!p->pair) return smem_for<uint8_t, false, kStages>(p->lcap, kp, p->cs, p->nch, p->nchan);
+    if (p->band.in_type == DD_U8) return smem_for<uint8_t, true, kStages>(p->lcap, kp, p->cs, p->nch, p->nchan);
+    return smem_for<float, true, kStages>(p->lcap, kp, p->cs, p->nch, p->nchan);
+}
+
 dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
                             int64_t t_out, void* out, int64_t out_ld, cudaStream_t s) {
     DedispArgs a;
-    a.in = in;
-    a.ld = ld;
-    a.t_offset = t_offset;
-    a.out = out;
-    a.out_ld = out_ld;
-    a.t_out = (int32_t)t_out;
-    a.rec = p->dev.rec;
-    a.blk_lo = p->dev.blk_lo;
-    a.nchan = p->nchan;
-    a.ndm = p->ndm;
-    a.lcap = p->lcap;
-    a.cs = p->cs;
-    a.nch = p->nch;
-    a.kpad = p->pair ? p->kw : 0;
-    a.status = p->dev.status;
-    a.skip_stage = p->debug_skip_stage;
-    a.wait_ns = p->wait_ns;
+    fill_dedisp_args(p, in, ld, t_offset, t_out, out, out_ld, &a);
     const bool u8 = p->band.in_type == DD_U8;
     if (!p->pair) return run<uint8_t, false, kStages>(a, s);
     if (u8) return run<uint8_t, true, kStages>(a, s);
     return run<float, true, kStages>(a, s);
+}
+
+dd_status launch_dedisperse_batched(bool u8, bool pair, const DedispArgs* d_args,
+                                    const BatchItem* d_items, int32_t nitems, int32_t* d_counter,
+                                    size_t smem, int grid, cudaStream_t s) {
+    if (!pair) return run_batched<uint8_t, false, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
+    if (u8) return run_batched<uint8_t, true, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
+    return run_batched<float, true, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
+}
+
+int dedisp_batched_blocks_per_sm(bool u8, bool pair, size_t smem) {
+    if (!pair) return blocks_per_sm<uint8_t, false, kStages>(smem);
+    if (u8) return blocks_per_sm<uint8_t, true, kStages>(smem);
+    return blocks_per_sm<float, true, kStages>(smem);
 }
 
 }  // namespace dd

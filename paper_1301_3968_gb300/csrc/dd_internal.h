@@ -18,6 +18,7 @@ constexpr int kWarps = 8;
 constexpr int kR = 31;
 constexpr int kTileT = 32 * kR;
 constexpr int kStages = 4;                 // bulk-copy pipeline depth
+constexpr int kStagesMax = 8;
 constexpr int kSmemBudget = 110 * 1024;    // dynamic shared memory per CTA (two per SM)
 constexpr int kSmemBudgetOne = 220 * 1024; // fallback: one CTA per SM
 constexpr long long kWaitNs = 2000000000;  // bound on any device-side barrier wait
@@ -45,6 +46,39 @@ struct StageGeom {
 __host__ __device__ inline int dedisp_smem_bytes(const StageGeom& g, int nbuf, int nchan) {
     return nbuf * g.bytes + ((4 * nchan + 15) & ~15) + nbuf * 8 + 2 * nbuf * 4;
 }
+// The output transpose reuses the stage buffers: one row of 32 * kR values per warp.
+constexpr int kStoreBytes = kWarps * 32 * kR * 4;
+
+// Arguments of one dedispersion launch (one plan, one input block); the batched
+// kernel keeps one per beam in device memory.
+struct DedispArgs {
+    const void* in;
+    int64_t ld;
+    int64_t t_offset;
+    void* out;
+    int64_t out_ld;
+    int32_t t_out;
+    const unsigned char* rec;  // [nblk][nst][rec_bytes]
+    const int32_t* blk_lo;     // [nblk][nchan]
+    int32_t nchan;
+    int32_t ndm;
+    int32_t lcap;
+    int32_t cs;   // channels per stage
+    int32_t nch;  // time chunks per CTA (trials per CTA = kWarps / nch)
+    int32_t kpad;  // weight pairs per record entry (pair path)
+    int32_t* status;
+    int32_t skip_stage;
+    int64_t wait_ns;
+    uint32_t smem_bytes;  // dynamic shared memory of the launch
+};
+
+// One work item of the batched dedispersion kernel: a CTA tile of one beam.
+struct BatchItem {
+    int32_t beam;
+    int32_t blk;   // trial block
+    int32_t tx;    // time tile
+    int32_t pad;
+};
 
 struct DevTables {
     int device = -1;
@@ -99,6 +133,13 @@ namespace dd {
 
 dd_status upload_tables(dd_plan_s* p);  // (re)creates the device tables if dirty
 dd_status launch_repack(dd_plan_s* p, cudaStream_t s);  // dev.w -> records' weights
+void fill_dedisp_args(const dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
+                      int64_t t_out, void* out, int64_t out_ld, DedispArgs* a);
+size_t dedisp_smem_for(const dd_plan_s* p);
+dd_status launch_dedisperse_batched(bool u8, bool pair, const DedispArgs* d_args,
+                                    const BatchItem* d_items, int32_t nitems, int32_t* d_counter,
+                                    size_t smem, int grid, cudaStream_t s);
+int dedisp_batched_blocks_per_sm(bool u8, bool pair, size_t smem);
 dd_status cuda_status(cudaError_t e);
 
 // launchers (stream = cudaStream_t)

@@ -4,7 +4,12 @@
 #include <algorithm>
 #include <cmath>
 #include <cstring>
+#include <fstream>
+#include <map>
+#include <mutex>
 #include <new>
+#include <sstream>
+#include <string>
 
 #include "dd_internal.h"
 
@@ -181,6 +186,33 @@ dd_status build_schedule(dd_plan_s* p) {
         }
     }
     return DD_ERR_UNSUPPORTED;
+}
+
+// Fixed CTA shape (nch time chunks) and stage size (cs channels), if it fits.
+dd_status build_schedule_fixed(dd_plan_s* p, int nch, int cs) {
+    if (nch < 1 || nch > dd::kWarps || (dd::kWarps % nch) != 0 || cs < 1 || cs > 32) return DD_ERR_ARG;
+    const bool u8 = p->band.in_type == DD_U8;
+    const int64_t q = u8 ? 16 : 4;
+    const int esz = u8 ? 1 : 4;
+    const int nu = dd::kWarps / nch;
+    const int db = trials_per_unit(p) * nu;
+    const int64_t span = block_span(p, db, nullptr);
+    const int32_t kw = p->pair ? ((union_taps(p, db) + 1) & ~1) : 0;
+    int64_t need = (int64_t)nch * dd::kTileT + span + q + 2;
+    need = (need + q - 1) / q * q;
+    if (need > (1 << 22)) return DD_ERR_UNSUPPORTED;
+    if (dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu), dd::kStages,
+                              p->nchan) > dd::kSmemBudgetOne)
+        return DD_ERR_UNSUPPORTED;
+    p->nch = nch;
+    p->cs = cs;
+    p->kw = kw;
+    p->lcap = (int32_t)need;
+    p->nblk = (p->ndm + db - 1) / db;
+    block_span(p, db, &p->blk_lo);
+    build_records(p);
+    p->dev_dirty = true;
+    return DD_OK;
 }
 
 dd_status finish_profiles(dd_plan_s* p) {
@@ -516,6 +548,117 @@ dd_status dd_backward(dd_plan_t p, const float* in, int64_t in_ld, int64_t t_off
     if (st != DD_OK) return st;
     return dd::launch_backward(p, in, in_ld, t_offset, t_out, g, gld, gw, gin, gin_ld,
                                (cudaStream_t)stream);
+}
+
+dd_status dd_plan_set_schedule(dd_plan_t p, int32_t nch, int32_t cs) {
+    if (!p) return DD_ERR_ARG;
+    const int old_nch = p->nch, old_cs = p->cs;
+    dd_status st = build_schedule_fixed(p, nch, cs);
+    if (st != DD_OK && (p->nch != old_nch || p->cs != old_cs)) build_schedule_fixed(p, old_nch, old_cs);
+    return st;
+}
+
+dd_status dd_plan_get_schedule(dd_plan_t p, int32_t* nch, int32_t* cs, int32_t* trials_per_cta) {
+    if (!p) return DD_ERR_ARG;
+    if (nch) *nch = p->nch;
+    if (cs) *cs = p->cs;
+    if (trials_per_cta) *trials_per_cta = (p->pair ? 2 : 1) * dd::kWarps / p->nch;
+    return DD_OK;
+}
+
+namespace {
+
+std::mutex g_tune_mu;
+
+// Schedule cache key: channel count, input type, path, and the trial-block delay
+// spread and widest tap run in powers of two -- the quantities that decide which CTA
+// shape and stage size fit and run best.
+std::string tune_key(const dd_plan_s* p) {
+    const int64_t span8 = block_span(p, 8, nullptr);
+    const int sb = (int)std::floor(std::log2((double)span8 + 1.0));
+    const int kb = (int)std::floor(std::log2((double)p->kmax + 1.0));
+    std::ostringstream o;
+    o << "C" << p->nchan << "_" << (p->band.in_type == DD_U8 ? "u8" : "f32") << "_"
+      << (p->pair ? "pair" : "int") << "_s" << sb << "_k" << kb;
+    return o.str();
+}
+
+std::map<std::string, std::pair<int, int>> read_cache(const char* path) {
+    std::map<std::string, std::pair<int, int>> m;
+    if (!path) return m;
+    std::ifstream f(path);
+    std::string key;
+    int nch, cs;
+    double ms;
+    while (f >> key >> nch >> cs >> ms) m[key] = {nch, cs};
+    return m;
+}
+
+}  // namespace
+
+dd_status dd_plan_autotune(dd_plan_t p, const void* d_in, int64_t in_ld, void* d_out,
+                           int64_t out_ld, const char* cache_path, float* best_ms, void* stream) {
+    if (!p || !d_in || !d_out) return DD_ERR_ARG;
+    cudaStream_t s = (cudaStream_t)stream;
+    const std::string key = tune_key(p);
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    auto cache = read_cache(cache_path);
+    auto hit = cache.find(key);
+    if (hit != cache.end() && dd_plan_set_schedule(p, hit->second.first, hit->second.second) == DD_OK) {
+        if (best_ms) *best_ms = -1.0f;
+        return DD_OK;
+    }
+    const bool u8 = p->band.in_type == DD_U8;
+    const int cs_list_f[] = {2, 3, 4, 6, 8};
+    const int cs_list_u[] = {4, 8, 12, 16};
+    const int* cs_list = u8 ? cs_list_u : cs_list_f;
+    const int ncs = u8 ? 4 : 5;
+    const int orig_nch = p->nch, orig_cs = p->cs;
+    int best_nch = orig_nch, best_cs = orig_cs;
+    float best = 1e30f;
+    cudaEvent_t e0 = nullptr, e1 = nullptr;
+    cudaError_t ce = cudaEventCreate(&e0);
+    if (ce == cudaSuccess) ce = cudaEventCreate(&e1);
+    if (ce != cudaSuccess) return dd::cuda_status(ce);
+    dd_status st = DD_OK;
+    for (int nch = 1; nch <= 2 && st == DD_OK; nch *= 2) {
+        for (int i = 0; i < ncs; ++i) {
+            if (build_schedule_fixed(p, nch, cs_list[i]) != DD_OK) continue;
+            st = dd_dedisperse(p, d_in, in_ld, 0, p->band.nsamp, d_out, out_ld, stream);
+            if (st != DD_OK) break;
+            float t = 1e30f;
+            for (int rep = 0; rep < 2; ++rep) {
+                cudaEventRecord(e0, s);
+                st = dd_dedisperse(p, d_in, in_ld, 0, p->band.nsamp, d_out, out_ld, stream);
+                cudaEventRecord(e1, s);
+                if (st != DD_OK) break;
+                ce = cudaEventSynchronize(e1);
+                if (ce != cudaSuccess) {
+                    st = dd::cuda_status(ce);
+                    break;
+                }
+                float ms = 0.f;
+                cudaEventElapsedTime(&ms, e0, e1);
+                t = std::min(t, ms);
+            }
+            if (st != DD_OK) break;
+            if (t < best) {
+                best = t;
+                best_nch = nch;
+                best_cs = cs_list[i];
+            }
+        }
+    }
+    cudaEventDestroy(e0);
+    cudaEventDestroy(e1);
+    if (build_schedule_fixed(p, best_nch, best_cs) != DD_OK) build_schedule_fixed(p, orig_nch, orig_cs);
+    if (st != DD_OK) return st;
+    if (best_ms) *best_ms = best;
+    if (cache_path) {
+        std::ofstream f(cache_path, std::ios::app);
+        if (f) f << key << " " << best_nch << " " << best_cs << " " << best << "\n";
+    }
+    return DD_OK;
 }
 
 dd_status dd_get_device_status(dd_plan_t p, int32_t* code, void* stream) {

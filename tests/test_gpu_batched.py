@@ -1,0 +1,125 @@
+"""Batched beams, CUDA graph replay and the schedule autotuner against per-beam launches
+and the oracle."""
+import os
+import tempfile
+
+import numpy as np
+import pytest
+
+import oracle
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dd():
+    import torch
+    from paper_1301_3968_gb300 import build
+    build.build()
+    import paper_1301_3968_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+def _beams(dd, n=6, seed=31):
+    """Small uneven beams on the CRAFT band (the batched configuration at reduced size)."""
+    import torch
+    rng = np.random.default_rng(seed)
+    b = synth.CRAFT_BAND
+    out = []
+    for i in range(n):
+        T = int(round(2 ** rng.uniform(12, 13.5)))
+        D = int(round(2 ** rng.uniform(5, 8)))
+        dm_max = float(np.exp(rng.uniform(np.log(100.0), np.log(600.0))))
+        band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, T, "u8")
+        dms, _ = dd.trial_dms(band, 0.0, dm_max, D, tau_av_ms=1.0)
+        plan = dd.Plan(band, dms)
+        beam = dict(nsamp=T, ndm=D, dm_max=dm_max, seed=1000 + i)
+        data = synth.make_beam_data(beam)
+        x = torch.from_numpy(data).cuda()
+        outb = torch.zeros((D, T - plan.d_max), dtype=torch.int32, device="cuda")
+        out.append((plan, x, outb, data))
+    return out
+
+
+def test_batched_equals_per_beam_and_oracle(dd):
+    import torch
+    beams = _beams(dd)
+    batch = dd.Batch([p for p, _, _, _ in beams])
+    batch.bind([x for _, x, _, _ in beams], [o for _, _, o, _ in beams])
+    batch.dedisperse()
+    torch.cuda.synchronize()
+    info = batch.info()
+    assert info["items"] > 0 and info["grid"] > 0
+    for plan, x, o, data in beams:
+        ref = plan.dedisperse(x, nsamp=plan.band.nsamp)
+        np.testing.assert_array_equal(o.cpu().numpy(), ref.cpu().numpy())
+        delay, taps = plan.tables()
+        rows = [0, plan.ndm // 2, plan.ndm - 1]
+        want = oracle.c_dedisperse(data, delay, taps, nsamp=plan.band.nsamp, rows=rows)
+        np.testing.assert_array_equal(o.cpu().numpy()[rows].astype(np.int64), want)
+    # a second launch (the work counter is reset) gives the same result
+    before = [o.clone() for _, _, o, _ in beams]
+    for _, _, o, _ in beams:
+        o.zero_()
+    batch.dedisperse()
+    torch.cuda.synchronize()
+    for b_, (_, _, o, _) in zip(before, beams):
+        assert torch.equal(b_, o)
+
+
+def test_graph_replay_equals_eager(dd):
+    import torch
+    beams = _beams(dd, n=4, seed=32)
+    batch = dd.Batch([p for p, _, _, _ in beams])
+    batch.bind([x for _, x, _, _ in beams], [o for _, _, o, _ in beams])
+    widths = np.arange(1, 17, dtype=np.int32)
+    means = [torch.empty(p.band.nchan, dtype=torch.float64, device="cuda") for p, _, _, _ in beams]
+    sds = [torch.empty_like(m) for m in means]
+    peaks = [torch.empty((p.ndm, 16), dtype=torch.float32, device="cuda") for p, _, _, _ in beams]
+    args = [torch.empty((p.ndm, 16), dtype=torch.int32, device="cuda") for p, _, _, _ in beams]
+    batch.bind_boxcar(widths, means, sds, peaks, args)
+    batch.run()
+    torch.cuda.synchronize()
+    eager = [(o.clone(), pk.clone(), a.clone()) for (_, _, o, _), pk, a in zip(beams, peaks, args)]
+    s = torch.cuda.Stream()
+    batch.capture(s)
+    for (_, _, o, _), pk, a in zip(beams, peaks, args):
+        o.zero_()
+        pk.zero_()
+        a.zero_()
+    torch.cuda.synchronize()
+    batch.replay(s)
+    s.synchronize()
+    for (o0, p0, a0), (_, _, o, _), pk, a in zip(eager, beams, peaks, args):
+        assert torch.equal(o0, o) and torch.equal(p0, pk) and torch.equal(a0, a)
+    # each beam's boxcar matches its own single-plan call
+    for (plan, x, o, _), pk, a in zip(beams, peaks, args):
+        m, sd = plan.channel_stats(x, nsamp=plan.band.nsamp)
+        p1, a1, _ = plan.boxcar_snr(o, widths, m, sd)
+        assert torch.equal(p1, pk) and torch.equal(a1, a)
+
+
+def test_autotune_keeps_results_and_uses_cache(dd):
+    import torch
+    cfg = synth.make_craft(nsamp=8192, npulse=2)
+    b = cfg["band"]
+    band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, 8192, "f32")
+    dms, _ = dd.trial_dms(band, 0.0, 1000.0, 128, tau_av_ms=1.0)
+    plan = dd.Plan(band, dms)
+    x = torch.from_numpy(cfg["data"]).cuda()
+    ref = plan.dedisperse(x, nsamp=8192).clone()
+    out = torch.empty_like(ref)
+    with tempfile.TemporaryDirectory() as tmp:
+        path = os.path.join(tmp, "tune.txt")
+        ms = plan.autotune(x, out, cache_path=path)
+        assert ms > 0 and os.path.exists(path)
+        sched = plan.schedule()
+        got = plan.dedisperse(x, nsamp=8192)
+        # fp32 sums in another stage grouping may round differently only by reassociation
+        # across stage boundaries -- none here: the channel order is fixed, so identical
+        assert torch.equal(got, ref)
+        plan2 = dd.Plan(band, dms)
+        assert plan2.autotune(x, out, cache_path=path) == -1.0
+        assert plan2.schedule() == sched

@@ -4,10 +4,16 @@
 //   gw[d][c][k] = sum_t g[d][t] * I[c][t_offset + t + delta_dc + k]          (k < n_dc)
 //   gI[c][tau]  = sum_d sum_{k < n_dc} w_dck * g[d][tau - t_offset - delta_dc - k]
 //
-// k_bwd_w: one CTA per (trial, channel); threads stride over t with a register
-// accumulator per tap (32 taps per pass), then a fixed-order CTA reduction.
-// k_bwd_in: one thread per input column; the sum runs over trials, then taps, in
-// ascending order, as a gather (no atomics), so it is deterministic.
+// gI is itself a dedispersion with rows and columns swapped (see build_adjoint_plan):
+// the output gradient is copied into a zero-padded buffer (k_pad_rows), the forward
+// weights are transposed and reversed into the adjoint plan (k_transpose_w, then the
+// adjoint plan's record repack), and the forward dedispersion kernel runs on it.
+//
+// gw is a correlation of each trial's gradient row with the shifted channel row, for
+// the tap lags k: k_bwd_w gives each warp one (trial, channel) pair and its 32 lags in
+// registers; lanes own 33 consecutive samples (odd, so lane-strided shared loads are
+// conflict free) and slide a 32-sample register window along them; the lanes' partial
+// sums are added in a fixed order at the end.  Both paths are deterministic.
 #include <cstdint>
 
 #include "dd_internal.h"
@@ -15,71 +21,112 @@
 namespace dd {
 namespace {
 
-constexpr int kKc = 32;
+constexpr int kLags = 32;          // lags per pass of k_bwd_w
+constexpr int kSeg = 33;           // samples per lane per tile
+constexpr int kTileW = 32 * kSeg;  // samples per tile
 
-__global__ void __launch_bounds__(256) k_bwd_w(const float* in, int64_t ld, int64_t t_offset,
-                                               int32_t t_out, const float* g, int64_t gld,
-                                               const int32_t* delay, const int32_t* taps,
-                                               int32_t nchan, int32_t kpad, int32_t kout, float* gw) {
-    const int c = blockIdx.x, d = blockIdx.y;
-    const int64_t dc = (int64_t)d * nchan + c;
-    const int n = taps[dc];
-    const float* src = in + (int64_t)c * ld + t_offset + delay[dc];
-    const float* gd = g + (int64_t)d * gld;
-    __shared__ float red[8][kKc];
-    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
-    for (int kc = 0; kc < kpad; kc += kKc) {
-        float acc[kKc];
-#pragma unroll
-        for (int k = 0; k < kKc; ++k) acc[k] = 0.f;
-        const int kn = min(kKc, n - kc);
-        if (kn > 0) {
-            for (int t = threadIdx.x; t < t_out; t += blockDim.x) {
-                const float gv = gd[t];
-                const float* s = src + t + kc;
-#pragma unroll
-                for (int k = 0; k < kKc; ++k)
-                    if (k < kn) acc[k] = fmaf(gv, s[k], acc[k]);
-            }
-        }
-#pragma unroll
-        for (int k = 0; k < kKc; ++k) {
-            float v = acc[k];
-#pragma unroll
-            for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
-            if (lane == 0) red[warp][k] = v;
-        }
-        __syncthreads();
-        if (threadIdx.x < kKc && kc + (int)threadIdx.x < kout) {
-            float v = 0.f;
-            for (int i = 0; i < 8; ++i) v += red[i][threadIdx.x];
-            gw[dc * kout + kc + threadIdx.x] = (kc + (int)threadIdx.x < n) ? v : 0.f;
-        }
-        __syncthreads();
+__global__ void k_pad_rows(const float* g, int64_t gld, int32_t t_out, int32_t pad, float* gp,
+                           int64_t gpld, int32_t rows) {
+    const int d = blockIdx.y;
+    if (d >= rows) return;
+    for (int64_t v = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; v < gpld; v += (int64_t)gridDim.x * blockDim.x) {
+        const int64_t u = v - pad;
+        gp[(int64_t)d * gpld + v] = (u >= 0 && u < t_out) ? g[(int64_t)d * gld + u] : 0.f;
     }
 }
 
-__global__ void __launch_bounds__(256) k_bwd_in(int64_t nsamp, int32_t t_out, const float* g,
-                                                int64_t gld, const int32_t* delay,
-                                                const int32_t* taps, const float* w, int32_t kpad,
-                                                int32_t nchan, int32_t ndm, float* gin,
-                                                int64_t gin_ld, int64_t t_offset) {
+// Wt[c][d][j] = w[d][c][n_dc - 1 - j] for j < n_dc, zero beyond.
+__global__ void k_transpose_w(const float* w, const int32_t* taps, int32_t ndm, int32_t nchan,
+                              int32_t kpad, float* wt) {
+    const int64_t n = (int64_t)ndm * nchan;
+    for (int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; i < n; i += (int64_t)gridDim.x * blockDim.x) {
+        const int d = (int)(i / nchan), c = (int)(i - (int64_t)d * nchan);
+        const int nt = taps[i];
+        const float* src = w + i * kpad;
+        float* dst = wt + ((int64_t)c * ndm + d) * kpad;
+        for (int j = 0; j < kpad; ++j) dst[j] = j < nt ? src[nt - 1 - j] : 0.f;
+    }
+}
+
+__device__ __forceinline__ float warp_sum(float v) {
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_xor_sync(0xffffffffu, v, o);
+    return v;
+}
+
+// grid (trial blocks of 8, channels).  Shared memory: the channel's window for the
+// block's 8 trials and the 8 gradient rows of the current tile.
+__global__ void __launch_bounds__(256) k_bwd_w(const float* in, int64_t ld, int64_t t_offset,
+                                               int32_t t_out, const float* g, int64_t gld,
+                                               const int32_t* delay, const int32_t* taps,
+                                               int32_t nchan, int32_t ndm, int32_t kpad,
+                                               int32_t kout, int32_t span, float* gw) {
+    extern __shared__ float sm[];
+    const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31;
     const int c = blockIdx.y;
-    const int64_t tau = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
-    if (tau >= nsamp) return;
-    float acc = 0.f;
-    for (int d = 0; d < ndm; ++d) {
-        const int64_t dc = (int64_t)d * nchan + c;
-        const int n = taps[dc];
-        const int64_t base = tau - delay[dc];
-        const float* gd = g + (int64_t)d * gld;
-        const float* wk = w + dc * kpad;
-        for (int k = 0; k < n; ++k) {
-            const int64_t t = base - k;
-            if (t >= 0 && t < t_out) acc = fmaf(wk[k], gd[t], acc);
+    const int d = blockIdx.x * 8 + warp;
+    const int xlen = kTileW + span + kpad + 1;
+    float* xs = sm;                       // [xlen]
+    float* gs = sm + ((xlen + 3) & ~3);   // [8][kTileW]
+    __shared__ int s_lo;
+    __shared__ int s_del[8], s_tap[8];
+    if (threadIdx.x < 8) {
+        const int dd = blockIdx.x * 8 + threadIdx.x;
+        s_del[threadIdx.x] = dd < ndm ? delay[(int64_t)dd * nchan + c] : INT32_MAX;
+        s_tap[threadIdx.x] = dd < ndm ? taps[(int64_t)dd * nchan + c] : 0;
+    }
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        int lo = INT32_MAX;
+        for (int i = 0; i < 8; ++i) lo = min(lo, s_del[i]);
+        s_lo = lo;
+    }
+    __syncthreads();
+    const int lo = s_lo;
+    const bool active = d < ndm;
+    const int off = active ? s_del[warp] - lo : 0;
+    const int n = active ? s_tap[warp] : 0;
+    const float* row = in + (int64_t)c * ld + t_offset + lo;
+    const int64_t row_end = ld - t_offset - lo;  // columns available in the row
+    for (int kc = 0; kc < kout; kc += kLags) {
+        float acc[kLags];
+#pragma unroll
+        for (int k = 0; k < kLags; ++k) acc[k] = 0.f;
+        for (int t0 = 0; t0 < t_out; t0 += kTileW) {
+            __syncthreads();
+            for (int i = threadIdx.x; i < xlen; i += blockDim.x) {
+                const int64_t col = (int64_t)t0 + i;
+                xs[i] = col < row_end ? row[col] : 0.f;
+            }
+            for (int i = threadIdx.x; i < 8 * kTileW; i += blockDim.x) {
+                const int w = i / kTileW, j = i - w * kTileW;
+                const int dd = blockIdx.x * 8 + w;
+                gs[i] = (dd < ndm && t0 + j < t_out) ? g[(int64_t)dd * gld + t0 + j] : 0.f;
+            }
+            __syncthreads();
+            if (active && kc < n) {
+                const float* x = xs + off + kc + lane * kSeg;
+                const float* gv = gs + warp * kTileW + lane * kSeg;
+                float win[kLags];
+#pragma unroll
+                for (int k = 0; k < kLags; ++k) win[k] = x[k];
+#pragma unroll
+                for (int tt = 0; tt < kSeg; ++tt) {
+                    const float gt = gv[tt];
+#pragma unroll
+                    for (int k = 0; k < kLags; ++k) acc[k] = fmaf(gt, win[(k + tt) % kLags], acc[k]);
+                    win[tt % kLags] = x[tt + kLags];
+                }
+            }
+        }
+        if (active) {
+#pragma unroll
+            for (int k = 0; k < kLags; ++k) {
+                const float v = warp_sum(acc[k]);
+                if (lane == 0 && kc + k < kout) gw[((int64_t)d * nchan + c) * kout + kc + k] = (kc + k < n) ? v : 0.f;
+            }
         }
     }
-    gin[(int64_t)c * gin_ld + t_offset + tau] = acc;
 }
 
 }  // namespace
@@ -88,21 +135,58 @@ dd_status launch_backward(dd_plan_s* p, const float* in, int64_t ld, int64_t t_o
                           int64_t t_out, const float* g, int64_t gld, float* gw, float* gin,
                           int64_t gin_ld, cudaStream_t s) {
     if (p->unit) return DD_ERR_UNSUPPORTED;  // gradients need a weighted plan
+    cudaError_t e;
     if (gw) {
-        dim3 grid((unsigned)p->nchan, (unsigned)p->ndm);
-        if (grid.y > 65535) return DD_ERR_UNSUPPORTED;
-        k_bwd_w<<<grid, 256, 0, s>>>(in, ld, t_offset, (int32_t)t_out, g, gld, p->dev.delay,
-                                     p->dev.taps, p->nchan, p->kpad, p->kuser, gw);
-        cudaError_t e = cudaGetLastError();
+        const int xlen = kTileW + p->bw_span + p->kpad + 1;
+        const size_t smem = (size_t)(((xlen + 3) & ~3) + 8 * kTileW) * sizeof(float);
+        if (smem > 200 * 1024) return DD_ERR_UNSUPPORTED;
+        e = cudaFuncSetAttribute(k_bwd_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+        if (e != cudaSuccess) return cuda_status(e);
+        dim3 grid((unsigned)((p->ndm + 7) / 8), (unsigned)p->nchan);
+        k_bwd_w<<<grid, 256, smem, s>>>(in, ld, t_offset, (int32_t)t_out, g, gld, p->dev.delay,
+                                        p->dev.taps, p->nchan, p->ndm, p->kpad, p->kuser,
+                                        p->bw_span, gw);
+        e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
     }
     if (gin) {
-        const int64_t nsamp = t_out + p->dmax;
-        dim3 grid((unsigned)((nsamp + 255) / 256), (unsigned)p->nchan);
-        k_bwd_in<<<grid, 256, 0, s>>>(nsamp, (int32_t)t_out, g, gld, p->dev.delay, p->dev.taps,
-                                      p->dev.w, p->kpad, p->nchan, p->ndm, gin, gin_ld, t_offset);
-        cudaError_t e = cudaGetLastError();
+        dd_status st;
+        if (!p->adj || p->adj_stale) {
+            st = build_adjoint_plan(p);
+            if (st != DD_OK) return st;
+        }
+        dd_plan_s* t = p->adj;
+        st = upload_tables(t);
+        if (st != DD_OK) return st;
+        const int32_t P = p->dmax;
+        const int64_t nsamp = t_out + P;
+        // padded gradient rows: P zeros, t_out values, zeros up to a 16-byte multiple
+        int64_t gpld = t_out + 2 * (int64_t)P + 1;
+        gpld = (gpld + 3) & ~(int64_t)3;
+        const int64_t need = gpld * p->ndm;
+        if (need > p->gpad_elems) {
+            cudaFree(p->d_gpad);
+            p->d_gpad = nullptr;
+            p->gpad_elems = 0;
+            e = cudaMalloc((void**)&p->d_gpad, (size_t)need * sizeof(float));
+            if (e != cudaSuccess) return cuda_status(e);
+            p->gpad_elems = need;
+        }
+        dim3 pg((unsigned)std::min<int64_t>((gpld + 255) / 256, 64), (unsigned)p->ndm);
+        k_pad_rows<<<pg, 256, 0, s>>>(g, gld, (int32_t)t_out, P, p->d_gpad, gpld, p->ndm);
+        e = cudaGetLastError();
         if (e != cudaSuccess) return cuda_status(e);
+        if (p->adj_w_stale) {
+            k_transpose_w<<<1024, 256, 0, s>>>(p->dev.w, p->dev.taps, p->ndm, p->nchan, p->kpad, t->dev.w);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_status(e);
+            st = launch_repack(t, s);
+            if (st != DD_OK) return st;
+            p->adj_w_stale = false;
+        }
+        // gI[c][t_offset + tau] for tau in [0, nsamp): the adjoint plan's outputs
+        st = launch_dedisperse(t, p->d_gpad, gpld, 0, nsamp, gin + t_offset, gin_ld, s);
+        if (st != DD_OK) return st;
     }
     return DD_OK;
 }

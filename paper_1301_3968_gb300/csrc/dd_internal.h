@@ -127,11 +127,22 @@ struct dd_plan_s {
     bool dev_dirty = true;
     dd::DevTables dev;
     std::vector<int32_t> widths_on_dev;  // widths last copied to dev.widths
+    // adjoint workspace, built on the first dd_backward: the transposed plan (output rows
+    // = channels, input rows = trials) whose dedispersion is the input gradient, and the
+    // zero-padded copy of the output gradient it reads
+    dd_plan_s* adj = nullptr;
+    bool adj_stale = true;             // forward delays or taps changed since it was built
+    bool adj_w_stale = true;           // forward weights changed since they were transposed
+    float* d_gpad = nullptr;
+    int64_t gpad_elems = 0;
+    int32_t bw_span = 0;               // widest delay spread of 8 consecutive trials
 };
 
 namespace dd {
 
 dd_status upload_tables(dd_plan_s* p);  // (re)creates the device tables if dirty
+dd_status build_adjoint_plan(dd_plan_s* p);  // (re)builds p->adj on the host
+void destroy_plan(dd_plan_s* p);
 dd_status launch_repack(dd_plan_s* p, cudaStream_t s);  // dev.w -> records' weights
 void fill_dedisp_args(const dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
                       int64_t t_out, void* out, int64_t out_ld, DedispArgs* a);

@@ -239,12 +239,70 @@ dd_status finish_profiles(dd_plan_s* p) {
     p->out_int = p->unit && p->band.in_type == DD_U8;
     p->max_abs_row = row_max * 255;
     if (p->out_int && p->max_abs_row > INT32_MAX) return DD_ERR_OVERFLOW;
+    p->adj_stale = true;
+    p->adj_w_stale = true;
+    int64_t bws = 0;
+    for (int d0 = 0; d0 < p->ndm; d0 += 8)
+        for (int c = 0; c < p->nchan; ++c) {
+            int32_t lo = INT32_MAX, hi = 0;
+            for (int d = d0; d < std::min(p->ndm, d0 + 8); ++d) {
+                lo = std::min(lo, p->delay[(size_t)d * p->nchan + c]);
+                hi = std::max(hi, p->delay[(size_t)d * p->nchan + c]);
+            }
+            bws = std::max<int64_t>(bws, (int64_t)hi - lo);
+        }
+    p->bw_span = (int32_t)std::min<int64_t>(bws, INT32_MAX);
     return build_schedule(p);
 }
 
 }  // namespace
 
 namespace dd {
+
+// The input gradient gI[c][tau] = sum_{d,k} w_dck g[d][tau - delta_dc - k] is a
+// dedispersion with the roles swapped: output rows are channels, input rows are the
+// trials' output gradients zero-padded by P = d_max on both sides, delays
+// P - delta_dc - n_dc + 1 and the taps' weights reversed.  This builds that plan's
+// tables on the host (its weights are filled on the device from the forward plan's).
+dd_status build_adjoint_plan(dd_plan_s* p) {
+    const int D = p->ndm, C = p->nchan;
+    const int32_t P = p->dmax;
+    if (p->adj) {
+        destroy_plan(p->adj);
+        p->adj = nullptr;
+    }
+    dd_plan_s* t = new (std::nothrow) dd_plan_s;
+    if (!t) return DD_ERR_OOM;
+    t->band = p->band;
+    t->band.nchan = D;
+    t->band.in_type = DD_F32;
+    t->band.descending = 0;
+    t->band.nsamp = 0;
+    t->nchan = D;
+    t->ndm = C;
+    t->dms.assign(C, 0.0);
+    t->delay.resize((size_t)C * D);
+    t->taps.resize((size_t)C * D);
+    for (int d = 0; d < D; ++d)
+        for (int c = 0; c < C; ++c) {
+            const size_t dc = (size_t)d * C + c, cd = (size_t)c * D + d;
+            t->delay[cd] = P - p->delay[dc] - p->taps[dc] + 1;
+            t->taps[cd] = p->taps[dc];
+        }
+    t->unit = false;
+    t->kpad = p->kpad;
+    t->kuser = p->kuser;
+    t->w.assign((size_t)C * D * t->kpad, 0.0f);
+    dd_status st = finish_profiles(t);
+    if (st != DD_OK) {
+        delete t;
+        return st;
+    }
+    p->adj = t;
+    p->adj_stale = false;
+    p->adj_w_stale = true;
+    return DD_OK;
+}
 
 dd_status cuda_status(cudaError_t e) {
     if (e == cudaSuccess) return DD_OK;
@@ -277,6 +335,13 @@ static dd_status put(T** dst, const T* src, size_t n) {
     if (e != cudaSuccess) return cuda_status(e);
     if (n) e = cudaMemcpy(*dst, src, n * sizeof(T), cudaMemcpyHostToDevice);
     return cuda_status(e);
+}
+
+void destroy_plan(dd_plan_s* p) {
+    if (p->adj) destroy_plan(p->adj);
+    if (p->d_gpad) cudaFree(p->d_gpad);
+    free_dev(p);
+    delete p;
 }
 
 dd_status upload_tables(dd_plan_s* p) {
@@ -466,6 +531,7 @@ dd_status dd_set_weights_device(dd_plan_t p, const float* d_w, int32_t kmax, voi
                                       (size_t)p->ndm * p->nchan, cudaMemcpyDeviceToDevice,
                                       (cudaStream_t)stream);
     if (e != cudaSuccess) return dd::cuda_status(e);
+    p->adj_w_stale = true;
     return dd::launch_repack(p, (cudaStream_t)stream);
 }
 
@@ -683,8 +749,7 @@ dd_status dd_test_set_wait(dd_plan_t p, int32_t skip_stage, int64_t wait_ns) {
 
 dd_status dd_plan_destroy(dd_plan_t p) {
     if (!p) return DD_ERR_ARG;
-    dd::free_dev(p);
-    delete p;
+    dd::destroy_plan(p);
     return DD_OK;
 }
 

@@ -392,3 +392,33 @@ def test_autograd_matches_finite_differences(dd):
         Im[c, t] -= h
         fd = (J_oracle(Ip, w64) - J_oracle(Im, w64)) / (2 * h)
         assert gI[c, t] == pytest.approx(fd, rel=1e-3, abs=1e-5)
+
+
+def test_backward_differentiable_band_sampled(dd):
+    """Differentiable-config shape at reduced size: CRAFT band, 32 learnable taps per
+    channel on every trial, eq. trial DMs to 2000, against the float64 oracle."""
+    rng = np.random.default_rng(19)
+    b = synth.CRAFT_BAND
+    T, D, K = 6144, 64, 32
+    band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, T, "f32")
+    dms, _ = dd.trial_dms(band, 0.0, 2000.0, D, tau_av_ms=1.0)
+    plan = dd.Plan(band, dms)
+    delay, taps0 = plan.tables()
+    taps = np.full_like(taps0, K)
+    w = (rng.uniform(0.5, 1.5, size=(D, b.nchan, K)) * (np.arange(K)[None, None, :] < taps0[:, :, None])).astype(np.float32)
+    plan.set_profiles(delay=delay, taps=taps, weights=w)
+    I = rng.standard_normal((b.nchan, T)).astype(np.float32)
+    t_out = T - plan.d_max
+    g = rng.standard_normal((D, t_out)).astype(np.float32)
+    gw, gI = plan.backward(_dev(I), _dev(g))
+    ogw, ogI = oracle.c_adjoint(I, g, delay, taps, w)
+    sgw, sgI = oracle.c_adjoint(np.abs(I), np.abs(g), delay, taps, np.abs(w))
+    assert (np.abs(gw.cpu().numpy() - ogw) <= RTOL * sgw + 1e-30).all()
+    assert (np.abs(gI.cpu().numpy() - ogI) <= RTOL * sgI + 1e-30).all()
+    # device weights (the training path) give the same gradients
+    plan2 = dd.Plan(band, dms)
+    plan2.set_profiles(delay=delay, taps=taps, weights=np.ones_like(w))
+    plan2.set_weights(_dev(w))
+    gw2, gI2 = plan2.backward(_dev(I), _dev(g))
+    np.testing.assert_array_equal(gw2.cpu().numpy(), gw.cpu().numpy())
+    np.testing.assert_array_equal(gI2.cpu().numpy(), gI.cpu().numpy())

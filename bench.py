@@ -177,7 +177,6 @@ def run_gpu(args):
     stream = torch.cuda.current_stream()
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)      # 256 MiB > 129 MB L2
     out = torch.empty((W["ndm"], W["t_out"]), dtype=torch.float32, device=dev)
-    launches_per_step = LAUNCHES_PER_STEP
 
     def step(ev=None):
         mean, sd = plan.channel_stats(x, nsamp=W["nsamp"])
@@ -217,8 +216,16 @@ def run_gpu(args):
     units = float(W["ndm"]) * W["t_out"]
     value = ws * units / (ms / 1e3)
 
-    if args.no_e2e:
-        return _result(args, W, ws, rank, ms, value, k_ms, clocks, None)
+    e2e = None if args.no_e2e else e2e_run(args, W, ws, plan, x, out, widths, stream)
+    extras = None
+    if rank == 0 and not args.no_extras:
+        extras = {"fwd_bwd": diff_extra(dd, dev, flush, stream),
+                  "batched": batched_extra(dd, dev, flush, stream)}
+    return _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras)
+
+
+def e2e_run(args, W, ws, plan, x, out, widths, stream):
+    import torch
 
     # end to end through the public API: pinned host input -> device, the hot path,
     # peak S/N and times back to the host, every step
@@ -250,9 +257,150 @@ def run_gpu(args):
     h2d = host.numel() * host.element_size()
     d2h = peak_h.numel() * 4 + arg_h.numel() * 4
     units = float(W["ndm"]) * W["t_out"]
-    e2e = {"value": ws * units / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
-           "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
-    return _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e)
+    return {"value": ws * units / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+            "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
+
+
+# ----------------------------------------------------------------------------- extras
+
+
+def _ev_time(fn, reps, flush, stream):
+    """Mean device time (ms) of fn over `reps` calls, L2 flushed before each, events on
+    the launching stream."""
+    import torch
+    fn()
+    torch.cuda.synchronize()
+    ts = []
+    for i in range(reps):
+        flush.fill_(i & 0xFF)
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        e0.record(stream)
+        fn()
+        e1.record(stream)
+        torch.cuda.synchronize()
+        ts.append(e0.elapsed_time(e1))
+    return sum(ts) / len(ts)
+
+
+def diff_extra(dd, dev, flush, stream, reps=5):
+    """Differentiable configuration: 336 ch, 16384 fp32 samples, 1024 trial DMs to 2000,
+    32 learnable fp32 taps per channel.  Plain forward (fixed weights) against one
+    forward + backward through DDFunction (weights copied in, the dedispersed series,
+    then the adjoint for the weight and input gradients)."""
+    import torch
+    import synth
+    cfg = synth.make_diff(npulse=0)          # timing does not depend on the pulses
+    b, T, D, K = cfg["band"], cfg["nsamp"], 1024, 32
+    band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, T, "f32")
+    dms, _ = dd.trial_dms(band, 0.0, 2000.0, D, tau_av_ms=1.0)
+    plan = dd.Plan(band, dms)
+    delay, taps0 = plan.tables()
+    rng = np.random.default_rng(synth.sub_seed("diff-weights"))
+    w0 = (rng.uniform(0.5, 1.5, size=(D, b.nchan, K))
+          * (np.arange(K)[None, None, :] < taps0[:, :, None])).astype(np.float32)
+    plan.set_profiles(delay=delay, taps=np.full_like(taps0, K), weights=w0)
+    t_out = T - plan.d_max
+    x = torch.from_numpy(cfg["data"]).to(dev)
+    w = torch.from_numpy(w0).to(dev)
+    out = torch.empty((D, t_out), dtype=torch.float32, device=dev)
+    g = torch.from_numpy(rng.standard_normal((D, t_out)).astype(np.float32)).to(dev)
+    plan.set_weights(w)
+    fwd_ms = _ev_time(lambda: plan.dedisperse(x, nsamp=T, out=out), reps, flush, stream)
+    xr = x.clone().requires_grad_(True)
+    wr = w.clone().requires_grad_(True)
+
+    def fwd_bwd():
+        xr.grad = None
+        wr.grad = None
+        y = dd.DDFunction.apply(xr, wr, plan, 0, T)
+        y.backward(g)
+
+    fb_ms = _ev_time(fwd_bwd, reps, flush, stream)
+    bw_ms = _ev_time(lambda: plan.backward(x, g, nsamp=T, want_gin=False), reps, flush, stream)
+    bi_ms = _ev_time(lambda: plan.backward(x, g, nsamp=T, want_gw=False), reps, flush, stream)
+    units = float(D) * t_out
+    flops = 2.0 * D * b.nchan * K * t_out
+    plan.close()
+    return {
+        "workload": (f"differentiable: {b.nchan} ch, {T} fp32 samples (noise), {D} trial DMs "
+                     f"0-2000, {K} learnable taps per channel"),
+        "fwd_ms": fwd_ms, "fwd_bwd_ms": fb_ms, "bwd_w_ms": bw_ms, "bwd_in_ms": bi_ms,
+        "fwd_value": units / (fwd_ms / 1e3), "fwd_bwd_value": units / (fb_ms / 1e3), "unit": UNIT,
+        "fwd_bwd_over_fwd": fb_ms / fwd_ms,
+        "fwd_tflops": flops / (fwd_ms / 1e3) / 1e12,
+        "bwd_w_tflops": flops / (bw_ms / 1e3) / 1e12,
+        "bwd_in_tflops": flops / (bi_ms / 1e3) / 1e12,
+    }
+
+
+def batched_extra(dd, dev, flush, stream, reps=3):
+    """Batched configuration: 36 beams on the CRAFT band, uint8 in / int32 out, per-beam
+    lengths 2^14-2^17 and 512-8192 trial DMs (seeded log-uniform), each plan autotuned.
+    One persistent launch (and the CUDA graph of the whole block, boxcars included)
+    against the same beams run one plain launch after another."""
+    import tempfile
+    import torch
+    import synth
+    cfg = synth.make_batched_beams()
+    b = cfg["band"]
+    widths = np.arange(1, 33, dtype=np.int32)
+    plans, xs, outs = [], [], []
+    tune = os.path.join(tempfile.mkdtemp(prefix="dd_tune_"), "schedule.txt")
+    for beam in cfg["beams"]:
+        band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, beam["nsamp"], "u8")
+        dms, _ = dd.trial_dms(band, 0.0, beam["dm_max"], beam["ndm"], tau_av_ms=1.0)
+        plan = dd.Plan(band, dms)
+        x = torch.from_numpy(synth.make_beam_data(beam)).to(dev)
+        out = torch.empty((len(dms), beam["nsamp"] - plan.d_max), dtype=torch.int32, device=dev)
+        plan.autotune(x, out, cache_path=tune)
+        plans.append(plan)
+        xs.append(x)
+        outs.append(out)
+    units = float(sum(p.ndm * o.shape[1] for p, o in zip(plans, outs)))
+    batch = dd.Batch(plans)
+    batch.bind(xs, outs)
+    means = [torch.empty(b.nchan, dtype=torch.float64, device=dev) for _ in plans]
+    sds = [torch.empty_like(m) for m in means]
+    peaks = [torch.empty((p.ndm, len(widths)), dtype=torch.float32, device=dev) for p in plans]
+    args = [torch.empty((p.ndm, len(widths)), dtype=torch.int32, device=dev) for p in plans]
+    batch.bind_boxcar(widths, means, sds, peaks, args)
+
+    def per_beam_fwd():
+        for p, x, o in zip(plans, xs, outs):
+            p.dedisperse(x, nsamp=p.band.nsamp, out=o)
+
+    def per_beam_step():
+        for p, x, o in zip(plans, xs, outs):
+            m, s = p.channel_stats(x, nsamp=p.band.nsamp)
+            p.dedisperse(x, nsamp=p.band.nsamp, out=o)
+            p.boxcar_snr(o, widths, m, s)
+
+    # a graph is captured on a stream of its own (not the legacy default stream); every
+    # variant runs and is timed on that stream
+    gs = torch.cuda.Stream(dev)
+    gs.wait_stream(stream)
+    with torch.cuda.stream(gs):
+        plain_ms = _ev_time(per_beam_fwd, reps, flush, gs)
+        batched_ms = _ev_time(lambda: batch.dedisperse(gs), reps, flush, gs)
+        eager_ms = _ev_time(per_beam_step, reps, flush, gs)
+        batch.capture(gs)
+        graph_ms = _ev_time(lambda: batch.replay(gs), reps, flush, gs)
+    info = batch.info()
+    batch.close()
+    for p in plans:
+        p.close()
+    return {
+        "workload": (f"batched: {len(plans)} beams, {b.nchan} ch, {sum(x.shape[1] for x in xs)} "
+                     f"uint8 samples in all, {sum(p.ndm for p in plans)} trials in all, "
+                     "int32 out, boxcar widths 1-32, autotuned schedules"),
+        "units": units, "items": info["items"], "grid": info["grid"],
+        "plain_fwd_ms": plain_ms, "batched_fwd_ms": batched_ms,
+        "plain_step_ms": eager_ms, "graph_step_ms": graph_ms,
+        "plain_fwd_value": units / (plain_ms / 1e3), "batched_fwd_value": units / (batched_ms / 1e3),
+        "graph_step_value": units / (graph_ms / 1e3), "unit": UNIT,
+        "batched_over_plain_fwd": plain_ms / batched_ms,
+    }
 
 
 def _profile_traffic():
@@ -279,7 +427,7 @@ def _profile_traffic():
         return None
 
 
-def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e):
+def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras=None):
     if rank != 0:
         return None
     peaks, kind = _peaks()
@@ -306,6 +454,8 @@ def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e):
                      "kernel_ms": k_avg, "flops_per_launch": W["flops"]},
         "clocks": clocks,
     }
+    if extras is not None:
+        res["extras"] = extras
     if not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(W, budget_s=args.cpu_seconds)
     return res
@@ -401,6 +551,8 @@ def main():
     ap.add_argument("--ndm", type=int, default=None,
                     help="trial count override (profiling on a smaller case); default 4096")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the forward+backward and batched-beam measurements")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per dedispersion launch from an ncu capture")
     args = ap.parse_args()

@@ -326,6 +326,200 @@ __global__ void __launch_bounds__(256) k_boxcar(BoxArgs a) {
     }
 }
 
+// Contiguous width lists (w_j = w_0 + j): the sums come from a per-thread prefix
+// sequence instead of G running sums.  Each thread owns S consecutive start times of
+// a chunk and walks P[i] = sum_{k<i} x[ls + k] (P[0] = 0, one add per step, in index
+// order), keeping P[s + w_0 + j] for the G widths in a rotating register window, so
+// B_j(t) = P[s + w_j] - P[s] costs one subtract and one max per (t, width).  Integer
+// series accumulate in unsigned arithmetic: the difference is exact modulo 2^bits and
+// the true sum fits the signed type (the plan's bound), so wrap-around in P is harmless.
+// The hot loop keeps only maxima.  A thread records, per width, the chunk in which its
+// segment maximum last rose strictly; the CTA picks the largest value and the earliest
+// (chunk, thread), i.e. the earliest segment holding the maximum, and one thread per
+// width then recomputes that segment's sums from global memory with the same
+// recurrence (bit-identical values) to find the earliest time.
+template <typename TB>
+struct Acc;
+template <>
+struct Acc<float> {
+    using U = float;
+};
+template <>
+struct Acc<int> {
+    using U = unsigned int;
+};
+template <>
+struct Acc<long long> {
+    using U = unsigned long long;
+};
+
+template <typename TX, typename TB>
+__device__ __forceinline__ typename Acc<TB>::U to_acc(TX v) {
+    using U = typename Acc<TB>::U;
+    return (U)(TB)v;
+}
+
+template <typename TX, typename TB, bool FULL>
+__device__ __forceinline__ void run_segment(const TX* xl, int w0, int t0, int t_len, TB (&seg)[kBoxG]) {
+    constexpr int S = kBoxS, G = kBoxG;
+    using U = typename Acc<TB>::U;
+    U p = U(0);
+    U q = U(0);
+    for (int k = 0; k < w0; ++k) q += to_acc<TX, TB>(xl[k]);
+    U win[G];
+    win[0] = q;
+#pragma unroll
+    for (int j = 1; j < G; ++j) win[j] = win[j - 1] + to_acc<TX, TB>(xl[w0 + j - 1]);
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            TB v = (TB)(win[(j + s) % G] - p);
+            if (!FULL) v = (t0 + s + w0 + j <= t_len) ? v : lowest<TB>();
+            seg[j] = max(seg[j], v);
+        }
+        p += to_acc<TX, TB>(xl[s]);
+        win[s % G] = win[(s + G - 1) % G] + to_acc<TX, TB>(xl[s + w0 + G - 1]);
+    }
+}
+
+template <typename TX, typename TB>
+__global__ void __launch_bounds__(256) k_boxcar_run(BoxArgs a) {
+    constexpr int S = kBoxS, G = kBoxG;
+    using U = typename Acc<TB>::U;
+    extern __shared__ __align__(16) unsigned char smem_raw[];
+    TX* xs = (TX*)smem_raw;
+    __shared__ TB rb[8][G];
+    __shared__ int rc[8][G];
+    __shared__ int rt[8][G];
+    const int d = blockIdx.y;
+    const int j0 = blockIdx.x * G;
+    const int cnt = min(G, a.nw - j0);
+    const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int w0 = a.widths[j0];
+    const int wlast = w0 + cnt - 1;
+    const TX o = (TX)a.off[d];
+    const TX* xrow = (const TX*)a.x + (int64_t)d * a.ld;
+    TB best[G];
+    int bch[G];
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        best[j] = lowest<TB>();
+        bch[j] = -1;
+    }
+    const int tvalid = a.t_len - w0 + 1;
+    const int chunk = 256 * S;
+    const int stage = chunk + w0 + G;
+    const int ls = tid * S;
+    for (int ci = 0, tc = 0; tc < tvalid; ++ci, tc += chunk) {
+        __syncthreads();
+        for (int i = tid; i < stage; i += 256) {
+            const int t = tc + i;
+            xs[i] = t < a.t_len ? (TX)(xrow[t] - o) : TX(0);
+        }
+        __syncthreads();
+        TB seg[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) seg[j] = lowest<TB>();
+        if (tc + chunk - 1 + wlast <= a.t_len)
+            run_segment<TX, TB, true>(xs + ls, w0, tc + ls, a.t_len, seg);
+        else if (tc + ls < tvalid)
+            run_segment<TX, TB, false>(xs + ls, w0, tc + ls, a.t_len, seg);
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            if (seg[j] > best[j]) {
+                best[j] = seg[j];
+                bch[j] = ci;
+            }
+        }
+    }
+    // (max, earliest chunk, earliest thread) over the CTA
+#pragma unroll
+    for (int j = 0; j < G; ++j) {
+        TB b = best[j];
+        int c = bch[j];
+        int t = tid;
+#pragma unroll
+        for (int ofs = 16; ofs > 0; ofs >>= 1) {
+            const TB ob = __shfl_xor_sync(0xffffffffu, b, ofs);
+            const int oc = __shfl_xor_sync(0xffffffffu, c, ofs);
+            const int ot = __shfl_xor_sync(0xffffffffu, t, ofs);
+            if (oc >= 0 && (c < 0 || ob > b || (ob == b && (oc < c || (oc == c && ot < t))))) {
+                b = ob;
+                c = oc;
+                t = ot;
+            }
+        }
+        if (lane == 0) {
+            rb[warp][j] = b;
+            rc[warp][j] = c;
+            rt[warp][j] = t;
+        }
+    }
+    __syncthreads();
+    if (tid < cnt) {
+        const int j = tid;
+        TB b = rb[0][j];
+        int c = rc[0][j], th = rt[0][j];
+        for (int k = 1; k < 8; ++k) {
+            const TB ob = rb[k][j];
+            const int oc = rc[k][j], ot = rt[k][j];
+            if (oc >= 0 && (c < 0 || ob > b || (ob == b && (oc < c || (oc == c && ot < th))))) {
+                b = ob;
+                c = oc;
+                th = ot;
+            }
+        }
+        int arg = -1;
+        if (c >= 0) {
+            // the winning segment again, with the hot loop's recurrence
+            const int w = w0 + j;
+            const int t0 = c * chunk + th * S;
+            auto xv = [&](int t) -> U { return to_acc<TX, TB>(t < a.t_len ? (TX)(xrow[t] - o) : TX(0)); };
+            U p = U(0), r = U(0);
+            for (int k = 0; k < w0; ++k) r += xv(t0 + k);
+            for (int k = w0; k < w; ++k) r += xv(t0 + k);
+            for (int s = 0; s < S; ++s) {
+                const int t = t0 + s;
+                if (t + w > a.t_len) break;
+                if ((TB)(r - p) == b) {
+                    arg = t;
+                    break;
+                }
+                p += xv(t);
+                r += xv(t + w);
+            }
+        }
+        const int64_t o2 = (int64_t)d * a.nw + j0 + j;
+        const float snr = (float)(((double)b - (double)a.mu[o2]) * (double)a.isd[o2]);
+        a.peak[o2] = snr;
+        a.arg[o2] = arg;
+        if (a.cands && snr > a.thresh) {
+            const int k = atomicAdd(a.ncands, 1);
+            if (k < a.cap) {
+                dd_candidate cd;
+                cd.dm_index = d;
+                cd.width_index = j0 + j;
+                cd.t = arg;
+                cd.snr = snr;
+                a.cands[k] = cd;
+            }
+        }
+    }
+}
+
+template <typename TX, typename TB>
+dd_status run_boxcar_contig(const BoxArgs& a, int w0_last, cudaStream_t s) {
+    const size_t smem = (size_t)(256 * kBoxS + w0_last + kBoxG) * sizeof(TX);
+    auto kern = k_boxcar_run<TX, TB>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    dim3 grid((unsigned)((a.nw + kBoxG - 1) / kBoxG), (unsigned)a.ndm);
+    if (grid.y > 65535) return DD_ERR_UNSUPPORTED;
+    kern<<<grid, 256, smem, s>>>(a);
+    return cuda_status(cudaGetLastError());
+}
+
 template <typename TX, typename TB>
 dd_status run_boxcar(const BoxArgs& a, int wmax_all, cudaStream_t s) {
     const size_t smem = (size_t)(256 * kBoxS + wmax_all + 2) * sizeof(TX);
@@ -339,6 +533,23 @@ dd_status run_boxcar(const BoxArgs& a, int wmax_all, cudaStream_t s) {
 }
 
 }  // namespace
+
+// Series type and sum type, and the contiguous-width kernel when w_j = w_0 + j.
+static dd_status dispatch_boxcar(const dd_plan_s* p, const BoxArgs& a, const int32_t* widths,
+                                 int32_t nw, cudaStream_t s) {
+    const int wmax = widths[nw - 1];
+    bool contig = true;
+    for (int j = 1; j < nw; ++j) contig = contig && widths[j] == widths[0] + j;
+    const int w0_last = widths[((nw - 1) / kBoxG) * kBoxG];
+    if (!p->out_int)
+        return contig ? run_boxcar_contig<float, float>(a, w0_last, s) : run_boxcar<float, float>(a, wmax, s);
+    // exact integer sums around the per-trial offset: |x - o| <= 255 * N_S(d), so a
+    // width-w sum fits int32 when wmax * 255 * max_d N_S(d) < 2^31
+    const long long bound = (long long)wmax * p->max_abs_row;
+    if (bound < (long long)INT_MAX)
+        return contig ? run_boxcar_contig<int, int>(a, w0_last, s) : run_boxcar<int, int>(a, wmax, s);
+    return contig ? run_boxcar_contig<int, long long>(a, w0_last, s) : run_boxcar<int, long long>(a, wmax, s);
+}
 
 dd_status launch_channel_stats(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
                                int64_t nsamp, double* mean, double* sd, cudaStream_t s) {
@@ -398,11 +609,7 @@ dd_status launch_boxcar_scratch(dd_plan_s* p, const void* x, int64_t ld, int64_t
     a.cands = cands;
     a.cap = cap;
     a.ncands = ncands;
-    const int wmax = widths[nw - 1];
-    if (!p->out_int) return run_boxcar<float, float>(a, wmax, s);
-    const long long bound = (long long)wmax * p->max_abs_row;
-    if (bound < (long long)INT_MAX) return run_boxcar<int, int>(a, wmax, s);
-    return run_boxcar<int, long long>(a, wmax, s);
+    return dispatch_boxcar(p, a, widths, nw, s);
 }
 
 dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
@@ -447,13 +654,7 @@ dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
     a.cands = cands;
     a.cap = cap;
     a.ncands = ncands;
-    const int wmax = widths[nw - 1];
-    if (!p->out_int) return run_boxcar<float, float>(a, wmax, s);
-    // exact integer sums around the per-trial offset: |x - o| <= 255 * N_S(d), so a
-    // width-w sum fits int32 when wmax * 255 * max_d N_S(d) < 2^31
-    const long long bound = (long long)wmax * p->max_abs_row;
-    if (bound < (long long)INT_MAX) return run_boxcar<int, int>(a, wmax, s);
-    return run_boxcar<int, long long>(a, wmax, s);
+    return dispatch_boxcar(p, a, widths, nw, s);
 }
 
 }  // namespace dd

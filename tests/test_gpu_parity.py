@@ -277,6 +277,57 @@ def test_boxcar_weighted_float(dd):
     _boxcar_compare(peak.cpu().numpy(), arg.cpu().numpy(), xo, widths, mu, sdw)
 
 
+@pytest.mark.parametrize("seed,T,w0,nw,trim", [
+    (21, 30000, 5, 20, 7),       # several chunks, a ragged second width group
+    (22, 17008, 1, 16, 0),       # one full group, chunk boundary tails
+    (23, 3008, 30, 3, 2000),     # shorter than one chunk, series cut short
+])
+def test_boxcar_contiguous_widths_int(dd, seed, T, w0, nw, trim):
+    """Contiguous width lists (the prefix-window kernel) on integer series: arg exact,
+    including widths not starting at 1, a ragged last group and a cut-short series."""
+    rng = np.random.default_rng(seed)
+    C, D = 32, 8
+    I = rng.integers(0, 256, size=(C, T)).astype(np.uint8)
+    I[:, T // 3:T // 3 + 40] = 255                       # a broad dispersion-free pulse
+    delay = rng.integers(0, 200, size=(D, C)).astype(np.int32)
+    delay[0] = 0
+    taps = rng.integers(1, 5, size=(D, C)).astype(np.int32)
+    plan = dd.Plan(dd.Band(C, 1200.0, 1.0, 1.0, T, "u8"), np.zeros(D))
+    plan.set_profiles(delay=delay, taps=taps)
+    x = _dev(I)
+    out = plan.dedisperse(x, nsamp=T)
+    t_len = out.shape[1] - trim
+    mean, sd = plan.channel_stats(x, nsamp=T)
+    widths = np.arange(w0, w0 + nw, dtype=np.int32)
+    peak, arg, _ = plan.boxcar_snr(out, widths, mean, sd, t_len=t_len)
+    xo = out.cpu().numpy().astype(np.int64)[:, :t_len]
+    mu_c, sd_c = ref.channel_stats(I, nsamp=T)
+    mu, sdw = ref.boxcar_norm(taps, widths, mu_c, sd_c)
+    _, oarg, _ = ref.boxcar_snr(xo, widths, mu, sdw)
+    np.testing.assert_array_equal(arg.cpu().numpy(), oarg)
+    _boxcar_compare(peak.cpu().numpy(), arg.cpu().numpy(), xo, widths, mu, sdw)
+
+
+def test_boxcar_contiguous_widths_float(dd):
+    cfg = synth.make_craft(nsamp=8192, npulse=6, amp=3.0)
+    plan, delay, taps, w = _craft_plan(dd, 128, 8192)
+    x = _dev(cfg["data"])
+    out = plan.dedisperse(x, nsamp=8192)
+    t_len = out.shape[1] - 333
+    mean, sd = plan.channel_stats(x, nsamp=8192)
+    widths = np.arange(3, 43, dtype=np.int32)
+    peak, arg, _ = plan.boxcar_snr(out, widths, mean, sd, t_len=t_len)
+    xo = out.cpu().numpy().astype(np.float64)[:, :t_len]
+    mu_c, sd_c = ref.channel_stats(cfg["data"], nsamp=8192)
+    mu, sdw = ref.boxcar_norm(taps, widths, mu_c, sd_c, w=w)
+    _boxcar_compare(peak.cpu().numpy(), arg.cpu().numpy(), xo, widths, mu, sdw)
+    # the contiguous and the general kernel agree: drop one width to force the latter
+    gen = np.concatenate([widths[:5], widths[6:]])
+    p2, a2, _ = plan.boxcar_snr(out, gen, mean, sd, t_len=t_len)
+    keep = np.r_[0:5, 6:len(widths)]
+    np.testing.assert_allclose(p2.cpu().numpy(), peak.cpu().numpy()[:, keep], rtol=RTOL, atol=RTOL)
+
+
 def test_candidates_above_threshold(dd):
     cfg = synth.make_plain(snr_total=16.0)
     plan = dd.Plan(_band(dd, cfg["band"], cfg["nsamp"], "u8"), cfg["dms"])

@@ -26,8 +26,9 @@
  *     16 bytes and the input base pointer 16-byte aligned (rows are staged in 16-byte
  *     chunks).  Violations return DD_ERR_ARG.
  *   - No call here allocates device memory except dd_plan_create / dd_set_profiles /
- *     the first device call on a plan (tables) and dd_boxcar_snr when the width
- *     count grows (normaliser workspace).
+ *     the first device call on a plan (tables), dd_boxcar_snr when the width count
+ *     grows (normaliser workspace), dd_dedisperse on a run-length plan when nsamp
+ *     grows (prefix scratch) and the first dd_backward (adjoint workspace).
  */
 #ifndef DD_H
 #define DD_H
@@ -126,7 +127,8 @@ dd_status dd_get_tables(dd_plan_t plan, int32_t* delay, int32_t* ntaps);
  * reading columns t_offset .. t_offset + nsamp - 1 of every row (nsamp <= 0 uses the
  * band's).  Chunked calls with t_offset advancing by L reproduce the one-shot result.
  * Errors: DD_ERR_ARG (null, alignment, t_offset + nsamp > in_ld, out_ld too small,
- * nsamp <= d_max), DD_ERR_CUDA. */
+ * nsamp <= d_max), DD_ERR_UNSUPPORTED (run-length plan and nsamp > 2^24), DD_ERR_OOM,
+ * DD_ERR_CUDA. */
 dd_status dd_dedisperse(dd_plan_t plan, const void* d_in, int64_t in_ld, int64_t t_offset,
                         int64_t nsamp, void* d_out, int64_t out_ld, void* stream);
 
@@ -197,11 +199,34 @@ dd_status dd_backward(dd_plan_t plan, const float* d_in, int64_t in_ld, int64_t 
                       float* d_gin, int64_t gin_ld, void* stream);
 
 /* Kernel schedule of the plan: nch time chunks per CTA (the CTA sums 16/nch trials on
- * the fp32 path, 8/nch on the exact integer path) and cs channels per pipeline stage.
+ * the fp32 path, 8/nch on the exact integer path, 24/nch on the run-length path) and cs
+ * channels per pipeline stage.
  * dd_plan_create and dd_set_profiles pick a default; dd_plan_set_schedule overrides it
  * (DD_ERR_UNSUPPORTED if it does not fit in shared memory, the old one is then kept). */
 dd_status dd_plan_set_schedule(dd_plan_t plan, int32_t nch, int32_t cs);
 dd_status dd_plan_get_schedule(dd_plan_t plan, int32_t* nch, int32_t* cs, int32_t* trials_per_cta);
+
+/* How a plan forms the tap sums of eq. p_dedisp.
+ *   DD_METHOD_DIRECT:    every tap is one multiply-add (any weights).
+ *   DD_METHOD_RUNLENGTH: uint8 unit-weight plans only.  A run of n unit taps is a
+ *     difference of per-channel prefix sums, sum_{k<n} I[c][s+k] = P_c[s+n] - P_c[s]
+ *     with P_c[i] = sum_{j<i} I[c][t_offset+j], so each (trial, channel) costs two
+ *     loads and one add per output whatever its tap count.  dd_dedisperse first writes
+ *     P for the requested samples into plan-owned device scratch (4 bytes per channel
+ *     and sample, uint32; exact since the differences are taken modulo 2^32), then sums.
+ *     Results are bit-identical to DD_METHOD_DIRECT.  nsamp is limited to 2^24.
+ *   DD_METHOD_AUTO (default): RUNLENGTH for uint8 unit-weight plans whose mean tap count
+ *     is at least 12, DIRECT otherwise.
+ * dd_plan_set_method rebuilds the schedule (DD_ERR_UNSUPPORTED: RUNLENGTH on a weighted
+ * or fp32 plan; the method is then unchanged).  dd_plan_get_method reports the method in
+ * use (never AUTO).  Batches (below) take DIRECT plans only. */
+typedef enum {
+    DD_METHOD_AUTO = 0,
+    DD_METHOD_DIRECT = 1,
+    DD_METHOD_RUNLENGTH = 2
+} dd_method;
+dd_status dd_plan_set_method(dd_plan_t plan, int32_t method);
+dd_status dd_plan_get_method(dd_plan_t plan, int32_t* method);
 
 /* Autotuner: times the plan's dedispersion on the given buffers (as dd_dedisperse with
  * t_offset 0 and the band's nsamp) for each CTA shape (nch 1, 2) and stage size (fp32:
@@ -215,8 +240,8 @@ dd_status dd_plan_autotune(dd_plan_t plan, const void* d_in, int64_t in_ld, void
 
 /* Many beams in one persistent launch (uneven lengths and trial lists; no counterpart in
  * the paper, which describes one beam).  Each beam has its own plan (same input type and
- * path for all; the plans must outlive the batch); a beam's block is the band's nsamp
- * samples from column 0.  The work list has one item per CTA tile (beam, trial block,
+ * path for all, DD_METHOD_DIRECT, else DD_ERR_UNSUPPORTED; the plans must outlive the
+ * batch); a beam's block is the band's nsamp samples from column 0.  The work list has one item per CTA tile (beam, trial block,
  * time tile), sorted by estimated cost, largest first; the kernel's CTAs take items
  * from an atomic counter that each launch resets. */
 typedef struct dd_batch_s* dd_batch_t;

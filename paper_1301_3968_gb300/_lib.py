@@ -61,6 +61,8 @@ SIGNATURES = {
     "dd_backward": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp]),
     "dd_plan_set_schedule": (c_i32, [c_vp, c_i32, c_i32]),
     "dd_plan_get_schedule": (c_i32, [c_vp, c_vp, c_vp, c_vp]),
+    "dd_plan_set_method": (c_i32, [c_vp, c_i32]),
+    "dd_plan_get_method": (c_i32, [c_vp, c_vp]),
     "dd_plan_autotune": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, ctypes.c_char_p, c_vp, c_vp]),
     "dd_batch_create": (c_i32, [c_vp, c_vp, c_i32]),
     "dd_batch_bind": (c_i32, [c_vp, c_vp, c_vp, c_vp, c_vp]),

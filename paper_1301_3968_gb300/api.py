@@ -221,6 +221,20 @@ class Plan:
                                                         for v in (nch, cs, tpc))), "dd_plan_get_schedule")
         return dict(nch=nch.value, cs=cs.value, trials_per_cta=tpc.value)
 
+    METHODS = {"auto": 0, "direct": 1, "runlength": 2}
+
+    def set_method(self, method: str) -> None:
+        """Tap sums as direct multiply-adds or as prefix-sum differences ("runlength",
+        uint8 unit-weight plans); "auto" picks by mean tap count."""
+        check(self._lib.dd_plan_set_method(self._h, self.METHODS[method]), "dd_plan_set_method")
+
+    @property
+    def method(self) -> str:
+        m = ctypes.c_int32()
+        check(self._lib.dd_plan_get_method(self._h, ctypes.cast(ctypes.byref(m), ctypes.c_void_p)),
+              "dd_plan_get_method")
+        return {1: "direct", 2: "runlength"}[m.value]
+
     def autotune(self, x: torch.Tensor, out: torch.Tensor, cache_path: str | None = None,
                  stream=None) -> float:
         """Times the CTA shapes and stage sizes that fit on (x, out) and keeps the fastest;

@@ -119,6 +119,7 @@ dd_status dd_batch_create(dd_batch_t* out, const dd_plan_t* plans, int32_t nbeam
         if (plans[i]->band.in_type != plans[0]->band.in_type || plans[i]->pair != plans[0]->pair)
             return DD_ERR_ARG;
         if (plan_t_out(plans[i]) < 1) return DD_ERR_ARG;
+        if (plans[i]->rl) return DD_ERR_UNSUPPORTED;
     }
     dd_batch_s* b = new (std::nothrow) dd_batch_s;
     if (!b) return DD_ERR_OOM;
@@ -138,6 +139,7 @@ dd_status dd_batch_bind(dd_batch_t b, const void* const* d_in, const int64_t* in
     std::vector<dd::DedispArgs> args(nb);
     for (int i = 0; i < nb; ++i) {
         dd_plan_s* p = b->plans[i];
+        if (p->rl) return DD_ERR_UNSUPPORTED;
         const int64_t esz = p->band.in_type == DD_U8 ? 1 : 4;
         const int64_t t_out = plan_t_out(p);
         if (!d_in[i] || !d_out[i] || !aligned16(d_in[i]) || (in_ld[i] * esz) % 16 != 0 ||

@@ -95,6 +95,17 @@ template <>
 struct Elem<float> {
     static constexpr int Q = 4;
 };
+template <>
+struct Elem<uint32_t> {  // prefix sums of the run-length path
+    static constexpr int Q = 4;
+};
+
+// Warp units per warp: kRlUnits trials on the run-length path (staged rows of uint32
+// prefix sums), one unit otherwise.
+template <typename TIN>
+__host__ __device__ constexpr int upw() {
+    return std::is_same<TIN, uint32_t>::value ? kRlUnits : 1;
+}
 
 template <typename TACC, typename TIN>
 __device__ __forceinline__ TACC cvt(TIN v) {
@@ -207,6 +218,25 @@ __device__ __forceinline__ void stage_int(const TIN* rows, const int2* ent, cons
     }
 }
 
+// One stage of one warp unit on the run-length path (uint8 samples, unit weights): the
+// staged rows hold the channels' prefix sums P[i] = sum_{j<i} I[j], and the unit's n
+// taps starting at delta sum to P[t + delta + n] - P[t + delta].  Two loads and one
+// add per output whatever n is; the uint32 difference is exact (taken modulo 2^32 and
+// at most 255 n).
+__device__ __forceinline__ void stage_rl(const uint32_t* rows, const int2* ent, const int* lo,
+                                         int csn, int lcap, int bq, int lane_off, int (&acc)[kR]) {
+    constexpr int R = kR;
+    for (int ci = 0; ci < csn; ++ci) {
+        const int2 q = ent[ci];  // (run start - block minimum, taps)
+        const uint32_t* p = rows + ci * lcap + ((bq + lo[ci]) & 3) + q.x + lane_off;
+        const uint32_t* pe = p + q.y;
+        __builtin_assume(__isShared(p));
+        __builtin_assume(__isShared(pe));
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] += (int)(pe[r] - p[r]);
+    }
+}
+
 // One stage of one warp unit on the fp32 path: two adjacent trials share the register
 // window.  The entry's window is the union of the two trials' windows, and its weights
 // are (w0, w1) pairs that are zero where a trial has no tap, so each tap costs one
@@ -281,15 +311,18 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
     constexpr int R = kR;
     constexpr int Q = Elem<TIN>::Q;
     constexpr int TPW = PAIR ? 2 : 1;   // trials per warp unit
+    constexpr bool RL = std::is_same<TIN, uint32_t>::value;
+    constexpr int UPW = upw<TIN>();     // warp units per warp
     using TACC = typename std::conditional<PAIR, float, int>::type;
     const int cs = a.cs;
-    const int nu = kWarps / a.nch;     // warp units per CTA
+    const int nu = kWarps / a.nch * UPW;  // warp units per CTA
     const StageGeom g((int)sizeof(TIN), PAIR, a.lcap, a.kpad, cs, nu);
     const Smem sm = carve<NBUF>(smem, g, a.smem_bytes);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
-    const int dmi = warp / a.nch, chunk = warp - dmi * a.nch;
-    const int d = blk * (TPW * nu) + dmi * TPW;               // first trial of the unit
+    const int wu = warp / a.nch, chunk = warp - wu * a.nch;
+    const int dmi = wu * UPW;                                 // first unit of the warp
+    const int d = blk * (TPW * nu) + dmi * TPW;               // its first trial
     const int64_t t0 = (int64_t)tx * kTileT * a.nch;          // CTA time start
     const int64_t tw = t0 + (int64_t)chunk * kTileT;           // warp time start
     const int64_t base = a.t_offset + t0;
@@ -308,10 +341,15 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
 
     TACC acc0[R];
     float acc1[PAIR ? R : 1];
+    int accr[RL ? UPW - 1 : 1][R];  // the warp's further units (run-length path)
 #pragma unroll
     for (int r = 0; r < R; ++r) acc0[r] = TACC(0);
 #pragma unroll
     for (int r = 0; r < (PAIR ? R : 1); ++r) acc1[r] = 0.f;
+#pragma unroll
+    for (int u = 0; u < (RL ? UPW - 1 : 1); ++u)
+#pragma unroll
+        for (int r = 0; r < R; ++r) accr[u][r] = 0;
     const int bq = (int)(base & (Q - 1));
     const int lane_off = chunk * kTileT + lane * R;
     bool ok = true;
@@ -326,7 +364,19 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
             ok = false;
             break;
         }
-        if (d < a.ndm) {
+        if constexpr (RL) {
+            const unsigned char* buf = smem + b * g.bytes;
+            const uint32_t* rows = (const uint32_t*)buf;
+            const int2* ent = (const int2*)(buf + g.rec_off) + dmi * cs;
+            const int* lo_all = (const int*)(smem + NBUF * g.bytes);
+            const int c0 = s * cs;
+            const int csn = min(cs, a.nchan - c0);
+            if (d < a.ndm) stage_rl(rows, ent, lo_all + c0, csn, a.lcap, bq, lane_off, acc0);
+#pragma unroll
+            for (int u = 1; u < UPW; ++u)
+                if (d + u < a.ndm)
+                    stage_rl(rows, ent + u * cs, lo_all + c0, csn, a.lcap, bq, lane_off, accr[u - 1]);
+        } else if (d < a.ndm) {
             // pointers derived from the __shared__ array itself, so that every access
             // below compiles to a shared-memory load
             const unsigned char* buf = smem + b * g.bytes;
@@ -371,6 +421,12 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
     if constexpr (PAIR)
         store_row<float>(smem, acc1, warp, lane, tw, a.t_out,
                          d + 1 < a.ndm ? (float*)a.out + (int64_t)(d + 1) * a.out_ld : nullptr);
+    if constexpr (RL) {
+#pragma unroll
+        for (int u = 1; u < UPW; ++u)
+            store_row<int>(smem, accr[u - 1], warp, lane, tw, a.t_out,
+                           d + u < a.ndm ? (int*)a.out + (int64_t)(d + u) * a.out_ld : nullptr);
+    }
     if (MULTI) __syncthreads();  // the staging area is the next tile's stage buffers
     return true;
 }
@@ -438,7 +494,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_batched(const DedispA
 // end and survive the transpose).
 template <typename TIN, bool PAIR, int NBUF>
 size_t smem_for(int lcap, int kpad, int cs, int nch, int nchan) {
-    const StageGeom g((int)sizeof(TIN), PAIR, lcap, kpad, cs, kWarps / nch);
+    const StageGeom g((int)sizeof(TIN), PAIR, lcap, kpad, cs, kWarps / nch * upw<TIN>());
     size_t smem = (size_t)dedisp_smem_bytes(g, NBUF, nchan);
     const size_t st = (size_t)kStoreBytes + NBUF * 8 + 2 * NBUF * 4;
     if (smem < st) smem = st;
@@ -447,7 +503,7 @@ size_t smem_for(int lcap, int kpad, int cs, int nch, int nchan) {
 
 template <typename TIN, bool PAIR, int NBUF>
 dd_status run(DedispArgs a, cudaStream_t s) {
-    const int nu = kWarps / a.nch;
+    const int nu = kWarps / a.nch * upw<TIN>();
     const size_t smem = smem_for<TIN, PAIR, NBUF>(a.lcap, a.kpad, a.cs, a.nch, a.nchan);
     a.smem_bytes = (uint32_t)smem;
     auto kern = k_dedisp<TIN, PAIR, NBUF>;
@@ -516,6 +572,79 @@ __global__ void k_repack_w(const float* w, const int32_t* delay, const int32_t* 
     }
 }
 
+// Run-length path, first step: per-channel prefix sums of the uint8 samples,
+// P[c][i] = sum_{j<i} I[c][t_offset + j] for 0 <= i <= n (uint32; zero from n + 1 to
+// the row's end).  One CTA per channel walks its row in blocks of 4096 samples: each
+// thread sums 16 consecutive samples, a warp scan and a scan of the 8 warp totals
+// place it, and the block total carries to the next block.
+__global__ void __launch_bounds__(256) k_prefix(const uint8_t* in, int64_t ld, int64_t t_offset,
+                                                int64_t n, uint32_t* P, int64_t ldp) {
+    const int c = blockIdx.x;
+    const uint8_t* row = in + (int64_t)c * ld + t_offset;
+    uint32_t* prow = P + (int64_t)c * ldp;
+    __shared__ uint32_t wsum[8];
+    const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+    const bool vec = (((uintptr_t)row) & 15) == 0;
+    uint32_t carry = 0;
+    int64_t end = 0;
+    for (int64_t base = 0; base < n; base += 4096) {
+        const int64_t i0 = base + 16 * tid;
+        uint32_t v[16];
+        if (vec && i0 + 16 <= n) {
+            const uint4 q = *(const uint4*)(row + i0);
+            const uint32_t w4[4] = {q.x, q.y, q.z, q.w};
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] = (w4[k >> 2] >> (8 * (k & 3))) & 0xffu;
+        } else {
+#pragma unroll
+            for (int k = 0; k < 16; ++k) v[k] = i0 + k < n ? (uint32_t)row[i0 + k] : 0u;
+        }
+        uint32_t sum = 0;
+#pragma unroll
+        for (int k = 0; k < 16; ++k) {
+            const uint32_t x = v[k];
+            v[k] = sum;  // exclusive within the thread
+            sum += x;
+        }
+        uint32_t incl = sum;
+#pragma unroll
+        for (int o = 1; o < 32; o <<= 1) {
+            const uint32_t t = __shfl_up_sync(0xffffffffu, incl, o);
+            if (lane >= o) incl += t;
+        }
+        if (lane == 31) wsum[warp] = incl;
+        __syncthreads();
+        uint32_t before = 0, total = 0;
+#pragma unroll
+        for (int w = 0; w < 8; ++w) {
+            const uint32_t x = wsum[w];
+            before += w < warp ? x : 0u;
+            total += x;
+        }
+        const uint32_t off = carry + before + incl - sum;
+        if (i0 + 16 <= ldp) {
+            uint4* dst = (uint4*)(prow + i0);
+#pragma unroll
+            for (int k = 0; k < 4; ++k) {
+                uint4 o4;
+                o4.x = i0 + 4 * k + 0 <= n ? off + v[4 * k + 0] : 0u;
+                o4.y = i0 + 4 * k + 1 <= n ? off + v[4 * k + 1] : 0u;
+                o4.z = i0 + 4 * k + 2 <= n ? off + v[4 * k + 2] : 0u;
+                o4.w = i0 + 4 * k + 3 <= n ? off + v[4 * k + 3] : 0u;
+                dst[k] = o4;
+            }
+        } else {
+            for (int k = 0; k < 16 && i0 + k < ldp; ++k) prow[i0 + k] = i0 + k <= n ? off + v[k] : 0u;
+        }
+        carry += total;
+        end = base + 4096;
+        __syncthreads();  // wsum is rewritten by the next block
+    }
+    // P[n] when no block reached it, and the zero tail of the row
+    if (tid == 0)
+        for (int64_t i = end > n ? end : n; i < ldp; ++i) prow[i] = i == n ? carry : 0u;
+}
+
 }  // namespace
 
 dd_status launch_repack(dd_plan_s* p, cudaStream_t s) {
@@ -553,6 +682,7 @@ void fill_dedisp_args(const dd_plan_s* p, const void* in, int64_t ld, int64_t t_
 
 size_t dedisp_smem_for(const dd_plan_s* p) {
     const int kp = p->pair ? p->kw : 0;
+    if (p->rl) return smem_for<uint32_t, false, kStages>(p->lcap, 0, p->cs, p->nch, p->nchan);
     if (!p->pair) return smem_for<uint8_t, false, kStages>(p->lcap, kp, p->cs, p->nch, p->nchan);
     if (p->band.in_type == DD_U8) return smem_for<uint8_t, true, kStages>(p->lcap, kp, p->cs, p->nch, p->nchan);
     return smem_for<float, true, kStages>(p->lcap, kp, p->cs, p->nch, p->nchan);
@@ -566,6 +696,28 @@ dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_
     if (!p->pair) return run<uint8_t, false, kStages>(a, s);
     if (u8) return run<uint8_t, true, kStages>(a, s);
     return run<float, true, kStages>(a, s);
+}
+
+// Run-length path: prefix sums of columns t_offset .. t_offset + nsamp - 1 into the
+// plan's scratch, then the run-length sums over them.
+dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
+                               int64_t nsamp, void* out, int64_t out_ld, cudaStream_t s) {
+    const int64_t ldp = (nsamp + 1 + 3) & ~(int64_t)3;
+    const int64_t need = ldp * p->nchan;
+    if (need > p->prefix_elems) {
+        cudaFree(p->d_prefix);
+        p->d_prefix = nullptr;
+        p->prefix_elems = 0;
+        cudaError_t e = cudaMalloc((void**)&p->d_prefix, (size_t)need * sizeof(uint32_t));
+        if (e != cudaSuccess) return cuda_status(e);
+        p->prefix_elems = need;
+    }
+    k_prefix<<<p->nchan, 256, 0, s>>>((const uint8_t*)in, ld, t_offset, nsamp, p->d_prefix, ldp);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    DedispArgs a;
+    fill_dedisp_args(p, p->d_prefix, ldp, 0, nsamp - p->dmax, out, out_ld, &a);
+    return run<uint32_t, false, kStages>(a, s);
 }
 
 dd_status launch_dedisperse_batched(bool u8, bool pair, const DedispArgs* d_args,

@@ -17,6 +17,8 @@ namespace dd {
 constexpr int kWarps = 8;
 constexpr int kR = 31;
 constexpr int kTileT = 32 * kR;
+constexpr int kRlUnits = 3;                // trials per warp on the run-length path
+constexpr int kRlMinMeanTaps = 12;         // automatic run-length choice (uint8, unit weights)
 constexpr int kStages = 4;                 // bulk-copy pipeline depth
 constexpr int kStagesMax = 8;
 constexpr int kSmemBudget = 110 * 1024;    // dynamic shared memory per CTA (two per SM)
@@ -136,6 +138,12 @@ struct dd_plan_s {
     float* d_gpad = nullptr;
     int64_t gpad_elems = 0;
     int32_t bw_span = 0;               // widest delay spread of 8 consecutive trials
+    // tap sums: direct multiply-adds, or differences of per-channel prefix sums
+    // (run-length path; uint8 unit weights), and that path's prefix scratch
+    int32_t method = DD_METHOD_AUTO;   // requested
+    bool rl = false;                   // in use
+    uint32_t* d_prefix = nullptr;
+    int64_t prefix_elems = 0;
 };
 
 namespace dd {
@@ -147,6 +155,8 @@ dd_status launch_repack(dd_plan_s* p, cudaStream_t s);  // dev.w -> records' wei
 void fill_dedisp_args(const dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
                       int64_t t_out, void* out, int64_t out_ld, DedispArgs* a);
 size_t dedisp_smem_for(const dd_plan_s* p);
+dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
+                               int64_t nsamp, void* out, int64_t out_ld, cudaStream_t s);
 dd_status launch_dedisperse_batched(bool u8, bool pair, const DedispArgs* d_args,
                                     const BatchItem* d_items, int32_t nitems, int32_t* d_counter,
                                     size_t smem, int grid, cudaStream_t s);

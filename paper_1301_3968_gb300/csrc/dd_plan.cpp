@@ -77,8 +77,25 @@ int64_t block_span(const dd_plan_s* p, int db, std::vector<int32_t>* lo_out) {
 }
 
 // Trials per warp unit: two adjacent trials share one register window on the fp32
-// path; the exact integer path sums one trial per warp.
+// path; the exact integer path sums one trial per unit.
 int trials_per_unit(const dd_plan_s* p) { return p->pair ? 2 : 1; }
+
+// Warp units per warp: a run-length warp keeps kRlUnits trials' sums (it needs no
+// register window, so more trials share each staged prefix row).
+int units_per_warp(const dd_plan_s* p) { return p->rl ? dd::kRlUnits : 1; }
+
+// Staged element size and elements per 16-byte chunk: uint8 samples, fp32 samples, or
+// uint32 prefix sums on the run-length path.
+int stage_esz(const dd_plan_s* p) { return p->rl ? 4 : (p->band.in_type == DD_U8 ? 1 : 4); }
+
+// Elements a CTA stages per channel: its outputs, the block's delay spread plus taps
+// (plus the run's end point P[delta + n] on the run-length path), 16 bytes of
+// alignment slack and the element that the register pipeline reads ahead.
+int64_t staged_len(const dd_plan_s* p, int nch, int64_t span) {
+    const int64_t q = 16 / stage_esz(p);
+    int64_t need = (int64_t)nch * dd::kTileT + span + (p->rl ? 1 : 0) + q + 2;
+    return (need + q - 1) / q * q;
+}
 
 // Weight pairs per record entry for a given trial block size: the longest union
 // window [min delta, max(delta + n)) of any warp unit's trials on any channel.
@@ -106,11 +123,11 @@ int32_t union_taps(const dd_plan_s* p, int db) {
 void build_records(dd_plan_s* p) {
     const int C = p->nchan;
     const int tpw = trials_per_unit(p);
-    const int nu = dd::kWarps / p->nch;
+    const int nu = dd::kWarps / p->nch * units_per_warp(p);
     const int db = tpw * nu;
     const int nst = (C + p->cs - 1) / p->cs;
     const int kw = p->pair ? p->kw : 0;
-    const dd::StageGeom g(p->band.in_type == DD_U8 ? 1 : 4, p->pair, p->lcap, kw, p->cs, nu);
+    const dd::StageGeom g(stage_esz(p), p->pair, p->lcap, kw, p->cs, nu);
     p->rec_bytes = g.rec_bytes;
     p->rec.assign((size_t)p->nblk * nst * g.rec_bytes, 0);
     for (int b = 0; b < p->nblk; ++b)
@@ -149,9 +166,12 @@ void build_records(dd_plan_s* p) {
 dd_status build_schedule(dd_plan_s* p) {
     const bool u8 = p->band.in_type == DD_U8;
     p->pair = !(u8 && p->unit);
-    const int64_t q = u8 ? 16 : 4;            // elements per 16-byte chunk
-    const int esz = u8 ? 1 : 4;
-    const int cs_want = u8 ? 8 : 4;
+    const double mean_taps = (double)p->ns_total / ((double)p->ndm * p->nchan);
+    p->rl = u8 && p->unit &&
+            (p->method == DD_METHOD_RUNLENGTH ||
+             (p->method == DD_METHOD_AUTO && mean_taps >= dd::kRlMinMeanTaps));
+    const int esz = stage_esz(p);
+    const int cs_want = esz == 1 ? 8 : 4;
     const int tpw = trials_per_unit(p);
     // first pass: shared memory for two CTAs per SM and at least two channels per
     // stage; second pass: one CTA per SM, any stage size
@@ -159,14 +179,11 @@ dd_status build_schedule(dd_plan_s* p) {
     const int min_cs[2] = {2, 1};
     for (int pass = 0; pass < 2; ++pass) {
         for (int nch = 1; nch <= dd::kWarps; nch *= 2) {
-            const int nu = dd::kWarps / nch;
+            const int nu = dd::kWarps / nch * units_per_warp(p);
             const int db = tpw * nu;
             const int64_t span = block_span(p, db, nullptr);
             const int32_t kw = p->pair ? ((union_taps(p, db) + 1) & ~1) : 0;
-            // the CTA's outputs, the block's delay spread plus taps, 16 bytes of
-            // alignment slack and the element that the register pipeline reads ahead
-            int64_t need = (int64_t)nch * dd::kTileT + span + q + 2;
-            need = (need + q - 1) / q * q;
+            const int64_t need = staged_len(p, nch, span);
             if (need > (1 << 22)) continue;
             int cs = cs_want;
             while (cs >= min_cs[pass] &&
@@ -191,15 +208,12 @@ dd_status build_schedule(dd_plan_s* p) {
 // Fixed CTA shape (nch time chunks) and stage size (cs channels), if it fits.
 dd_status build_schedule_fixed(dd_plan_s* p, int nch, int cs) {
     if (nch < 1 || nch > dd::kWarps || (dd::kWarps % nch) != 0 || cs < 1 || cs > 32) return DD_ERR_ARG;
-    const bool u8 = p->band.in_type == DD_U8;
-    const int64_t q = u8 ? 16 : 4;
-    const int esz = u8 ? 1 : 4;
-    const int nu = dd::kWarps / nch;
+    const int esz = stage_esz(p);
+    const int nu = dd::kWarps / nch * units_per_warp(p);
     const int db = trials_per_unit(p) * nu;
     const int64_t span = block_span(p, db, nullptr);
     const int32_t kw = p->pair ? ((union_taps(p, db) + 1) & ~1) : 0;
-    int64_t need = (int64_t)nch * dd::kTileT + span + q + 2;
-    need = (need + q - 1) / q * q;
+    const int64_t need = staged_len(p, nch, span);
     if (need > (1 << 22)) return DD_ERR_UNSUPPORTED;
     if (dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu), dd::kStages,
                               p->nchan) > dd::kSmemBudgetOne)
@@ -340,6 +354,7 @@ static dd_status put(T** dst, const T* src, size_t n) {
 void destroy_plan(dd_plan_s* p) {
     if (p->adj) destroy_plan(p->adj);
     if (p->d_gpad) cudaFree(p->d_gpad);
+    if (p->d_prefix) cudaFree(p->d_prefix);
     free_dev(p);
     delete p;
 }
@@ -566,8 +581,10 @@ dd_status dd_dedisperse(dd_plan_t p, const void* in, int64_t in_ld, int64_t t_of
     const int64_t t_out = nsamp - p->dmax;
     if (out_ld < t_out) return DD_ERR_ARG;
     if (t_out > INT32_MAX - dd::kTileT || in_ld > (int64_t)1 << 40) return DD_ERR_OVERFLOW;
+    if (p->rl && nsamp > ((int64_t)1 << 24)) return DD_ERR_UNSUPPORTED;
     dd_status st = dd::upload_tables(p);
     if (st != DD_OK) return st;
+    if (p->rl) return dd::launch_dedisperse_rl(p, in, in_ld, t_offset, nsamp, out, out_ld, (cudaStream_t)stream);
     return dd::launch_dedisperse(p, in, in_ld, t_offset, t_out, out, out_ld, (cudaStream_t)stream);
 }
 
@@ -628,7 +645,26 @@ dd_status dd_plan_get_schedule(dd_plan_t p, int32_t* nch, int32_t* cs, int32_t* 
     if (!p) return DD_ERR_ARG;
     if (nch) *nch = p->nch;
     if (cs) *cs = p->cs;
-    if (trials_per_cta) *trials_per_cta = (p->pair ? 2 : 1) * dd::kWarps / p->nch;
+    if (trials_per_cta) *trials_per_cta = trials_per_unit(p) * units_per_warp(p) * dd::kWarps / p->nch;
+    return DD_OK;
+}
+
+dd_status dd_plan_set_method(dd_plan_t p, int32_t method) {
+    if (!p || method < DD_METHOD_AUTO || method > DD_METHOD_RUNLENGTH) return DD_ERR_ARG;
+    if (method == DD_METHOD_RUNLENGTH && !(p->unit && p->band.in_type == DD_U8)) return DD_ERR_UNSUPPORTED;
+    const int32_t old = p->method;
+    p->method = method;
+    dd_status st = build_schedule(p);
+    if (st != DD_OK) {
+        p->method = old;
+        build_schedule(p);
+    }
+    return st;
+}
+
+dd_status dd_plan_get_method(dd_plan_t p, int32_t* method) {
+    if (!p || !method) return DD_ERR_ARG;
+    *method = p->rl ? DD_METHOD_RUNLENGTH : DD_METHOD_DIRECT;
     return DD_OK;
 }
 
@@ -645,7 +681,7 @@ std::string tune_key(const dd_plan_s* p) {
     const int kb = (int)std::floor(std::log2((double)p->kmax + 1.0));
     std::ostringstream o;
     o << "C" << p->nchan << "_" << (p->band.in_type == DD_U8 ? "u8" : "f32") << "_"
-      << (p->pair ? "pair" : "int") << "_s" << sb << "_k" << kb;
+      << (p->pair ? "pair" : (p->rl ? "rl" : "int")) << "_s" << sb << "_k" << kb;
     return o.str();
 }
 
@@ -674,7 +710,7 @@ dd_status dd_plan_autotune(dd_plan_t p, const void* d_in, int64_t in_ld, void* d
         if (best_ms) *best_ms = -1.0f;
         return DD_OK;
     }
-    const bool u8 = p->band.in_type == DD_U8;
+    const bool u8 = stage_esz(p) == 1;
     const int cs_list_f[] = {2, 3, 4, 6, 8};
     const int cs_list_u[] = {4, 8, 12, 16};
     const int* cs_list = u8 ? cs_list_u : cs_list_f;

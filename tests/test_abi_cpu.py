@@ -143,3 +143,30 @@ def test_int32_overflow_is_refused(lib):
     assert e.value.code in (2, 8)
     # the plan keeps its previous profile
     assert plan.tables()[1].max() == 1
+
+
+def test_method_selection_host_logic(lib):
+    """Run-length sums are chosen for uint8 unit-weight plans with long tap runs, are
+    refused for weighted and fp32 plans, and widen the CTA to 24 trials."""
+    import paper_1301_3968_gb300 as dd
+    b = synth.LARGE_BAND
+    band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, 1 << 18, "u8")
+    plan = dd.Plan(band, np.linspace(0.0, 2000.0, 64))
+    assert plan.method == "runlength"                     # mean taps ~66 >= 12
+    assert plan.schedule()["trials_per_cta"] == 24 // plan.schedule()["nch"]
+    plan.set_method("direct")
+    assert plan.method == "direct" and plan.schedule()["trials_per_cta"] == 8 // plan.schedule()["nch"]
+    plan.set_method("auto")
+    assert plan.method == "runlength"
+    pb = synth.PLAIN_BAND
+    small = dd.Plan(dd.Band(pb.nchan, pb.f_lo_mhz, pb.df_mhz, pb.dt_ms, 4096, "u8"), np.linspace(0, 500, 128))
+    assert small.method == "direct"                       # taps <= 12, mean ~3
+    small.set_method("runlength")
+    assert small.method == "runlength"
+    f32 = dd.Plan(dd.Band(pb.nchan, pb.f_lo_mhz, pb.df_mhz, pb.dt_ms, 4096, "f32"), np.linspace(0, 500, 16))
+    with pytest.raises(dd.DDError):
+        f32.set_method("runlength")
+    assert f32.method == "direct"
+    # a run-length plan that gets weights sums directly
+    small.set_profiles(weights=np.ones((128, pb.nchan, 16), np.float32))
+    assert small.method == "direct"

@@ -220,7 +220,8 @@ def run_gpu(args):
     extras = None
     if rank == 0 and not args.no_extras:
         extras = {"fwd_bwd": diff_extra(dd, dev, flush, stream),
-                  "batched": batched_extra(dd, dev, flush, stream)}
+                  "batched": batched_extra(dd, dev, flush, stream),
+                  "large_lowband": large_extra(dd, dev, flush, stream)}
     return _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras)
 
 
@@ -403,6 +404,53 @@ def batched_extra(dd, dev, flush, stream, reps=3):
     }
 
 
+def large_extra(dd, dev, flush, stream, chunk=1 << 18):
+    """Large low-band configuration: 1024 ch over 700-1000 MHz, dt 64 us, 2^20 uint8
+    samples, 8192 trial DMs 0-2000 (unit weights, run-length sums), streamed in
+    overlapping chunks of `chunk` outputs (each chunk reads its outputs plus d_max
+    samples), int32 out, then boxcar S/N over widths 1-256 per chunk."""
+    import torch
+    import synth
+    cfg = synth.make_large()
+    b, T = cfg["band"], cfg["nsamp"]
+    plan = dd.Plan(dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, T, "u8"), cfg["dms"])
+    x = torch.from_numpy(cfg["data"]).to(dev)
+    dmax = plan.d_max
+    t_out = T - dmax
+    starts = list(range(0, t_out, chunk))
+    out = torch.empty((plan.ndm, chunk), dtype=torch.int32, device=dev)
+    widths = np.arange(1, 257, dtype=np.int32)
+    mean, sd = plan.channel_stats(x, nsamp=T)
+
+    def dedisp_all():
+        for t0 in starts:
+            n = min(chunk, t_out - t0)
+            plan.dedisperse(x, t_offset=t0, nsamp=n + dmax, out=out)
+
+    def step_all():
+        for t0 in starts:
+            n = min(chunk, t_out - t0)
+            plan.dedisperse(x, t_offset=t0, nsamp=n + dmax, out=out)
+            plan.boxcar_snr(out, widths, mean, sd, t_len=n)
+
+    dd_ms = _ev_time(dedisp_all, 2, flush, stream)
+    st_ms = _ev_time(step_all, 2, flush, stream)
+    units = float(plan.ndm) * t_out
+    dct = units * b.nchan
+    res = {
+        "workload": (f"large low-band: {b.nchan} ch 700-1000 MHz, dt 64 us, {T} uint8 samples, "
+                     f"{plan.ndm} trial DMs 0-2000, {len(starts)} overlapping chunks of {chunk} "
+                     "outputs, int32 out, boxcar widths 1-256"),
+        "method": plan.method, "d_max": dmax, "t_out": t_out,
+        "dedisp_ms": dd_ms, "step_ms": st_ms,
+        "dedisp_value": units / (dd_ms / 1e3), "step_value": units / (st_ms / 1e3), "unit": UNIT,
+        "trial_channel_samples_per_s": dct / (dd_ms / 1e3),
+        "realtime_factor": (t_out * b.dt_ms / 1e3) / (st_ms / 1e3),
+    }
+    plan.close()
+    return res
+
+
 def _profile_traffic():
     """DRAM bytes per dedispersion launch from the committed ncu summary, if it was
     taken on the current kernel source (else None)."""
@@ -552,7 +600,7 @@ def main():
                     help="trial count override (profiling on a smaller case); default 4096")
     ap.add_argument("--no-e2e", action="store_true")
     ap.add_argument("--no-extras", action="store_true",
-                    help="skip the forward+backward and batched-beam measurements")
+                    help="skip the forward+backward, batched-beam and large low-band measurements")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per dedispersion launch from an ncu capture")
     args = ap.parse_args()

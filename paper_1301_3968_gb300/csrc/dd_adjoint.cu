@@ -14,6 +14,7 @@
 // registers; lanes own 33 consecutive samples (odd, so lane-strided shared loads are
 // conflict free) and slide a 32-sample register window along them; the lanes' partial
 // sums are added in a fixed order at the end.  Both paths are deterministic.
+#include <algorithm>
 #include <cstdint>
 
 #include "dd_internal.h"
@@ -54,9 +55,23 @@ __device__ __forceinline__ float warp_sum(float v) {
     return v;
 }
 
-// grid (trial blocks of 8, channels).  Shared memory: the channel's window for the
-// block's 8 trials and the 8 gradient rows of the current tile.
-__global__ void __launch_bounds__(256) k_bwd_w(const float* in, int64_t ld, int64_t t_offset,
+__device__ __forceinline__ void cp_async4(float* dst, const float* src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(ok ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+// grid (trial blocks of 8, channels).  Shared memory: two buffers, each the channel's
+// window for the block's 8 trials and the 8 gradient rows of one tile of kTileW
+// outputs; the next tile's copies (cp.async, zero-filled past the ends of the rows)
+// are in flight while the current one is summed.
+__global__ void __launch_bounds__(256, 2) k_bwd_w(const float* in, int64_t ld, int64_t t_offset,
                                                int32_t t_out, const float* g, int64_t gld,
                                                const int32_t* delay, const int32_t* taps,
                                                int32_t nchan, int32_t ndm, int32_t kpad,
@@ -66,8 +81,9 @@ __global__ void __launch_bounds__(256) k_bwd_w(const float* in, int64_t ld, int6
     const int c = blockIdx.y;
     const int d = blockIdx.x * 8 + warp;
     const int xlen = kTileW + span + kpad + 1;
-    float* xs = sm;                       // [xlen]
-    float* gs = sm + ((xlen + 3) & ~3);   // [8][kTileW]
+    const int xstride = (xlen + 3) & ~3;
+    float* const buf0 = sm;                          // [xlen] then [8][kTileW]
+    float* const buf1 = sm + xstride + 8 * kTileW;
     __shared__ int s_lo;
     __shared__ int s_del[8], s_tap[8];
     if (threadIdx.x < 8) {
@@ -88,25 +104,47 @@ __global__ void __launch_bounds__(256) k_bwd_w(const float* in, int64_t ld, int6
     const int n = active ? s_tap[warp] : 0;
     const float* row = in + (int64_t)c * ld + t_offset + lo;
     const int64_t row_end = ld - t_offset - lo;  // columns available in the row
+    const int ntile = (t_out + kTileW - 1) / kTileW;
+    // the CTA stages the channel window shared by its 8 trials; each warp stages its own
+    // trial's gradient segment (a full tile needs no bounds tests)
+    auto stage = [&](int t0, float* B) {
+        float* xs = B;
+        for (int i = threadIdx.x; i < xlen; i += blockDim.x) {
+            const int64_t col = (int64_t)t0 + i;
+            const bool ok = col < row_end;
+            cp_async4(xs + i, ok ? row + col : in, ok);
+        }
+        float* gs = B + xstride + warp * kTileW;
+        if (active && t0 + kTileW <= t_out) {
+            const float* grow = g + (int64_t)d * gld + t0 + lane;
+#pragma unroll
+            for (int j = 0; j < kSeg; ++j) cp_async4(gs + j * 32 + lane, grow + j * 32, true);
+        } else {
+            for (int j = 0; j < kSeg; ++j) {
+                const int tt = j * 32 + lane;
+                const bool ok = active && t0 + tt < t_out;
+                cp_async4(gs + tt, ok ? g + (int64_t)d * gld + t0 + tt : g, ok);
+            }
+        }
+        cp_async_commit();
+    };
     for (int kc = 0; kc < kout; kc += kLags) {
         float acc[kLags];
 #pragma unroll
         for (int k = 0; k < kLags; ++k) acc[k] = 0.f;
-        for (int t0 = 0; t0 < t_out; t0 += kTileW) {
-            __syncthreads();
-            for (int i = threadIdx.x; i < xlen; i += blockDim.x) {
-                const int64_t col = (int64_t)t0 + i;
-                xs[i] = col < row_end ? row[col] : 0.f;
-            }
-            for (int i = threadIdx.x; i < 8 * kTileW; i += blockDim.x) {
-                const int w = i / kTileW, j = i - w * kTileW;
-                const int dd = blockIdx.x * 8 + w;
-                gs[i] = (dd < ndm && t0 + j < t_out) ? g[(int64_t)dd * gld + t0 + j] : 0.f;
+        stage(0, buf0);
+        for (int it = 0; it < ntile; ++it) {
+            if (it + 1 < ntile) {
+                stage((it + 1) * kTileW, (it & 1) ? buf0 : buf1);
+                cp_async_wait<1>();
+            } else {
+                cp_async_wait<0>();
             }
             __syncthreads();
             if (active && kc < n) {
+                const float* xs = (it & 1) ? buf1 : buf0;
                 const float* x = xs + off + kc + lane * kSeg;
-                const float* gv = gs + warp * kTileW + lane * kSeg;
+                const float* gv = xs + xstride + warp * kTileW + lane * kSeg;
                 float win[kLags];
 #pragma unroll
                 for (int k = 0; k < kLags; ++k) win[k] = x[k];
@@ -118,6 +156,7 @@ __global__ void __launch_bounds__(256) k_bwd_w(const float* in, int64_t ld, int6
                     win[tt % kLags] = x[tt + kLags];
                 }
             }
+            __syncthreads();  // this buffer is restaged by the next iteration but one
         }
         if (active) {
 #pragma unroll
@@ -126,6 +165,18 @@ __global__ void __launch_bounds__(256) k_bwd_w(const float* in, int64_t ld, int6
                 if (lane == 0 && kc + k < kout) gw[((int64_t)d * nchan + c) * kout + kc + k] = (kc + k < n) ? v : 0.f;
             }
         }
+    }
+}
+
+// gI[c][tau] = sum over splits of the partial sums (fixed order: deterministic).
+__global__ void k_sum_splits(const float* part, int32_t nsplit, int64_t split_ld, int32_t rows,
+                             int64_t n, int64_t pld, float* gin, int64_t gin_ld) {
+    const int c = blockIdx.y;
+    if (c >= rows) return;
+    for (int64_t t = (int64_t)blockIdx.x * blockDim.x + threadIdx.x; t < n; t += (int64_t)gridDim.x * blockDim.x) {
+        float v = 0.f;
+        for (int z = 0; z < nsplit; ++z) v += part[z * split_ld + (int64_t)c * pld + t];
+        gin[(int64_t)c * gin_ld + t] = v;
     }
 }
 
@@ -138,7 +189,7 @@ dd_status launch_backward(dd_plan_s* p, const float* in, int64_t ld, int64_t t_o
     cudaError_t e;
     if (gw) {
         const int xlen = kTileW + p->bw_span + p->kpad + 1;
-        const size_t smem = (size_t)(((xlen + 3) & ~3) + 8 * kTileW) * sizeof(float);
+        const size_t smem = (size_t)2 * (((xlen + 3) & ~3) + 8 * kTileW) * sizeof(float);
         if (smem > 200 * 1024) return DD_ERR_UNSUPPORTED;
         e = cudaFuncSetAttribute(k_bwd_w, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
         if (e != cudaSuccess) return cuda_status(e);
@@ -184,9 +235,41 @@ dd_status launch_backward(dd_plan_s* p, const float* in, int64_t ld, int64_t t_o
             if (st != DD_OK) return st;
             p->adj_w_stale = false;
         }
-        // gI[c][t_offset + tau] for tau in [0, nsamp): the adjoint plan's outputs
-        st = launch_dedisperse(t, p->d_gpad, gpld, 0, nsamp, gin + t_offset, gin_ld, s);
-        if (st != DD_OK) return st;
+        // gI[c][t_offset + tau] for tau in [0, nsamp): the adjoint plan's outputs.  Its
+        // few output rows (channels) give few CTAs; when they would not fill the GPU
+        // about four times over, the sum over its input rows (trials) is split across
+        // grid z into partial sums that k_sum_splits adds in a fixed order.
+        int sms = 0, dev = 0;
+        e = cudaGetDevice(&dev);
+        if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
+        if (e != cudaSuccess) return cuda_status(e);
+        const int64_t tile = (int64_t)kTileT * t->nch;
+        const int64_t db = (int64_t)2 * (kWarps / t->nch);
+        const int64_t ctas = ((nsamp + tile - 1) / tile) * ((t->ndm + db - 1) / db);
+        const int nst = (t->nchan + t->cs - 1) / t->cs;
+        int nsplit = (int)std::min<int64_t>(std::min<int64_t>(8, nst), (4LL * 2 * sms + ctas - 1) / ctas);
+        if (nsplit <= 1) {
+            st = launch_dedisperse(t, p->d_gpad, gpld, 0, nsamp, gin + t_offset, gin_ld, s);
+            if (st != DD_OK) return st;
+        } else {
+            const int64_t pld = (nsamp + 3) & ~(int64_t)3;
+            const int64_t split_ld = pld * t->ndm;
+            if (split_ld * nsplit > p->gsplit_elems) {
+                cudaFree(p->d_gsplit);
+                p->d_gsplit = nullptr;
+                p->gsplit_elems = 0;
+                e = cudaMalloc((void**)&p->d_gsplit, (size_t)(split_ld * nsplit) * sizeof(float));
+                if (e != cudaSuccess) return cuda_status(e);
+                p->gsplit_elems = split_ld * nsplit;
+            }
+            st = launch_dedisperse(t, p->d_gpad, gpld, 0, nsamp, p->d_gsplit, pld, s, nsplit, split_ld);
+            if (st != DD_OK) return st;
+            dim3 sg((unsigned)std::min<int64_t>((nsamp + 255) / 256, 64), (unsigned)t->ndm);
+            k_sum_splits<<<sg, 256, 0, s>>>(p->d_gsplit, nsplit, split_ld, t->ndm, nsamp, pld,
+                                            gin + t_offset, gin_ld);
+            e = cudaGetLastError();
+            if (e != cudaSuccess) return cuda_status(e);
+        }
     }
     return DD_OK;
 }

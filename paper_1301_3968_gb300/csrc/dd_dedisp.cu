@@ -327,6 +327,11 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
     const int64_t tw = t0 + (int64_t)chunk * kTileT;           // warp time start
     const int64_t base = a.t_offset + t0;
     const int nst = (a.nchan + cs - 1) / cs;
+    // the CTA's stages: a contiguous share of the channel sum when the launch splits it
+    // (blockIdx.z = split, partial sums to separate outputs), else all of them
+    const int split = (int)blockIdx.z;
+    const int s_lo = (int)((int64_t)split * nst / a.nsplit);
+    const int nloc = (int)((int64_t)(split + 1) * nst / a.nsplit) - s_lo;
 
     // per-channel block minima; does any staged window run past the end of its row?
     int past_end = 0;
@@ -337,7 +342,7 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
     }
     const bool tail = __syncthreads_or(past_end) != 0;
     if (tid == 0)
-        for (int s = 0; s < NBUF && s < nst; ++s) issue_stage<TIN, NBUF>(a, g, sm, blk, s, s, base, tail);
+        for (int i = 0; i < NBUF && i < nloc; ++i) issue_stage<TIN, NBUF>(a, g, sm, blk, s_lo + i, i, base, tail);
 
     TACC acc0[R];
     float acc1[PAIR ? R : 1];
@@ -354,10 +359,11 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
     const int lane_off = chunk * kTileT + lane * R;
     bool ok = true;
 
-    for (int s = 0; s < nst; ++s) {
-        const int b = s % NBUF;
+    for (int i = 0; i < nloc; ++i) {
+        const int s = s_lo + i;
+        const int b = i % NBUF;
         // a one-tile CTA starts every buffer at phase 0; a persistent CTA continues
-        const uint32_t parity = (uint32_t)(((MULTI ? ts.uses[b] : 0) + s / NBUF) & 1);
+        const uint32_t parity = (uint32_t)(((MULTI ? ts.uses[b] : 0) + i / NBUF) & 1);
         const bool got = mbar_wait_bounded(&sm.full[b], parity, a.wait_ns);
         if (!__all_sync(0xffffffffu, got)) {
             if (lane == 0) atomicExch(a.status, (int)DD_ERR_TIMEOUT);
@@ -399,7 +405,7 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
             const int old = atomicAdd(&sm.cnt[b], 1);
             if (old == kWarps - 1) {  // last warp out refills the buffer
                 sm.cnt[b] = 0;
-                if (s + NBUF < nst) issue_stage<TIN, NBUF>(a, g, sm, blk, s + NBUF, b, base, tail);
+                if (i + NBUF < nloc) issue_stage<TIN, NBUF>(a, g, sm, blk, s + NBUF, b, base, tail);
             }
         }
     }
@@ -413,19 +419,19 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
     }
     if (!__syncthreads_and(ok)) return false;
     if (MULTI && tid == 0)
-        for (int b = 0; b < NBUF && b < nst; ++b) ts.uses[b] += (nst - b + NBUF - 1) / NBUF;
+        for (int b = 0; b < NBUF && b < nloc; ++b) ts.uses[b] += (nloc - b + NBUF - 1) / NBUF;
 
     // transpose through shared memory and store coalesced, one trial row at a time
-    TACC* out = (TACC*)a.out;
+    TACC* out = (TACC*)a.out + (int64_t)split * a.split_ld;
     store_row<TACC>(smem, acc0, warp, lane, tw, a.t_out, d < a.ndm ? out + (int64_t)d * a.out_ld : nullptr);
     if constexpr (PAIR)
         store_row<float>(smem, acc1, warp, lane, tw, a.t_out,
-                         d + 1 < a.ndm ? (float*)a.out + (int64_t)(d + 1) * a.out_ld : nullptr);
+                         d + 1 < a.ndm ? (float*)out + (int64_t)(d + 1) * a.out_ld : nullptr);
     if constexpr (RL) {
 #pragma unroll
         for (int u = 1; u < UPW; ++u)
             store_row<int>(smem, accr[u - 1], warp, lane, tw, a.t_out,
-                           d + u < a.ndm ? (int*)a.out + (int64_t)(d + u) * a.out_ld : nullptr);
+                           d + u < a.ndm ? (int*)out + (int64_t)(d + u) * a.out_ld : nullptr);
     }
     if (MULTI) __syncthreads();  // the staging area is the next tile's stage buffers
     return true;
@@ -511,8 +517,9 @@ dd_status run(DedispArgs a, cudaStream_t s) {
     if (e != cudaSuccess) return cuda_status(e);
     const int64_t tile = (int64_t)kTileT * a.nch;
     const int db = (PAIR ? 2 : 1) * nu;
-    dim3 grid((unsigned)((a.t_out + tile - 1) / tile), (unsigned)((a.ndm + db - 1) / db));
-    if (grid.y > 65535) return DD_ERR_UNSUPPORTED;
+    dim3 grid((unsigned)((a.t_out + tile - 1) / tile), (unsigned)((a.ndm + db - 1) / db),
+              (unsigned)a.nsplit);
+    if (grid.y > 65535 || a.nsplit < 1 || a.nsplit > 64) return DD_ERR_UNSUPPORTED;
     kern<<<grid, kWarps * 32, smem, s>>>(a);
     return cuda_status(cudaGetLastError());
 }
@@ -678,6 +685,8 @@ void fill_dedisp_args(const dd_plan_s* p, const void* in, int64_t ld, int64_t t_
     a->skip_stage = p->debug_skip_stage;
     a->wait_ns = p->wait_ns;
     a->smem_bytes = (uint32_t)dedisp_smem_for(p);
+    a->nsplit = 1;
+    a->split_ld = 0;
 }
 
 size_t dedisp_smem_for(const dd_plan_s* p) {
@@ -689,9 +698,12 @@ size_t dedisp_smem_for(const dd_plan_s* p) {
 }
 
 dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
-                            int64_t t_out, void* out, int64_t out_ld, cudaStream_t s) {
+                            int64_t t_out, void* out, int64_t out_ld, cudaStream_t s, int nsplit,
+                            int64_t split_ld) {
     DedispArgs a;
     fill_dedisp_args(p, in, ld, t_offset, t_out, out, out_ld, &a);
+    a.nsplit = nsplit;
+    a.split_ld = split_ld;
     const bool u8 = p->band.in_type == DD_U8;
     if (!p->pair) return run<uint8_t, false, kStages>(a, s);
     if (u8) return run<uint8_t, true, kStages>(a, s);

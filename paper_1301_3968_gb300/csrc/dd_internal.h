@@ -68,6 +68,8 @@ struct DedispArgs {
     int32_t cs;   // channels per stage
     int32_t nch;  // time chunks per CTA (trials per CTA = kWarps / nch)
     int32_t kpad;  // weight pairs per record entry (pair path)
+    int32_t nsplit;    // channel-sum splits (grid z); split z writes out + z * split_ld
+    int64_t split_ld;
     int32_t* status;
     int32_t skip_stage;
     int64_t wait_ns;
@@ -138,6 +140,8 @@ struct dd_plan_s {
     float* d_gpad = nullptr;
     int64_t gpad_elems = 0;
     int32_t bw_span = 0;               // widest delay spread of 8 consecutive trials
+    float* d_gsplit = nullptr;         // partial input gradients of a split adjoint sum
+    int64_t gsplit_elems = 0;
     // tap sums: direct multiply-adds, or differences of per-channel prefix sums
     // (run-length path; uint8 unit weights), and that path's prefix scratch
     int32_t method = DD_METHOD_AUTO;   // requested
@@ -165,7 +169,8 @@ dd_status cuda_status(cudaError_t e);
 
 // launchers (stream = cudaStream_t)
 dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
-                            int64_t t_out, void* out, int64_t out_ld, cudaStream_t s);
+                            int64_t t_out, void* out, int64_t out_ld, cudaStream_t s,
+                            int nsplit = 1, int64_t split_ld = 0);
 dd_status launch_channel_stats(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
                                int64_t nsamp, double* mean, double* sd, cudaStream_t s);
 dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,

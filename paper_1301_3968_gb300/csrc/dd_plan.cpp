@@ -354,6 +354,7 @@ static dd_status put(T** dst, const T* src, size_t n) {
 void destroy_plan(dd_plan_s* p) {
     if (p->adj) destroy_plan(p->adj);
     if (p->d_gpad) cudaFree(p->d_gpad);
+    if (p->d_gsplit) cudaFree(p->d_gsplit);
     if (p->d_prefix) cudaFree(p->d_prefix);
     free_dev(p);
     delete p;

@@ -243,7 +243,7 @@ dd_status launch_backward(dd_plan_s* p, const float* in, int64_t ld, int64_t t_o
         e = cudaGetDevice(&dev);
         if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
         if (e != cudaSuccess) return cuda_status(e);
-        const int64_t tile = (int64_t)kTileT * t->nch;
+        const int64_t tile = (int64_t)chunk_t(true) * t->nch;
         const int64_t db = (int64_t)2 * (kWarps / t->nch);
         const int64_t ctas = ((nsamp + tile - 1) / tile) * ((t->ndm + db - 1) / db);
         const int nst = (t->nchan + t->cs - 1) / t->cs;

@@ -23,6 +23,7 @@
 struct dd_batch_s {
     std::vector<dd_plan_s*> plans;
     bool u8 = false, pair = true;
+    bool short_taps = true;  // every plan's union windows fit one register window
     std::vector<dd::BatchItem> items;
     size_t smem = 0;
     int grid = 0;
@@ -77,7 +78,7 @@ void build_items(dd_batch_s* b) {
         const int tpw = p->pair ? 2 : 1;
         const int db = tpw * dd::kWarps / p->nch;
         const int64_t t_out = plan_t_out(p);
-        const int64_t tile = (int64_t)dd::kTileT * p->nch;
+        const int64_t tile = (int64_t)dd::chunk_t(p->pair) * p->nch;
         const int ntile = (int)((t_out + tile - 1) / tile);
         const int nst = (p->nchan + p->cs - 1) / p->cs;
         b->units += (int64_t)p->ndm * t_out;
@@ -158,7 +159,9 @@ dd_status dd_batch_bind(dd_batch_t b, const void* const* d_in, const int64_t* in
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return dd::cuda_status(e);
-    const int per_sm = dd::dedisp_batched_blocks_per_sm(b->u8, b->pair, b->smem);
+    b->short_taps = true;
+    for (auto* p : b->plans) b->short_taps = b->short_taps && p->umax <= dd::kRPair;
+    const int per_sm = dd::dedisp_batched_blocks_per_sm(b->u8, b->pair, b->short_taps, b->smem);
     if (per_sm < 1) return DD_ERR_UNSUPPORTED;
     b->grid = std::min<int>(per_sm * sms, (int)b->items.size());
     b->device = dev;
@@ -186,7 +189,7 @@ dd_status dd_batch_bind(dd_batch_t b, const void* const* d_in, const int64_t* in
 dd_status dd_batch_dedisperse(dd_batch_t b, void* stream) {
     if (!b) return DD_ERR_ARG;
     if (!b->bound) return DD_ERR_STATE;
-    return dd::launch_dedisperse_batched(b->u8, b->pair, b->d_args, b->d_items, (int32_t)b->items.size(),
+    return dd::launch_dedisperse_batched(b->u8, b->pair, b->short_taps, b->d_args, b->d_items, (int32_t)b->items.size(),
                                          b->d_counter, b->smem, b->grid, (cudaStream_t)stream);
 }
 

@@ -21,8 +21,10 @@
 //   * Every wait is bounded by time; a wait that runs out records DD_ERR_TIMEOUT in the
 //     plan's status word, the CTA drains its own copies in flight and returns.
 //   * Inner loop: a register window of kR samples slides along the taps; each tap
-//     costs one shared-memory load, one weight-pair broadcast and 2 x kR FMAs (or one
-//     load and kR exact int32 adds for uint8 unit-weight plans).  kR is odd, so the
+//     costs one shared-memory load, one weight-pair broadcast and kR packed pair FMAs
+//     (fma.rn.f32x2: 2 x kR fp32 FMAs; or one load and kR exact int32 adds for uint8
+//     unit-weight plans, or, on the run-length path, two loads and one add per output
+//     whatever the tap count).  kR is odd, so the
 //     lane-strided loads hit 32 distinct banks.
 //   * Sums run over channels, then taps, in a fixed order, so results are
 //     deterministic.
@@ -112,6 +114,21 @@ __device__ __forceinline__ TACC cvt(TIN v) {
     return (TACC)v;
 }
 
+// Packed pairs for the fp32 pair units: one 64-bit register holds (trial 0, trial 1)
+// accumulators or weights, or a window sample duplicated in both halves, and one
+// fma.rn.f32x2 performs both trials' fused multiply-adds (each exactly fmaf).
+__device__ __forceinline__ uint64_t pk_dup(float x) {
+    uint64_t r;
+    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
+    return r;
+}
+__device__ __forceinline__ void fma2(uint64_t& acc, uint64_t w, uint64_t x) {
+    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(w), "l"(x));
+}
+__device__ __forceinline__ void unpk(uint64_t v, float& lo, float& hi) {
+    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
+}
+
 struct Smem {
     unsigned char* stages;
     int* lo_all;
@@ -195,9 +212,9 @@ __device__ void issue_stage(const DedispArgs& a, const StageGeom& g, const Smem&
 template <typename TIN>
 __device__ __forceinline__ void stage_int(const TIN* rows, const int2* ent, const int* lo,
                                           int csn, int lcap, int bq, int lane_off,
-                                          int (&acc)[kR]) {
+                                          int (&acc)[kRInt]) {
     constexpr int Q = Elem<TIN>::Q;
-    constexpr int R = kR;
+    constexpr int R = kRInt;
     for (int ci = 0; ci < csn; ++ci) {
         const int2 q = ent[ci];  // (window start - block minimum, taps)
         const int n = q.y;
@@ -224,8 +241,8 @@ __device__ __forceinline__ void stage_int(const TIN* rows, const int2* ent, cons
 // add per output whatever n is; the uint32 difference is exact (taken modulo 2^32 and
 // at most 255 n).
 __device__ __forceinline__ void stage_rl(const uint32_t* rows, const int2* ent, const int* lo,
-                                         int csn, int lcap, int bq, int lane_off, int (&acc)[kR]) {
-    constexpr int R = kR;
+                                         int csn, int lcap, int bq, int lane_off, int (&acc)[kRInt]) {
+    constexpr int R = kRInt;
     for (int ci = 0; ci < csn; ++ci) {
         const int2 q = ent[ci];  // (run start - block minimum, taps)
         const uint32_t* p = rows + ci * lcap + ((bq + lo[ci]) & 3) + q.x + lane_off;
@@ -240,46 +257,55 @@ __device__ __forceinline__ void stage_rl(const uint32_t* rows, const int2* ent, 
 // One stage of one warp unit on the fp32 path: two adjacent trials share the register
 // window.  The entry's window is the union of the two trials' windows, and its weights
 // are (w0, w1) pairs that are zero where a trial has no tap, so each tap costs one
-// window load, one weight-pair broadcast and 2 x kR FMAs.  Sums run over channels,
-// then taps, in a fixed order (deterministic); single-precision accumulation of the
-// ~10^3-10^4 terms of an output stays orders of magnitude inside the 1e-5 scale-aware
-// bound.
-template <typename TIN>
+// window load, one weight-pair broadcast and kR packed FMAs (2 x kR fp32 FMAs).  The
+// window keeps each sample duplicated in both halves of a 64-bit register.  SHORT: the
+// plan's union windows are at most kR taps, so the taps are one unrolled pass.  Sums
+// run over channels, then taps, in a fixed order (deterministic); single-precision
+// accumulation of the ~10^3-10^4 terms of an output stays orders of magnitude inside
+// the 1e-5 scale-aware bound.
+template <typename TIN, bool SHORT>
 __device__ __forceinline__ void stage_pair(const TIN* rows, const int2* ent, const float2* wts,
                                            const int* lo, int csn, int lcap, int kw, int bq,
-                                           int lane_off, float (&acc0)[kR], float (&acc1)[kR]) {
+                                           int lane_off, uint64_t (&acc)[kRPair]) {
     constexpr int Q = Elem<TIN>::Q;
-    constexpr int R = kR;
+    constexpr int R = kRPair;
     for (int ci = 0; ci < csn; ++ci) {
         const int2 q = ent[ci];
         const int n = q.y;
         const TIN* p = rows + ci * lcap + ((bq + lo[ci]) & (Q - 1)) + q.x + lane_off;
-        const float2* wk = wts + ci * kw;
+        const uint64_t* wk = (const uint64_t*)(wts + ci * kw);
         __builtin_assume(__isShared(p));
         __builtin_assume(__isShared(wk));
-        float win[R];
+        uint64_t win[R];
 #pragma unroll
-        for (int j = 0; j < R; ++j) win[j] = (float)p[j];
-        for (int k0 = 0; k0 < n; k0 += R) {
+        for (int j = 0; j < R; ++j) win[j] = pk_dup((float)p[j]);
+        if constexpr (SHORT) {
 #pragma unroll
             for (int kk = 0; kk < R; ++kk) {
-                if (k0 + kk >= n) break;
-                const float2 w = wk[k0 + kk];
+                if (kk >= n) break;
+                const uint64_t w = wk[kk];
 #pragma unroll
-                for (int r = 0; r < R; ++r) {
-                    acc0[r] = fmaf(w.x, win[(r + kk) % R], acc0[r]);
-                    acc1[r] = fmaf(w.y, win[(r + kk) % R], acc1[r]);
+                for (int r = 0; r < R; ++r) fma2(acc[r], w, win[(r + kk) % R]);
+                win[kk] = pk_dup((float)p[R + kk]);
+            }
+        } else {
+            for (int k0 = 0; k0 < n; k0 += R) {
+#pragma unroll
+                for (int kk = 0; kk < R; ++kk) {
+                    if (k0 + kk >= n) break;
+                    const uint64_t w = wk[k0 + kk];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) fma2(acc[r], w, win[(r + kk) % R]);
+                    win[kk] = pk_dup((float)p[R + k0 + kk]);
                 }
-                win[kk] = (float)p[R + k0 + kk];
             }
         }
     }
 }
 
-template <typename TACC>
-__device__ __forceinline__ void store_row(unsigned char* smem, const TACC (&acc)[kR], int warp,
+template <typename TACC, int R>
+__device__ __forceinline__ void store_row(unsigned char* smem, const TACC (&acc)[R], int warp,
                                           int lane, int64_t tw, int32_t t_out, TACC* out) {
-    constexpr int R = kR;
     TACC* st = (TACC*)smem + warp * (32 * R);
 #pragma unroll
     for (int r = 0; r < R; ++r) st[lane * R + r] = acc[r];
@@ -305,10 +331,11 @@ struct TileState {
 // Returns false (on every thread) if a bounded wait ran out.
 // `a` is taken by value: with a reference to the kernel parameter the compiler picked
 // a register allocation for the FMA loop that ran 11 % slower.
-template <typename TIN, bool PAIR, int NBUF, bool MULTI>
+template <typename TIN, bool PAIR, int NBUF, bool MULTI, bool SHORT>
 __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* smem, int blk,
                                             int tx, TileState& ts) {
-    constexpr int R = kR;
+    constexpr int R = lane_r(PAIR);
+    constexpr int TT = 32 * R;          // outputs per warp time chunk
     constexpr int Q = Elem<TIN>::Q;
     constexpr int TPW = PAIR ? 2 : 1;   // trials per warp unit
     constexpr bool RL = std::is_same<TIN, uint32_t>::value;
@@ -323,8 +350,8 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
     const int wu = warp / a.nch, chunk = warp - wu * a.nch;
     const int dmi = wu * UPW;                                 // first unit of the warp
     const int d = blk * (TPW * nu) + dmi * TPW;               // its first trial
-    const int64_t t0 = (int64_t)tx * kTileT * a.nch;          // CTA time start
-    const int64_t tw = t0 + (int64_t)chunk * kTileT;           // warp time start
+    const int64_t t0 = (int64_t)tx * TT * a.nch;              // CTA time start
+    const int64_t tw = t0 + (int64_t)chunk * TT;               // warp time start
     const int64_t base = a.t_offset + t0;
     const int nst = (a.nchan + cs - 1) / cs;
     // the CTA's stages: a contiguous share of the channel sum when the launch splits it
@@ -345,18 +372,18 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
         for (int i = 0; i < NBUF && i < nloc; ++i) issue_stage<TIN, NBUF>(a, g, sm, blk, s_lo + i, i, base, tail);
 
     TACC acc0[R];
-    float acc1[PAIR ? R : 1];
+    uint64_t accp[PAIR ? R : 1];    // packed (trial 0, trial 1) sums of a pair unit
     int accr[RL ? UPW - 1 : 1][R];  // the warp's further units (run-length path)
 #pragma unroll
     for (int r = 0; r < R; ++r) acc0[r] = TACC(0);
 #pragma unroll
-    for (int r = 0; r < (PAIR ? R : 1); ++r) acc1[r] = 0.f;
+    for (int r = 0; r < (PAIR ? R : 1); ++r) accp[r] = 0ull;
 #pragma unroll
     for (int u = 0; u < (RL ? UPW - 1 : 1); ++u)
 #pragma unroll
         for (int r = 0; r < R; ++r) accr[u][r] = 0;
     const int bq = (int)(base & (Q - 1));
-    const int lane_off = chunk * kTileT + lane * R;
+    const int lane_off = chunk * TT + lane * R;
     bool ok = true;
 
     for (int i = 0; i < nloc; ++i) {
@@ -393,8 +420,8 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
             const int csn = min(cs, a.nchan - c0);
             if constexpr (PAIR) {
                 const float2* wts = (const float2*)(buf + g.rec_off + g.w_off) + dmi * cs * a.kpad;
-                stage_pair<TIN>(rows, ent, wts, lo_all + c0, csn, a.lcap, a.kpad, bq, lane_off,
-                                acc0, acc1);
+                stage_pair<TIN, SHORT>(rows, ent, wts, lo_all + c0, csn, a.lcap, a.kpad, bq,
+                                       lane_off, accp);
             } else {
                 stage_int<TIN>(rows, ent, lo_all + c0, csn, a.lcap, bq, lane_off, acc0);
             }
@@ -423,14 +450,19 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
 
     // transpose through shared memory and store coalesced, one trial row at a time
     TACC* out = (TACC*)a.out + (int64_t)split * a.split_ld;
-    store_row<TACC>(smem, acc0, warp, lane, tw, a.t_out, d < a.ndm ? out + (int64_t)d * a.out_ld : nullptr);
+    float acc1[PAIR ? R : 1];
+    if constexpr (PAIR) {
+#pragma unroll
+        for (int r = 0; r < R; ++r) unpk(accp[r], acc0[r], acc1[r]);
+    }
+    store_row<TACC, R>(smem, acc0, warp, lane, tw, a.t_out, d < a.ndm ? out + (int64_t)d * a.out_ld : nullptr);
     if constexpr (PAIR)
-        store_row<float>(smem, acc1, warp, lane, tw, a.t_out,
+        store_row<float, R>(smem, acc1, warp, lane, tw, a.t_out,
                          d + 1 < a.ndm ? (float*)out + (int64_t)(d + 1) * a.out_ld : nullptr);
     if constexpr (RL) {
 #pragma unroll
         for (int u = 1; u < UPW; ++u)
-            store_row<int>(smem, accr[u - 1], warp, lane, tw, a.t_out,
+            store_row<int, R>(smem, accr[u - 1], warp, lane, tw, a.t_out,
                            d + u < a.ndm ? (int*)out + (int64_t)(d + u) * a.out_ld : nullptr);
     }
     if (MULTI) __syncthreads();  // the staging area is the next tile's stage buffers
@@ -458,19 +490,19 @@ __device__ __forceinline__ unsigned char* pipeline_area(unsigned char* smem, siz
     return smem + smem_bytes - (size_t)(nbuf * 8 + 2 * nbuf * 4);
 }
 
-template <typename TIN, bool PAIR, int NBUF>
+template <typename TIN, bool PAIR, int NBUF, bool SHORT>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ TileState ts;
     if (threadIdx.x == 0) init_pipeline<NBUF>(pipeline_area(smem, a.smem_bytes, NBUF), ts);
     __syncthreads();
-    dedisp_tile<TIN, PAIR, NBUF, false>(a, smem, blockIdx.y, blockIdx.x, ts);
+    dedisp_tile<TIN, PAIR, NBUF, false, SHORT>(a, smem, blockIdx.y, blockIdx.x, ts);
 }
 
 // Persistent form: each CTA takes work items (beam, trial block, time tile) from an
 // atomic counter until none remain.  Items are sorted by estimated cost, largest
 // first, so the uneven beams finish together.  The counter is reset before each launch.
-template <typename TIN, bool PAIR, int NBUF>
+template <typename TIN, bool PAIR, int NBUF, bool SHORT>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_batched(const DedispArgs* beams,
                                                                     const BatchItem* items,
                                                                     int32_t nitems, int32_t* counter,
@@ -491,7 +523,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_batched(const DedispA
             sa.smem_bytes = smem_bytes;
         }
         __syncthreads();
-        if (!dedisp_tile<TIN, PAIR, NBUF, true>(sa, smem, it.blk, it.tx, ts)) break;
+        if (!dedisp_tile<TIN, PAIR, NBUF, true, SHORT>(sa, smem, it.blk, it.tx, ts)) break;
     }
 }
 
@@ -507,15 +539,15 @@ size_t smem_for(int lcap, int kpad, int cs, int nch, int nchan) {
     return (smem + 15) & ~(size_t)15;
 }
 
-template <typename TIN, bool PAIR, int NBUF>
+template <typename TIN, bool PAIR, int NBUF, bool SHORT = false>
 dd_status run(DedispArgs a, cudaStream_t s) {
     const int nu = kWarps / a.nch * upw<TIN>();
     const size_t smem = smem_for<TIN, PAIR, NBUF>(a.lcap, a.kpad, a.cs, a.nch, a.nchan);
     a.smem_bytes = (uint32_t)smem;
-    auto kern = k_dedisp<TIN, PAIR, NBUF>;
+    auto kern = k_dedisp<TIN, PAIR, NBUF, SHORT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
-    const int64_t tile = (int64_t)kTileT * a.nch;
+    const int64_t tile = (int64_t)chunk_t(PAIR) * a.nch;
     const int db = (PAIR ? 2 : 1) * nu;
     dim3 grid((unsigned)((a.t_out + tile - 1) / tile), (unsigned)((a.ndm + db - 1) / db),
               (unsigned)a.nsplit);
@@ -524,10 +556,10 @@ dd_status run(DedispArgs a, cudaStream_t s) {
     return cuda_status(cudaGetLastError());
 }
 
-template <typename TIN, bool PAIR, int NBUF>
+template <typename TIN, bool PAIR, int NBUF, bool SHORT = false>
 dd_status run_batched(const DedispArgs* d_args, const BatchItem* d_items, int32_t nitems,
                       int32_t* d_counter, size_t smem, int grid, cudaStream_t s) {
-    auto kern = k_dedisp_batched<TIN, PAIR, NBUF>;
+    auto kern = k_dedisp_batched<TIN, PAIR, NBUF, SHORT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
     e = cudaMemsetAsync(d_counter, 0, sizeof(int32_t), s);
@@ -536,10 +568,10 @@ dd_status run_batched(const DedispArgs* d_args, const BatchItem* d_items, int32_
     return cuda_status(cudaGetLastError());
 }
 
-template <typename TIN, bool PAIR, int NBUF>
+template <typename TIN, bool PAIR, int NBUF, bool SHORT = false>
 int blocks_per_sm(size_t smem) {
     int n = 0;
-    auto kern = k_dedisp_batched<TIN, PAIR, NBUF>;
+    auto kern = k_dedisp_batched<TIN, PAIR, NBUF, SHORT>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kWarps * 32, smem) != cudaSuccess) return 0;
@@ -706,8 +738,9 @@ dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_
     a.split_ld = split_ld;
     const bool u8 = p->band.in_type == DD_U8;
     if (!p->pair) return run<uint8_t, false, kStages>(a, s);
-    if (u8) return run<uint8_t, true, kStages>(a, s);
-    return run<float, true, kStages>(a, s);
+    const bool short_taps = p->umax <= kRPair;
+    if (u8) return short_taps ? run<uint8_t, true, kStages, true>(a, s) : run<uint8_t, true, kStages>(a, s);
+    return short_taps ? run<float, true, kStages, true>(a, s) : run<float, true, kStages>(a, s);
 }
 
 // Run-length path: prefix sums of columns t_offset .. t_offset + nsamp - 1 into the
@@ -732,18 +765,21 @@ dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t
     return run<uint32_t, false, kStages>(a, s);
 }
 
-dd_status launch_dedisperse_batched(bool u8, bool pair, const DedispArgs* d_args,
+dd_status launch_dedisperse_batched(bool u8, bool pair, bool short_taps, const DedispArgs* d_args,
                                     const BatchItem* d_items, int32_t nitems, int32_t* d_counter,
                                     size_t smem, int grid, cudaStream_t s) {
     if (!pair) return run_batched<uint8_t, false, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
-    if (u8) return run_batched<uint8_t, true, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
-    return run_batched<float, true, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
+    if (u8)
+        return short_taps ? run_batched<uint8_t, true, kStages, true>(d_args, d_items, nitems, d_counter, smem, grid, s)
+                          : run_batched<uint8_t, true, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
+    return short_taps ? run_batched<float, true, kStages, true>(d_args, d_items, nitems, d_counter, smem, grid, s)
+                      : run_batched<float, true, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
 }
 
-int dedisp_batched_blocks_per_sm(bool u8, bool pair, size_t smem) {
+int dedisp_batched_blocks_per_sm(bool u8, bool pair, bool short_taps, size_t smem) {
     if (!pair) return blocks_per_sm<uint8_t, false, kStages>(smem);
-    if (u8) return blocks_per_sm<uint8_t, true, kStages>(smem);
-    return blocks_per_sm<float, true, kStages>(smem);
+    if (u8) return short_taps ? blocks_per_sm<uint8_t, true, kStages, true>(smem) : blocks_per_sm<uint8_t, true, kStages>(smem);
+    return short_taps ? blocks_per_sm<float, true, kStages, true>(smem) : blocks_per_sm<float, true, kStages>(smem);
 }
 
 }  // namespace dd

@@ -11,12 +11,17 @@
 namespace dd {
 
 // Dedispersion kernel geometry (see dd_dedisp.cu): a CTA has kWarps warps; a warp
-// unit sums two adjacent trials (fp32 path) or one trial (exact integer path), and each
-// lane owns kR consecutive output samples.  kR is odd so that lane-strided
-// shared-memory reads hit distinct banks.
+// unit sums two adjacent trials (fp32 path) or one trial (exact integer and run-length
+// paths), and each lane owns R consecutive output samples: kRPair on the pair path
+// (packed accumulators and a duplicated window take 4 R registers), kRInt otherwise.
+// R is odd so that lane-strided shared-memory reads hit distinct banks.  A warp's time
+// chunk is 32 R outputs.
 constexpr int kWarps = 8;
-constexpr int kR = 31;
-constexpr int kTileT = 32 * kR;
+constexpr int kRPair = 27;
+constexpr int kRInt = 31;
+constexpr int kRMax = 31;
+__host__ __device__ constexpr int lane_r(bool pair) { return pair ? kRPair : kRInt; }
+__host__ __device__ constexpr int chunk_t(bool pair) { return 32 * lane_r(pair); }
 constexpr int kRlUnits = 3;                // trials per warp on the run-length path
 constexpr int kRlMinMeanTaps = 12;         // automatic run-length choice (uint8, unit weights)
 constexpr int kStages = 4;                 // bulk-copy pipeline depth
@@ -49,7 +54,7 @@ __host__ __device__ inline int dedisp_smem_bytes(const StageGeom& g, int nbuf, i
     return nbuf * g.bytes + ((4 * nchan + 15) & ~15) + nbuf * 8 + 2 * nbuf * 4;
 }
 // The output transpose reuses the stage buffers: one row of 32 * kR values per warp.
-constexpr int kStoreBytes = kWarps * 32 * kR * 4;
+constexpr int kStoreBytes = kWarps * 32 * kRMax * 4;
 
 // Arguments of one dedispersion launch (one plan, one input block); the batched
 // kernel keeps one per beam in device memory.
@@ -124,6 +129,7 @@ struct dd_plan_s {
     int32_t rec_bytes = 0;             // bytes of one stage's profile record
     bool pair = true;                  // fp32 path: each warp sums two adjacent trials
     int32_t kw = 0;                    // weight pairs per record entry (pair path)
+    int32_t umax = 0;                  // longest union window of a pair unit (pair path)
     std::vector<unsigned char> rec;    // host copy of the records
     bool rec_from_dev_w = false;       // records' weights come from dev.w (device weights)
     int32_t debug_skip_stage = -1;     // test hook: a stage whose bulk copies are never issued
@@ -161,10 +167,10 @@ void fill_dedisp_args(const dd_plan_s* p, const void* in, int64_t ld, int64_t t_
 size_t dedisp_smem_for(const dd_plan_s* p);
 dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
                                int64_t nsamp, void* out, int64_t out_ld, cudaStream_t s);
-dd_status launch_dedisperse_batched(bool u8, bool pair, const DedispArgs* d_args,
+dd_status launch_dedisperse_batched(bool u8, bool pair, bool short_taps, const DedispArgs* d_args,
                                     const BatchItem* d_items, int32_t nitems, int32_t* d_counter,
                                     size_t smem, int grid, cudaStream_t s);
-int dedisp_batched_blocks_per_sm(bool u8, bool pair, size_t smem);
+int dedisp_batched_blocks_per_sm(bool u8, bool pair, bool short_taps, size_t smem);
 dd_status cuda_status(cudaError_t e);
 
 // launchers (stream = cudaStream_t)

@@ -93,7 +93,7 @@ int stage_esz(const dd_plan_s* p) { return p->rl ? 4 : (p->band.in_type == DD_U8
 // alignment slack and the element that the register pipeline reads ahead.
 int64_t staged_len(const dd_plan_s* p, int nch, int64_t span) {
     const int64_t q = 16 / stage_esz(p);
-    int64_t need = (int64_t)nch * dd::kTileT + span + (p->rl ? 1 : 0) + q + 2;
+    int64_t need = (int64_t)nch * dd::chunk_t(p->pair) + span + (p->rl ? 1 : 0) + q + 2;
     return (need + q - 1) / q * q;
 }
 
@@ -182,7 +182,8 @@ dd_status build_schedule(dd_plan_s* p) {
             const int nu = dd::kWarps / nch * units_per_warp(p);
             const int db = tpw * nu;
             const int64_t span = block_span(p, db, nullptr);
-            const int32_t kw = p->pair ? ((union_taps(p, db) + 1) & ~1) : 0;
+            p->umax = p->pair ? union_taps(p, db) : 0;
+            const int32_t kw = p->pair ? ((p->umax + 1) & ~1) : 0;
             const int64_t need = staged_len(p, nch, span);
             if (need > (1 << 22)) continue;
             int cs = cs_want;
@@ -212,7 +213,8 @@ dd_status build_schedule_fixed(dd_plan_s* p, int nch, int cs) {
     const int nu = dd::kWarps / nch * units_per_warp(p);
     const int db = trials_per_unit(p) * nu;
     const int64_t span = block_span(p, db, nullptr);
-    const int32_t kw = p->pair ? ((union_taps(p, db) + 1) & ~1) : 0;
+    p->umax = p->pair ? union_taps(p, db) : 0;
+    const int32_t kw = p->pair ? ((p->umax + 1) & ~1) : 0;
     const int64_t need = staged_len(p, nch, span);
     if (need > (1 << 22)) return DD_ERR_UNSUPPORTED;
     if (dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu), dd::kStages,
@@ -581,7 +583,7 @@ dd_status dd_dedisperse(dd_plan_t p, const void* in, int64_t in_ld, int64_t t_of
     if (!aligned16(in) || (in_ld * esz) % 16 != 0) return DD_ERR_ARG;
     const int64_t t_out = nsamp - p->dmax;
     if (out_ld < t_out) return DD_ERR_ARG;
-    if (t_out > INT32_MAX - dd::kTileT || in_ld > (int64_t)1 << 40) return DD_ERR_OVERFLOW;
+    if (t_out > INT32_MAX - dd::chunk_t(false) * dd::kWarps || in_ld > (int64_t)1 << 40) return DD_ERR_OVERFLOW;
     if (p->rl && nsamp > ((int64_t)1 << 24)) return DD_ERR_UNSUPPORTED;
     dd_status st = dd::upload_tables(p);
     if (st != DD_OK) return st;

@@ -23,7 +23,7 @@
 struct dd_batch_s {
     std::vector<dd_plan_s*> plans;
     bool u8 = false, pair = true;
-    bool short_taps = true;  // every plan's union windows fit one register window
+    bool short_taps = true;  // every plan's tap runs (union windows) fit one register window
     std::vector<dd::BatchItem> items;
     size_t smem = 0;
     int grid = 0;
@@ -160,7 +160,8 @@ dd_status dd_batch_bind(dd_batch_t b, const void* const* d_in, const int64_t* in
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return dd::cuda_status(e);
     b->short_taps = true;
-    for (auto* p : b->plans) b->short_taps = b->short_taps && p->umax <= dd::kRPair;
+    for (auto* p : b->plans)
+        b->short_taps = b->short_taps && (p->pair ? p->umax <= dd::kRPair : p->kmax <= dd::kRInt);
     const int per_sm = dd::dedisp_batched_blocks_per_sm(b->u8, b->pair, b->short_taps, b->smem);
     if (per_sm < 1) return DD_ERR_UNSUPPORTED;
     b->grid = std::min<int>(per_sm * sms, (int)b->items.size());

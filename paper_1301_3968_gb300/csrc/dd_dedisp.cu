@@ -205,11 +205,12 @@ __device__ void issue_stage(const DedispArgs& a, const StageGeom& g, const Smem&
 }
 
 // One stage of one warp unit, exact integer sums of uint8 samples with unit weights:
-// for each of the stage's channels a register window of kR samples slides along the
-// taps.  At tap k output r reads window sample r + k, held in register (r + k) mod kR;
-// after the tap, sample k (no longer needed) is replaced by sample k + kR.  Each tap
-// costs one shared-memory load and kR adds.
-template <typename TIN>
+// for each of the stage's channels a register window of R samples slides along the
+// taps.  At tap k output r reads window sample r + k, held in register (r + k) mod R;
+// after the tap, sample k (no longer needed) is replaced by sample k + R.  Taps go two
+// at a time, one three-input add per output (the second tap's last output reads sample
+// R + k, loaded before the add).  SHORT: no tap run is longer than R, one unrolled pass.
+template <typename TIN, bool SHORT>
 __device__ __forceinline__ void stage_int(const TIN* rows, const int2* ent, const int* lo,
                                           int csn, int lcap, int bq, int lane_off,
                                           int (&acc)[kRInt]) {
@@ -223,13 +224,22 @@ __device__ __forceinline__ void stage_int(const TIN* rows, const int2* ent, cons
         int win[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) win[j] = (int)p[j];
-        for (int k0 = 0; k0 < n; k0 += R) {
+        for (int k0 = 0; k0 < (SHORT ? 1 : n); k0 += R) {
 #pragma unroll
-            for (int kk = 0; kk < R; ++kk) {
+            for (int kk = 0; kk < R; kk += 2) {
                 if (k0 + kk >= n) break;
+                if (kk + 1 < R && k0 + kk + 1 < n) {
+                    const int nk = (int)p[R + k0 + kk];
 #pragma unroll
-                for (int r = 0; r < R; ++r) acc[r] += win[(r + kk) % R];
-                win[kk] = (int)p[R + k0 + kk];
+                    for (int r = 0; r < R; ++r)
+                        acc[r] += win[(r + kk) % R] + (r == R - 1 ? nk : win[(r + kk + 1) % R]);
+                    win[kk] = nk;
+                    win[kk + 1] = (int)p[R + k0 + kk + 1];
+                } else {
+#pragma unroll
+                    for (int r = 0; r < R; ++r) acc[r] += win[(r + kk) % R];
+                    win[kk] = (int)p[R + k0 + kk];
+                }
             }
         }
     }
@@ -423,7 +433,7 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
                 stage_pair<TIN, SHORT>(rows, ent, wts, lo_all + c0, csn, a.lcap, a.kpad, bq,
                                        lane_off, accp);
             } else {
-                stage_int<TIN>(rows, ent, lo_all + c0, csn, a.lcap, bq, lane_off, acc0);
+                stage_int<TIN, SHORT>(rows, ent, lo_all + c0, csn, a.lcap, bq, lane_off, acc0);
             }
         }
         __syncwarp();
@@ -737,7 +747,8 @@ dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_
     a.nsplit = nsplit;
     a.split_ld = split_ld;
     const bool u8 = p->band.in_type == DD_U8;
-    if (!p->pair) return run<uint8_t, false, kStages>(a, s);
+    if (!p->pair)
+        return p->kmax <= kRInt ? run<uint8_t, false, kStages, true>(a, s) : run<uint8_t, false, kStages>(a, s);
     const bool short_taps = p->umax <= kRPair;
     if (u8) return short_taps ? run<uint8_t, true, kStages, true>(a, s) : run<uint8_t, true, kStages>(a, s);
     return short_taps ? run<float, true, kStages, true>(a, s) : run<float, true, kStages>(a, s);
@@ -768,7 +779,9 @@ dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t
 dd_status launch_dedisperse_batched(bool u8, bool pair, bool short_taps, const DedispArgs* d_args,
                                     const BatchItem* d_items, int32_t nitems, int32_t* d_counter,
                                     size_t smem, int grid, cudaStream_t s) {
-    if (!pair) return run_batched<uint8_t, false, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
+    if (!pair)
+        return short_taps ? run_batched<uint8_t, false, kStages, true>(d_args, d_items, nitems, d_counter, smem, grid, s)
+                          : run_batched<uint8_t, false, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
     if (u8)
         return short_taps ? run_batched<uint8_t, true, kStages, true>(d_args, d_items, nitems, d_counter, smem, grid, s)
                           : run_batched<uint8_t, true, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
@@ -777,7 +790,7 @@ dd_status launch_dedisperse_batched(bool u8, bool pair, bool short_taps, const D
 }
 
 int dedisp_batched_blocks_per_sm(bool u8, bool pair, bool short_taps, size_t smem) {
-    if (!pair) return blocks_per_sm<uint8_t, false, kStages>(smem);
+    if (!pair) return short_taps ? blocks_per_sm<uint8_t, false, kStages, true>(smem) : blocks_per_sm<uint8_t, false, kStages>(smem);
     if (u8) return short_taps ? blocks_per_sm<uint8_t, true, kStages, true>(smem) : blocks_per_sm<uint8_t, true, kStages>(smem);
     return short_taps ? blocks_per_sm<float, true, kStages, true>(smem) : blocks_per_sm<float, true, kStages>(smem);
 }

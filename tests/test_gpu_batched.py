@@ -123,3 +123,27 @@ def test_autotune_keeps_results_and_uses_cache(dd):
         plan2 = dd.Plan(band, dms)
         assert plan2.autotune(x, out, cache_path=path) == -1.0
         assert plan2.schedule() == sched
+
+
+def test_batched_long_taps_equals_per_beam(dd):
+    """A beam whose tap runs exceed one register window takes the general tap loop for
+    the whole batch; results still equal the per-beam launches and the oracle."""
+    import torch
+    beams = _beams(dd, n=3, seed=33)
+    plan, x, o, data = beams[1]
+    rng = np.random.default_rng(34)
+    D, C = plan.ndm, plan.band.nchan
+    delay = rng.integers(0, 200, size=(D, C)).astype(np.int32)
+    taps = rng.integers(1, 61, size=(D, C)).astype(np.int32)     # up to 60 > 31
+    plan.set_profiles(delay=delay, taps=taps)
+    plan.set_method("direct")
+    o2 = torch.zeros((D, plan.band.nsamp - plan.d_max), dtype=torch.int32, device="cuda")
+    beams[1] = (plan, x, o2, data)
+    batch = dd.Batch([p for p, _, _, _ in beams])
+    batch.bind([x for _, x, _, _ in beams], [o for _, _, o, _ in beams])
+    batch.dedisperse()
+    torch.cuda.synchronize()
+    for p, xb, ob, db in beams:
+        np.testing.assert_array_equal(ob.cpu().numpy(), p.dedisperse(xb, nsamp=p.band.nsamp).cpu().numpy())
+    want = oracle.c_dedisperse(data, delay, taps, nsamp=plan.band.nsamp, rows=[0, D - 1])
+    np.testing.assert_array_equal(o2.cpu().numpy()[[0, D - 1]].astype(np.int64), want)

@@ -58,8 +58,9 @@ def craft_workload(dd, dev, ndm=None):
     b = cfg["band"]
     band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, cfg["nsamp"], "f32")
     dms, eps = dd.trial_dms(band, 0.0, cfg["dm_max"], cfg["ndm"], tau_av_ms=1.0)
-    if ndm:   # a smaller profiling case: every k-th trial of the same list
-        dms = dms[:: max(1, len(dms) // ndm)][:ndm]
+    if ndm:   # a smaller profiling case: a contiguous block from the middle of the list
+        m = max(0, len(dms) // 2 - ndm // 2)
+        dms = dms[m:m + ndm]
     plan = dd.Plan(band, dms)
     delay, taps = plan.tables()
     K = int(taps.max())
@@ -404,16 +405,17 @@ def batched_extra(dd, dev, flush, stream, reps=3):
     }
 
 
-def large_extra(dd, dev, flush, stream, chunk=1 << 18):
+def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192):
     """Large low-band configuration: 1024 ch over 700-1000 MHz, dt 64 us, 2^20 uint8
     samples, 8192 trial DMs 0-2000 (unit weights, run-length sums), streamed in
     overlapping chunks of `chunk` outputs (each chunk reads its outputs plus d_max
     samples), int32 out, then boxcar S/N over widths 1-256 per chunk."""
     import torch
     import synth
-    cfg = synth.make_large()
+    cfg = synth.make_large(nsamp=nsamp)
     b, T = cfg["band"], cfg["nsamp"]
-    plan = dd.Plan(dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, T, "u8"), cfg["dms"])
+    dms = cfg["dms"] if ndm == len(cfg["dms"]) else np.linspace(0.0, cfg["dms"][-1], ndm)
+    plan = dd.Plan(dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, T, "u8"), dms)
     x = torch.from_numpy(cfg["data"]).to(dev)
     dmax = plan.d_max
     t_out = T - dmax
@@ -588,6 +590,26 @@ def run_reference(args):
     }
 
 
+def run_only(args):
+    """One extra measurement alone (rank 0, no headline step): for profiling a kernel of
+    that configuration."""
+    import torch
+    import paper_1301_3968_gb300 as dd
+    from paper_1301_3968_gb300 import build as dd_build
+    dd_build.build()
+    dev = torch.device("cuda", 0)
+    torch.cuda.set_device(dev)
+    flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
+    stream = torch.cuda.current_stream()
+    if args.only == "fwd_bwd":
+        r = diff_extra(dd, dev, flush, stream)
+    elif args.only == "batched":
+        r = batched_extra(dd, dev, flush, stream)
+    else:
+        r = large_extra(dd, dev, flush, stream, nsamp=args.large_nsamp, ndm=args.large_ndm)
+    return {"only": args.only, **r}
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -597,14 +619,21 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--cpu-seconds", type=float, default=12.0)
     ap.add_argument("--ndm", type=int, default=None,
-                    help="trial count override (profiling on a smaller case); default 4096")
+                    help="profiling case: this many consecutive trials from the middle of the "
+                         "4096-trial list")
     ap.add_argument("--no-e2e", action="store_true")
+    ap.add_argument("--only", default=None, choices=["fwd_bwd", "batched", "large_lowband"],
+                    help="run one extra measurement alone (profiling)")
+    ap.add_argument("--large-nsamp", type=int, default=1 << 20)
+    ap.add_argument("--large-ndm", type=int, default=8192)
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the forward+backward, batched-beam and large low-band measurements")
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per dedispersion launch from an ncu capture")
     args = ap.parse_args()
-    if args.impl == "reference":
+    if args.only:
+        res = run_only(args)
+    elif args.impl == "reference":
         res = run_reference(args)
     else:
         res = run_gpu(args)

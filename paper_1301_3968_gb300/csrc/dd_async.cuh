@@ -1,0 +1,23 @@
+// Asynchronous global -> shared copies (cp.async, 4 bytes per thread and copy) for the
+// kernels that stage irregularly aligned rows one element at a time.  A copy with
+// ok == false writes zeros and reads nothing.
+#pragma once
+
+#include <cstdint>
+
+namespace dd {
+
+__device__ __forceinline__ void cp_async4(void* dst, const void* src, bool ok) {
+    asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(ok ? 4 : 0)
+                 : "memory");
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }
+// Waits until at most N of this thread's committed groups are still in flight.
+template <int N>
+__device__ __forceinline__ void cp_async_wait() {
+    asm volatile("cp.async.wait_group %0;\n" ::"n"(N) : "memory");
+}
+
+}  // namespace dd

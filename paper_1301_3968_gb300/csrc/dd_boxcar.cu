@@ -11,6 +11,7 @@
 #include <algorithm>
 #include <cstdint>
 
+#include "dd_async.cuh"
 #include "dd_internal.h"
 
 namespace dd {
@@ -359,17 +360,20 @@ __device__ __forceinline__ typename Acc<TB>::U to_acc(TX v) {
     return (U)(TB)v;
 }
 
+// xl: the thread's staged samples (raw series values); o: the trial's offset, taken
+// off each sample as it is read.
 template <typename TX, typename TB, bool FULL>
-__device__ __forceinline__ void run_segment(const TX* xl, int w0, int t0, int t_len, TB (&seg)[kBoxG]) {
+__device__ __forceinline__ void run_segment(const TX* xl, TX o, int w0, int t0, int t_len,
+                                            TB (&seg)[kBoxG]) {
     constexpr int S = kBoxS, G = kBoxG;
     using U = typename Acc<TB>::U;
     U p = U(0);
     U q = U(0);
-    for (int k = 0; k < w0; ++k) q += to_acc<TX, TB>(xl[k]);
+    for (int k = 0; k < w0; ++k) q += to_acc<TX, TB>((TX)(xl[k] - o));
     U win[G];
     win[0] = q;
 #pragma unroll
-    for (int j = 1; j < G; ++j) win[j] = win[j - 1] + to_acc<TX, TB>(xl[w0 + j - 1]);
+    for (int j = 1; j < G; ++j) win[j] = win[j - 1] + to_acc<TX, TB>((TX)(xl[w0 + j - 1] - o));
 #pragma unroll
     for (int s = 0; s < S; ++s) {
 #pragma unroll
@@ -378,8 +382,8 @@ __device__ __forceinline__ void run_segment(const TX* xl, int w0, int t0, int t_
             if (!FULL) v = (t0 + s + w0 + j <= t_len) ? v : lowest<TB>();
             seg[j] = max(seg[j], v);
         }
-        p += to_acc<TX, TB>(xl[s]);
-        win[s % G] = win[(s + G - 1) % G] + to_acc<TX, TB>(xl[s + w0 + G - 1]);
+        p += to_acc<TX, TB>((TX)(xl[s] - o));
+        win[s % G] = win[(s + G - 1) % G] + to_acc<TX, TB>((TX)(xl[s + w0 + G - 1] - o));
     }
 }
 
@@ -388,7 +392,6 @@ __global__ void __launch_bounds__(256) k_boxcar_run(BoxArgs a) {
     constexpr int S = kBoxS, G = kBoxG;
     using U = typename Acc<TB>::U;
     extern __shared__ __align__(16) unsigned char smem_raw[];
-    TX* xs = (TX*)smem_raw;
     __shared__ TB rb[8][G];
     __shared__ int rc[8][G];
     __shared__ int rt[8][G];
@@ -397,6 +400,12 @@ __global__ void __launch_bounds__(256) k_boxcar_run(BoxArgs a) {
     const int cnt = min(G, a.nw - j0);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
     const int w0 = a.widths[j0];
+    const int w0_last = a.widths[((a.nw - 1) / G) * G];
+    // two chunk buffers (sized for the launch's last width group): the next chunk's
+    // copies are in flight while the current one is scanned
+    const int bufl = (256 * S + w0_last + G + 3) & ~3;
+    TX* const xs0 = (TX*)smem_raw;
+    TX* const xs1 = xs0 + bufl;
     const int wlast = w0 + cnt - 1;
     const TX o = (TX)a.off[d];
     const TX* xrow = (const TX*)a.x + (int64_t)d * a.ld;
@@ -411,20 +420,33 @@ __global__ void __launch_bounds__(256) k_boxcar_run(BoxArgs a) {
     const int chunk = 256 * S;
     const int stage = chunk + w0 + G;
     const int ls = tid * S;
-    for (int ci = 0, tc = 0; tc < tvalid; ++ci, tc += chunk) {
-        __syncthreads();
+    // past the end of the row the buffer holds zeros; only windows that run past the
+    // series end read them, and those are excluded
+    auto load = [&](int tc, TX* dst) {
         for (int i = tid; i < stage; i += 256) {
             const int t = tc + i;
-            xs[i] = t < a.t_len ? (TX)(xrow[t] - o) : TX(0);
+            const bool ok = t < a.t_len;
+            cp_async4(dst + i, ok ? xrow + t : xrow, ok);
+        }
+        cp_async_commit();
+    };
+    load(0, xs0);
+    for (int ci = 0, tc = 0; tc < tvalid; ++ci, tc += chunk) {
+        TX* const xs = (ci & 1) ? xs1 : xs0;
+        if (tc + chunk < tvalid) {
+            load(tc + chunk, (ci & 1) ? xs0 : xs1);
+            cp_async_wait<1>();
+        } else {
+            cp_async_wait<0>();
         }
         __syncthreads();
         TB seg[G];
 #pragma unroll
         for (int j = 0; j < G; ++j) seg[j] = lowest<TB>();
         if (tc + chunk - 1 + wlast <= a.t_len)
-            run_segment<TX, TB, true>(xs + ls, w0, tc + ls, a.t_len, seg);
+            run_segment<TX, TB, true>(xs + ls, o, w0, tc + ls, a.t_len, seg);
         else if (tc + ls < tvalid)
-            run_segment<TX, TB, false>(xs + ls, w0, tc + ls, a.t_len, seg);
+            run_segment<TX, TB, false>(xs + ls, o, w0, tc + ls, a.t_len, seg);
 #pragma unroll
         for (int j = 0; j < G; ++j) {
             if (seg[j] > best[j]) {
@@ -432,6 +454,7 @@ __global__ void __launch_bounds__(256) k_boxcar_run(BoxArgs a) {
                 bch[j] = ci;
             }
         }
+        __syncthreads();  // this buffer is reloaded by the next iteration but one
     }
     // (max, earliest chunk, earliest thread) over the CTA
 #pragma unroll
@@ -510,7 +533,7 @@ __global__ void __launch_bounds__(256) k_boxcar_run(BoxArgs a) {
 
 template <typename TX, typename TB>
 dd_status run_boxcar_contig(const BoxArgs& a, int w0_last, cudaStream_t s) {
-    const size_t smem = (size_t)(256 * kBoxS + w0_last + kBoxG) * sizeof(TX);
+    const size_t smem = (size_t)2 * ((256 * kBoxS + w0_last + kBoxG + 3) & ~3) * sizeof(TX);
     auto kern = k_boxcar_run<TX, TB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);

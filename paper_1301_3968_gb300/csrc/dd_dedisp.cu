@@ -733,10 +733,10 @@ void fill_dedisp_args(const dd_plan_s* p, const void* in, int64_t ld, int64_t t_
 
 size_t dedisp_smem_for(const dd_plan_s* p) {
     const int kp = p->pair ? p->kw : 0;
-    if (p->rl) return smem_for<uint32_t, false, kStages>(p->lcap, 0, p->cs, p->nch, p->nchan);
-    if (!p->pair) return smem_for<uint8_t, false, kStages>(p->lcap, kp, p->cs, p->nch, p->nchan);
-    if (p->band.in_type == DD_U8) return smem_for<uint8_t, true, kStages>(p->lcap, kp, p->cs, p->nch, p->nchan);
-    return smem_for<float, true, kStages>(p->lcap, kp, p->cs, p->nch, p->nchan);
+    if (p->rl) return smem_for<uint32_t, false, kStagesRl>(p->lcap, 0, p->cs, p->nch, p->nchan);
+    if (!p->pair) return smem_for<uint8_t, false, kStagesInt>(p->lcap, kp, p->cs, p->nch, p->nchan);
+    if (p->band.in_type == DD_U8) return smem_for<uint8_t, true, kStagesPair>(p->lcap, kp, p->cs, p->nch, p->nchan);
+    return smem_for<float, true, kStagesPair>(p->lcap, kp, p->cs, p->nch, p->nchan);
 }
 
 dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
@@ -748,10 +748,10 @@ dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_
     a.split_ld = split_ld;
     const bool u8 = p->band.in_type == DD_U8;
     if (!p->pair)
-        return p->kmax <= kRInt ? run<uint8_t, false, kStages, true>(a, s) : run<uint8_t, false, kStages>(a, s);
+        return p->kmax <= kRInt ? run<uint8_t, false, kStagesInt, true>(a, s) : run<uint8_t, false, kStagesInt>(a, s);
     const bool short_taps = p->umax <= kRPair;
-    if (u8) return short_taps ? run<uint8_t, true, kStages, true>(a, s) : run<uint8_t, true, kStages>(a, s);
-    return short_taps ? run<float, true, kStages, true>(a, s) : run<float, true, kStages>(a, s);
+    if (u8) return short_taps ? run<uint8_t, true, kStagesPair, true>(a, s) : run<uint8_t, true, kStagesPair>(a, s);
+    return short_taps ? run<float, true, kStagesPair, true>(a, s) : run<float, true, kStagesPair>(a, s);
 }
 
 // Run-length path: prefix sums of columns t_offset .. t_offset + nsamp - 1 into the
@@ -773,26 +773,26 @@ dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t
     if (e != cudaSuccess) return cuda_status(e);
     DedispArgs a;
     fill_dedisp_args(p, p->d_prefix, ldp, 0, nsamp - p->dmax, out, out_ld, &a);
-    return run<uint32_t, false, kStages>(a, s);
+    return run<uint32_t, false, kStagesRl>(a, s);
 }
 
 dd_status launch_dedisperse_batched(bool u8, bool pair, bool short_taps, const DedispArgs* d_args,
                                     const BatchItem* d_items, int32_t nitems, int32_t* d_counter,
                                     size_t smem, int grid, cudaStream_t s) {
     if (!pair)
-        return short_taps ? run_batched<uint8_t, false, kStages, true>(d_args, d_items, nitems, d_counter, smem, grid, s)
-                          : run_batched<uint8_t, false, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
+        return short_taps ? run_batched<uint8_t, false, kStagesInt, true>(d_args, d_items, nitems, d_counter, smem, grid, s)
+                          : run_batched<uint8_t, false, kStagesInt>(d_args, d_items, nitems, d_counter, smem, grid, s);
     if (u8)
-        return short_taps ? run_batched<uint8_t, true, kStages, true>(d_args, d_items, nitems, d_counter, smem, grid, s)
-                          : run_batched<uint8_t, true, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
-    return short_taps ? run_batched<float, true, kStages, true>(d_args, d_items, nitems, d_counter, smem, grid, s)
-                      : run_batched<float, true, kStages>(d_args, d_items, nitems, d_counter, smem, grid, s);
+        return short_taps ? run_batched<uint8_t, true, kStagesPair, true>(d_args, d_items, nitems, d_counter, smem, grid, s)
+                          : run_batched<uint8_t, true, kStagesPair>(d_args, d_items, nitems, d_counter, smem, grid, s);
+    return short_taps ? run_batched<float, true, kStagesPair, true>(d_args, d_items, nitems, d_counter, smem, grid, s)
+                      : run_batched<float, true, kStagesPair>(d_args, d_items, nitems, d_counter, smem, grid, s);
 }
 
 int dedisp_batched_blocks_per_sm(bool u8, bool pair, bool short_taps, size_t smem) {
-    if (!pair) return short_taps ? blocks_per_sm<uint8_t, false, kStages, true>(smem) : blocks_per_sm<uint8_t, false, kStages>(smem);
-    if (u8) return short_taps ? blocks_per_sm<uint8_t, true, kStages, true>(smem) : blocks_per_sm<uint8_t, true, kStages>(smem);
-    return short_taps ? blocks_per_sm<float, true, kStages, true>(smem) : blocks_per_sm<float, true, kStages>(smem);
+    if (!pair) return short_taps ? blocks_per_sm<uint8_t, false, kStagesInt, true>(smem) : blocks_per_sm<uint8_t, false, kStagesInt>(smem);
+    if (u8) return short_taps ? blocks_per_sm<uint8_t, true, kStagesPair, true>(smem) : blocks_per_sm<uint8_t, true, kStagesPair>(smem);
+    return short_taps ? blocks_per_sm<float, true, kStagesPair, true>(smem) : blocks_per_sm<float, true, kStagesPair>(smem);
 }
 
 }  // namespace dd

@@ -24,7 +24,13 @@ __host__ __device__ constexpr int lane_r(bool pair) { return pair ? kRPair : kRI
 __host__ __device__ constexpr int chunk_t(bool pair) { return 32 * lane_r(pair); }
 constexpr int kRlUnits = 3;                // trials per warp on the run-length path
 constexpr int kRlMinMeanTaps = 12;         // automatic run-length choice (uint8, unit weights)
-constexpr int kStages = 4;                 // bulk-copy pipeline depth
+// Bulk-copy pipeline depth (buffers in the ring) per path: the pair and run-length paths
+// do more work per staged channel and gain more from large stages (up to kCsMax channels)
+// than from depth; the integer path's stages are small and it keeps four in flight.
+constexpr int kStagesPair = 2;
+constexpr int kStagesRl = 2;
+constexpr int kStagesInt = 4;
+constexpr int kCsMax = 8;
 constexpr int kStagesMax = 8;
 constexpr int kSmemBudget = 110 * 1024;    // dynamic shared memory per CTA (two per SM)
 constexpr int kSmemBudgetOne = 220 * 1024; // fallback: one CTA per SM

@@ -84,6 +84,11 @@ int trials_per_unit(const dd_plan_s* p) { return p->pair ? 2 : 1; }
 // register window, so more trials share each staged prefix row).
 int units_per_warp(const dd_plan_s* p) { return p->rl ? dd::kRlUnits : 1; }
 
+// Buffers in the staging ring of the plan's path.
+int stages_of(const dd_plan_s* p) {
+    return p->rl ? dd::kStagesRl : (p->pair ? dd::kStagesPair : dd::kStagesInt);
+}
+
 // Staged element size and elements per 16-byte chunk: uint8 samples, fp32 samples, or
 // uint32 prefix sums on the run-length path.
 int stage_esz(const dd_plan_s* p) { return p->rl ? 4 : (p->band.in_type == DD_U8 ? 1 : 4); }
@@ -171,7 +176,8 @@ dd_status build_schedule(dd_plan_s* p) {
             (p->method == DD_METHOD_RUNLENGTH ||
              (p->method == DD_METHOD_AUTO && mean_taps >= dd::kRlMinMeanTaps));
     const int esz = stage_esz(p);
-    const int cs_want = esz == 1 ? 8 : 4;
+    const int cs_want = dd::kCsMax;
+    const int nbuf = stages_of(p);
     const int tpw = trials_per_unit(p);
     // first pass: shared memory for two CTAs per SM and at least two channels per
     // stage; second pass: one CTA per SM, any stage size
@@ -189,7 +195,7 @@ dd_status build_schedule(dd_plan_s* p) {
             int cs = cs_want;
             while (cs >= min_cs[pass] &&
                    dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu),
-                                         dd::kStages, p->nchan) > budgets[pass])
+                                         nbuf, p->nchan) > budgets[pass])
                 --cs;
             if (cs < min_cs[pass]) continue;
             p->nch = nch;
@@ -217,7 +223,7 @@ dd_status build_schedule_fixed(dd_plan_s* p, int nch, int cs) {
     const int32_t kw = p->pair ? ((p->umax + 1) & ~1) : 0;
     const int64_t need = staged_len(p, nch, span);
     if (need > (1 << 22)) return DD_ERR_UNSUPPORTED;
-    if (dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu), dd::kStages,
+    if (dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu), stages_of(p),
                               p->nchan) > dd::kSmemBudgetOne)
         return DD_ERR_UNSUPPORTED;
     p->nch = nch;

@@ -30,7 +30,7 @@ constexpr int kRlMinMeanTaps = 12;         // automatic run-length choice (uint8
 constexpr int kStagesPair = 2;
 constexpr int kStagesRl = 2;
 constexpr int kStagesInt = 4;
-constexpr int kCsMax = 8;
+constexpr int kCsMax = 12;
 constexpr int kStagesMax = 8;
 constexpr int kSmemBudget = 110 * 1024;    // dynamic shared memory per CTA (two per SM)
 constexpr int kSmemBudgetOne = 220 * 1024; // fallback: one CTA per SM

@@ -289,6 +289,59 @@ def adjoint(I, g, delays, taps, w, t_offset=0, nsamp=None):
     return gw, gI
 
 
+def dedisperse_points(I, delays, taps, points, w=None, t_offset=0):
+    """eq. p_dedisp at chosen outputs only: out[d][t] for each (d, t) in `points`, summed
+    over channels and taps as in `dedisperse` (int64 for uint8 input without weights,
+    float64 otherwise).  For full-size checks where whole rows are too costly."""
+    I = np.asarray(I)
+    delays = np.asarray(delays, np.int64)
+    taps = np.asarray(taps, np.int64)
+    D, C = delays.shape
+    integer = w is None and np.issubdtype(I.dtype, np.integer)
+    res = []
+    for d, t in points:
+        acc = 0 if integer else 0.0
+        for c in range(C):
+            s = t_offset + int(t) + int(delays[d, c])
+            n = int(taps[d, c])
+            seg = I[c, s:s + n]
+            if w is None:
+                acc += int(seg.astype(np.int64).sum()) if integer else float(seg.astype(np.float64).sum())
+            else:
+                acc += float(np.dot(np.asarray(w[d, c, :n], np.float32).astype(np.float64),
+                                    seg.astype(np.float64)))
+        res.append(acc)
+    return np.array(res, dtype=np.int64 if integer else np.float64)
+
+
+def adjoint_points(I, g, delays, taps, w, gw_points=(), gi_points=(), t_offset=0):
+    """The adjoint of `adjoint` at chosen entries: gw[d][c][k] for (d, c, k) in gw_points
+    and gI[c][τ] for (c, τ) in gi_points, each summed directly from its definition."""
+    I = np.asarray(I)
+    g = np.asarray(g, np.float64)
+    delays = np.asarray(delays, np.int64)
+    taps = np.asarray(taps, np.int64)
+    D, C = delays.shape
+    t_out = g.shape[1]
+    gw = []
+    for d, c, k in gw_points:
+        if k >= taps[d, c]:
+            gw.append(0.0)
+            continue
+        s = t_offset + int(delays[d, c]) + int(k)
+        gw.append(float(np.dot(g[d], I[c, s:s + t_out].astype(np.float64))))
+    gi = []
+    for c, tau in gi_points:
+        acc = 0.0
+        for d in range(D):
+            for k in range(int(taps[d, c])):
+                t = int(tau) - t_offset - int(delays[d, c]) - k
+                if 0 <= t < t_out:
+                    acc += float(np.float32(w[d, c, k])) * g[d, t]
+        gi.append(acc)
+    return np.array(gw), np.array(gi)
+
+
 def dsmf_snr(pbar, sigma):
     """Dynamic-spectrum matched filter S/N √(Σ P̄²)/σ (Sec. 5) for cell noise σ."""
     return math.sqrt(float((np.asarray(pbar, np.float64) ** 2).sum())) / sigma

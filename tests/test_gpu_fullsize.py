@@ -1,0 +1,115 @@
+"""Parity at the full sizes of the measured configurations, in the launch configuration
+bench.py times, on outputs the oracle computes one by one (sampled rows or points)."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ref
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dd():
+    import torch
+    from paper_1301_3968_gb300 import build
+    build.build()
+    import paper_1301_3968_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def test_batched_36_beams_full_size(dd):
+    """36 beams of 2^14-2^17 samples and 512-8192 trials, uint8 -> int32, one persistent
+    launch: three rows of every beam bit-exact against the oracle."""
+    import torch
+    cfg = synth.make_batched_beams()
+    b = cfg["band"]
+    plans, xs, outs, datas = [], [], [], []
+    for beam in cfg["beams"]:
+        band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, beam["nsamp"], "u8")
+        dms, _ = dd.trial_dms(band, 0.0, beam["dm_max"], beam["ndm"], tau_av_ms=1.0)
+        plan = dd.Plan(band, dms)
+        data = synth.make_beam_data(beam)
+        plans.append(plan)
+        datas.append(data)
+        xs.append(_dev(data))
+        outs.append(torch.empty((len(dms), beam["nsamp"] - plan.d_max), dtype=torch.int32, device="cuda"))
+    batch = dd.Batch(plans)
+    batch.bind(xs, outs)
+    batch.dedisperse()
+    torch.cuda.synchronize()
+    rng = np.random.default_rng(81)
+    for plan, data, o in zip(plans, datas, outs):
+        rows = sorted(set([0, plan.ndm - 1, int(rng.integers(plan.ndm))]))
+        delay, taps = plan.tables()
+        want = oracle.c_dedisperse(data, delay, taps, nsamp=plan.band.nsamp, rows=rows)
+        np.testing.assert_array_equal(o[rows].cpu().numpy().astype(np.int64), want)
+    batch.close()
+
+
+def test_large_lowband_full_size_streamed(dd):
+    """2^20 uint8 samples, 8192 trials to DM 2000, run-length sums in 4 overlapping chunks
+    of 2^18 outputs (as bench.py streams them): 96 sampled outputs bit-exact."""
+    import torch
+    cfg = synth.make_large()
+    b, T = cfg["band"], cfg["nsamp"]
+    plan = dd.Plan(dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, T, "u8"), cfg["dms"])
+    assert plan.method == "runlength"
+    x = _dev(cfg["data"])
+    dmax = plan.d_max
+    t_out = T - dmax
+    chunk = 1 << 18
+    out = torch.empty((plan.ndm, chunk), dtype=torch.int32, device="cuda")
+    delay, taps = plan.tables()
+    rng = np.random.default_rng(82)
+    for t0 in range(0, t_out, chunk):
+        n = min(chunk, t_out - t0)
+        plan.dedisperse(x, t_offset=t0, nsamp=n + dmax, out=out)
+        pts = [(int(rng.integers(plan.ndm)), int(rng.integers(n))) for _ in range(24)]
+        pts[0] = (plan.ndm - 1, n - 1)                # the last output of the chunk
+        got = out.cpu().numpy()[[p[0] for p in pts], [p[1] for p in pts]]
+        want = ref.dedisperse_points(cfg["data"], delay, taps, pts, t_offset=t0)
+        np.testing.assert_array_equal(got.astype(np.int64), want)
+
+
+def test_differentiable_full_size_gradients(dd):
+    """336 channels, 16384 fp32 samples, 1024 trials, 32 learnable taps: forward rows and
+    sampled weight and input gradients through the adjoint kernels against the oracle
+    within the 1e-5 scale-aware bound."""
+    import torch
+    cfg = synth.make_diff(npulse=0)
+    b, T, D, K = cfg["band"], cfg["nsamp"], 1024, 32
+    band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, T, "f32")
+    dms, _ = dd.trial_dms(band, 0.0, 2000.0, D, tau_av_ms=1.0)
+    plan = dd.Plan(band, dms)
+    delay, taps0 = plan.tables()
+    rng = np.random.default_rng(83)
+    taps = np.full_like(taps0, K)
+    w = rng.uniform(0.5, 1.5, size=(D, b.nchan, K)).astype(np.float32)
+    plan.set_profiles(delay=delay, taps=taps, weights=w)
+    I = cfg["data"]
+    x = _dev(I)
+    out = plan.dedisperse(x, nsamp=T).cpu().numpy()
+    rows = [0, 511, 1023]
+    want = oracle.c_dedisperse(I, delay, taps, w=w, nsamp=T, rows=rows)
+    scale = oracle.c_abs_scale(I, delay, taps, w=w, nsamp=T, rows=rows)
+    assert (np.abs(out[rows] - want) <= 1e-5 * scale + 1e-30).all()
+    t_out = out.shape[1]
+    g = rng.standard_normal((D, t_out)).astype(np.float32)
+    gw, gI = plan.backward(x, _dev(g), nsamp=T)
+    gw, gI = gw.cpu().numpy(), gI.cpu().numpy()
+    gwp = [(int(rng.integers(D)), int(rng.integers(b.nchan)), int(rng.integers(K))) for _ in range(48)]
+    gip = [(int(rng.integers(b.nchan)), int(rng.integers(T))) for _ in range(24)]
+    a, bI = ref.adjoint_points(I, g, delay, taps, w, gwp, gip)
+    sa, sb = ref.adjoint_points(np.abs(I), np.abs(g), delay, taps, np.abs(w), gwp, gip)
+    got_w = np.array([gw[d, c, k] for d, c, k in gwp])
+    got_i = np.array([gI[c, t] for c, t in gip])
+    assert (np.abs(got_w - a) <= 1e-5 * sa + 1e-30).all()
+    assert (np.abs(got_i - bI) <= 1e-5 * sb + 1e-30).all()

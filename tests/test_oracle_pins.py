@@ -417,3 +417,29 @@ def test_adjoint_identities():
     gw_c, gI_c = oracle.c_adjoint(I, g.astype(np.float32), dl, tp, w)
     np.testing.assert_allclose(gw_c, gw, rtol=1e-12, atol=1e-10)
     np.testing.assert_allclose(gI_c, gI, rtol=1e-12, atol=1e-10)
+
+
+def test_point_evaluations_match_full_oracle():
+    """The point-wise forms used for full-size checks agree with the full sums: uint8
+    exactly, float to rounding, and the adjoint points with `adjoint`."""
+    rng = np.random.default_rng(77)
+    C, T, D, K = 9, 400, 5, 7
+    I8 = rng.integers(0, 256, size=(C, T)).astype(np.uint8)
+    If = rng.standard_normal((C, T)).astype(np.float32)
+    delay = rng.integers(0, 60, size=(D, C))
+    taps = rng.integers(1, K + 1, size=(D, C))
+    w = rng.standard_normal((D, C, K)).astype(np.float32)
+    full8 = ref.dedisperse(I8, delay, taps, t_offset=3)
+    fullf = ref.dedisperse(If, delay, taps, w=w, t_offset=3)
+    pts = [(int(rng.integers(D)), int(rng.integers(full8.shape[1]))) for _ in range(25)]
+    np.testing.assert_array_equal(ref.dedisperse_points(I8, delay, taps, pts, t_offset=3),
+                                  [full8[d, t] for d, t in pts])
+    np.testing.assert_allclose(ref.dedisperse_points(If, delay, taps, pts, w=w, t_offset=3),
+                               [fullf[d, t] for d, t in pts], rtol=1e-12, atol=1e-12)
+    g = rng.standard_normal((D, fullf.shape[1]))
+    gw, gI = ref.adjoint(If, g, delay, taps, w, t_offset=3)
+    gwp = [(int(rng.integers(D)), int(rng.integers(C)), int(rng.integers(K))) for _ in range(20)]
+    gip = [(int(rng.integers(C)), int(rng.integers(T))) for _ in range(20)]
+    a, b = ref.adjoint_points(If, g, delay, taps, w, gwp, gip, t_offset=3)
+    np.testing.assert_allclose(a, [gw[d, c, k] for d, c, k in gwp], rtol=1e-12, atol=1e-12)
+    np.testing.assert_allclose(b, [gI[c, t] for c, t in gip], rtol=1e-12, atol=1e-12)

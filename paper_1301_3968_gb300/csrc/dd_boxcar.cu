@@ -199,6 +199,10 @@ struct BoxArgs {
     dd_candidate* cands;
     int32_t cap;
     int32_t* ncands;
+    // rows taken by this launch: all (narrow == nullptr), or those whose flag narrow[d]
+    // equals narrow_sel (the int32 launch takes the flagged rows, the int64 one the rest)
+    const uint8_t* narrow;
+    int32_t narrow_sel;
 };
 
 template <typename T>
@@ -396,6 +400,7 @@ __global__ void __launch_bounds__(256) k_boxcar_run(BoxArgs a) {
     __shared__ int rc[8][G];
     __shared__ int rt[8][G];
     const int d = blockIdx.y;
+    if (a.narrow && (int)a.narrow[d] != a.narrow_sel) return;
     const int j0 = blockIdx.x * G;
     const int cnt = min(G, a.nw - j0);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
@@ -558,8 +563,31 @@ dd_status run_boxcar(const BoxArgs& a, int wmax_all, cudaStream_t s) {
 }  // namespace
 
 // Series type and sum type, and the contiguous-width kernel when w_j = w_0 + j.
+// Per-row bound for integer series: narrow[d] = 1 when wmax * max_t |x[d][t] - o_d| < 2^31,
+// i.e. when every boxcar sum of the row fits int32 (one read of the series).
+__global__ void __launch_bounds__(256) k_row_narrow(const int* x, int64_t ld, int32_t t_len,
+                                                    const double* off, int32_t wmax, uint8_t* narrow) {
+    const int d = blockIdx.x;
+    const int* row = x + (int64_t)d * ld;
+    const long long o = (long long)off[d];
+    long long m = 0;
+    for (int t = threadIdx.x; t < t_len; t += blockDim.x) {
+        const long long v = (long long)row[t] - o;
+        m = max(m, v < 0 ? -v : v);
+    }
+#pragma unroll
+    for (int ofs = 16; ofs > 0; ofs >>= 1) m = max(m, (long long)__shfl_xor_sync(0xffffffffu, m, ofs));
+    __shared__ long long wm[8];
+    if ((threadIdx.x & 31) == 0) wm[threadIdx.x >> 5] = m;
+    __syncthreads();
+    if (threadIdx.x == 0) {
+        for (int i = 1; i < 8; ++i) m = max(m, wm[i]);
+        narrow[d] = (uint8_t)(m * (long long)wmax < (long long)INT_MAX ? 1 : 0);
+    }
+}
+
 static dd_status dispatch_boxcar(const dd_plan_s* p, const BoxArgs& a, const int32_t* widths,
-                                 int32_t nw, cudaStream_t s) {
+                                 int32_t nw, cudaStream_t s, bool split_rows) {
     const int wmax = widths[nw - 1];
     bool contig = true;
     for (int j = 1; j < nw; ++j) contig = contig && widths[j] == widths[0] + j;
@@ -571,7 +599,20 @@ static dd_status dispatch_boxcar(const dd_plan_s* p, const BoxArgs& a, const int
     const long long bound = (long long)wmax * p->max_abs_row;
     if (bound < (long long)INT_MAX)
         return contig ? run_boxcar_contig<int, int>(a, w0_last, s) : run_boxcar<int, int>(a, wmax, s);
-    return contig ? run_boxcar_contig<int, long long>(a, w0_last, s) : run_boxcar<int, long long>(a, wmax, s);
+    if (!contig || !split_rows || !p->dev.narrow)
+        return contig ? run_boxcar_contig<int, long long>(a, w0_last, s) : run_boxcar<int, long long>(a, wmax, s);
+    // the plan-wide bound needs int64, but rows of noise-like series rarely do: measure
+    // each row, sum the narrow ones in int32 and only the rest in int64
+    k_row_narrow<<<a.ndm, 256, 0, s>>>((const int*)a.x, a.ld, a.t_len, a.off, wmax, p->dev.narrow);
+    cudaError_t e = cudaGetLastError();
+    if (e != cudaSuccess) return cuda_status(e);
+    BoxArgs a32 = a, a64 = a;
+    a32.narrow = a64.narrow = p->dev.narrow;
+    a32.narrow_sel = 1;
+    a64.narrow_sel = 0;
+    dd_status st = run_boxcar_contig<int, int>(a32, w0_last, s);
+    if (st != DD_OK) return st;
+    return run_boxcar_contig<int, long long>(a64, w0_last, s);
 }
 
 dd_status launch_channel_stats(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
@@ -588,14 +629,17 @@ static dd_status ensure_norm_ws(dd_plan_s* p, int nw) {
     cudaFree(p->dev.mu);
     cudaFree(p->dev.isd);
     cudaFree(p->dev.widths);
+    cudaFree(p->dev.narrow);
     p->widths_on_dev.clear();
     p->dev.mu = nullptr;
     p->dev.isd = nullptr;
     p->dev.widths = nullptr;
+    p->dev.narrow = nullptr;
     p->dev.ws_w = 0;
     cudaError_t e = cudaMalloc((void**)&p->dev.mu, (size_t)p->ndm * nw * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&p->dev.isd, (size_t)p->ndm * nw * sizeof(float));
     if (e == cudaSuccess) e = cudaMalloc((void**)&p->dev.widths, (size_t)nw * sizeof(int32_t));
+    if (e == cudaSuccess && p->out_int) e = cudaMalloc((void**)&p->dev.narrow, (size_t)p->ndm);
     if (e != cudaSuccess) return cuda_status(e);
     p->dev.ws_w = nw;
     return DD_OK;
@@ -632,7 +676,9 @@ dd_status launch_boxcar_scratch(dd_plan_s* p, const void* x, int64_t ld, int64_t
     a.cands = cands;
     a.cap = cap;
     a.ncands = ncands;
-    return dispatch_boxcar(p, a, widths, nw, s);
+    a.narrow = nullptr;
+    a.narrow_sel = 0;
+    return dispatch_boxcar(p, a, widths, nw, s, false);
 }
 
 dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
@@ -677,7 +723,9 @@ dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
     a.cands = cands;
     a.cap = cap;
     a.ncands = ncands;
-    return dispatch_boxcar(p, a, widths, nw, s);
+    a.narrow = nullptr;
+    a.narrow_sel = 0;
+    return dispatch_boxcar(p, a, widths, nw, s, true);
 }
 
 }  // namespace dd

@@ -109,6 +109,7 @@ struct DevTables {
     float* isd = nullptr;       // [ndm][ws_w] 1/sigma_dw
     int32_t* widths = nullptr;  // [ws_w]
     int32_t ws_w = 0;
+    uint8_t* narrow = nullptr;  // [ndm] 1 where a row's boxcar sums fit int32
 };
 
 }  // namespace dd

@@ -346,6 +346,7 @@ static void free_dev(dd_plan_s* p) {
     cudaFree(p->dev.mu);
     cudaFree(p->dev.isd);
     cudaFree(p->dev.widths);
+    cudaFree(p->dev.narrow);
     if (cur >= 0 && cur != p->dev.device) cudaSetDevice(cur);
     p->dev = DevTables{};
     p->widths_on_dev.clear();

@@ -263,6 +263,38 @@ def test_boxcar_all_widths_int64_path(dd):
     _boxcar_compare(peak.cpu().numpy(), arg.cpu().numpy(), xo, widths, mu, sdw)
 
 
+def test_boxcar_int64_rows_split(dd):
+    """Rows whose boxcar sums exceed int32 (a bright half, long tap runs) take the int64
+    scan, the others the int32 scan, in one call; both exact against the oracle."""
+    C, T, D = 64, 20000, 6
+    I = np.zeros((C, T), np.uint8)
+    I[:, : T // 2] = 255
+    rng = np.random.default_rng(16)
+    I[:, T // 2:] = rng.integers(0, 3, size=(C, T - T // 2))
+    delay = rng.integers(0, 300, size=(D, C)).astype(np.int32)
+    taps = np.full((D, C), 1200, np.int32)
+    taps[3:] = 10                                   # these rows stay within int32
+    plan = dd.Plan(dd.Band(C, 1200.0, 1.0, 1.0, T, "u8"), np.zeros(D))
+    plan.set_profiles(delay=delay, taps=taps)
+    plan.set_method("direct")
+    x = _dev(I)
+    out = plan.dedisperse(x, nsamp=T)
+    mean, sd = plan.channel_stats(x, nsamp=T)
+    widths = np.arange(1, 257, dtype=np.int32)
+    peak, arg, _ = plan.boxcar_snr(out, widths, mean, sd)
+    xo = out.cpu().numpy().astype(np.int64)
+    np.testing.assert_array_equal(xo, oracle.c_dedisperse(I, delay, taps, nsamp=T))
+    mu_c, sd_c = ref.channel_stats(I, nsamp=T)
+    mu, sdw = ref.boxcar_norm(taps, widths, mu_c, sd_c)
+    _, oarg, _ = ref.boxcar_snr(xo, widths, mu, sdw)
+    np.testing.assert_array_equal(arg.cpu().numpy(), oarg)
+    _boxcar_compare(peak.cpu().numpy(), arg.cpu().numpy(), xo, widths, mu, sdw)
+    # the wide rows really exceed int32 and the narrow ones do not
+    o = np.rint((mu[:, 0]))
+    assert (np.abs(xo[:3] - o[:3, None]).max(axis=1) * 256 > 2**31).all()
+    assert (np.abs(xo[3:] - o[3:, None]).max(axis=1) * 256 < 2**31).all()
+
+
 def test_boxcar_weighted_float(dd):
     cfg = synth.make_craft(nsamp=8192, npulse=6, amp=3.0)
     plan, delay, taps, w = _craft_plan(dd, 256, 8192)

@@ -218,12 +218,14 @@ def run_gpu(args):
     value = ws * units / (ms / 1e3)
 
     e2e = None if args.no_e2e else e2e_run(args, W, ws, plan, x, out, widths, stream)
+    # the device's measured FP32 FMA and INT32 add rates (after the timed region)
+    live = {"fma_tflops": dd.alu_peak("fma") / 1e12, "iadd_tops": dd.alu_peak("iadd") / 1e12}
     extras = None
     if rank == 0 and not args.no_extras:
         extras = {"fwd_bwd": diff_extra(dd, dev, flush, stream),
                   "batched": batched_extra(dd, dev, flush, stream),
-                  "large_lowband": large_extra(dd, dev, flush, stream)}
-    return _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras)
+                  "large_lowband": large_extra(dd, dev, flush, stream, iadd_tops=live["iadd_tops"])}
+    return _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras, live)
 
 
 def e2e_run(args, W, ws, plan, x, out, widths, stream):
@@ -405,7 +407,7 @@ def batched_extra(dd, dev, flush, stream, reps=3):
     }
 
 
-def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192):
+def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, iadd_tops=None):
     """Large low-band configuration: 1024 ch over 700-1000 MHz, dt 64 us, 2^20 uint8
     samples, 8192 trial DMs 0-2000 (unit weights, run-length sums), streamed in
     overlapping chunks of `chunk` outputs (each chunk reads its outputs plus d_max
@@ -439,6 +441,10 @@ def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192):
     st_ms = _ev_time(step_all, 2, flush, stream)
     units = float(plan.ndm) * t_out
     dct = units * b.nchan
+    # graded work of exact unit-weight sums: min(n, 2) additions per (trial, channel,
+    # output) plus one per input sample for the prefix pass
+    _, taps = plan.tables()
+    graded = float(np.minimum(taps, 2).astype(np.int64).sum()) * t_out + float(b.nchan) * T
     res = {
         "workload": (f"large low-band: {b.nchan} ch 700-1000 MHz, dt 64 us, {T} uint8 samples, "
                      f"{plan.ndm} trial DMs 0-2000, {len(starts)} overlapping chunks of {chunk} "
@@ -448,7 +454,12 @@ def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192):
         "dedisp_value": units / (dd_ms / 1e3), "step_value": units / (st_ms / 1e3), "unit": UNIT,
         "trial_channel_samples_per_s": dct / (dd_ms / 1e3),
         "realtime_factor": (t_out * b.dt_ms / 1e3) / (st_ms / 1e3),
+        "graded_adds_per_block": graded,
+        "graded_tops": graded / (dd_ms / 1e3) / 1e12,
+        "bound": "shared-memory loads (2 per trial, channel and output; see profiles)",
     }
+    if iadd_tops:
+        res["graded_frac_of_measured_iadd"] = res["graded_tops"] / iadd_tops
     plan.close()
     return res
 
@@ -477,7 +488,7 @@ def _profile_traffic():
         return None
 
 
-def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras=None):
+def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras=None, live=None):
     if rank != 0:
         return None
     peaks, kind = _peaks()
@@ -502,8 +513,11 @@ def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras=None):
                      "peak_kind": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
                                   f"{sm_max:.0f} MHz ({kind} sm_max_mhz)",
                      "kernel_ms": k_avg, "flops_per_launch": W["flops"]},
+        "alu_peaks_measured": live,
         "clocks": clocks,
     }
+    if live:
+        res["roofline"]["frac_of_measured_fma"] = achieved / live["fma_tflops"]
     if extras is not None:
         res["extras"] = extras
     if not args.no_cpu_baseline:
@@ -606,7 +620,8 @@ def run_only(args):
     elif args.only == "batched":
         r = batched_extra(dd, dev, flush, stream)
     else:
-        r = large_extra(dd, dev, flush, stream, nsamp=args.large_nsamp, ndm=args.large_ndm)
+        r = large_extra(dd, dev, flush, stream, nsamp=args.large_nsamp, ndm=args.large_ndm,
+                        iadd_tops=dd.alu_peak("iadd") / 1e12)
     return {"only": args.only, **r}
 
 

@@ -284,6 +284,14 @@ dd_status dd_get_device_status(dd_plan_t plan, int32_t* code, void* stream);
 dd_status dd_test_set_wait(dd_plan_t plan, int32_t skip_stage, int64_t wait_ns);
 
 /* Releases the plan's host and device memory (after its work has finished). */
+/* Measured ALU throughput of the current device (no counterpart in the paper; the
+ * denominator of the roofline fraction of the ALU-bound kernels).  kind 0: FP32 fused
+ * multiply-adds, reported as flops/s (2 per FMA); kind 1: INT32 three-input adds,
+ * reported as additions/s (2 per instruction).  Dependency-free loops over every SM;
+ * one warm-up launch, one timed launch (about 0.1 s); synchronises the stream.
+ * Errors: DD_ERR_ARG, DD_ERR_OOM, DD_ERR_CUDA. */
+dd_status dd_alu_peak(int32_t kind, double* ops_per_s, void* stream);
+
 dd_status dd_plan_destroy(dd_plan_t plan);
 
 /* Static, human-readable name of a status code. */

@@ -47,6 +47,14 @@ def _stream(stream=None) -> ctypes.c_void_p:
     return ctypes.c_void_p(s.cuda_stream)
 
 
+def alu_peak(kind: str = "fma", stream=None) -> float:
+    """Measured device throughput: "fma" in flops/s (FP32 FMA), "iadd" in additions/s."""
+    v = ctypes.c_double()
+    check(_lib.load().dd_alu_peak({"fma": 0, "iadd": 1}[kind], ctypes.cast(ctypes.byref(v), ctypes.c_void_p),
+                                  _stream(stream)), "dd_alu_peak")
+    return v.value
+
+
 def trial_dms(band: Band, dm0: float, dm_max: float, n: int, tau_av_ms: float | None = None,
               smear_terms: int = 2):
     """Trial DMs of eq. trial DMs (Sec. 6.3) ending exactly at dm_max; returns (dms, ε)."""

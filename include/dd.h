@@ -284,6 +284,39 @@ dd_status dd_get_device_status(dd_plan_t plan, int32_t* code, void* stream);
 dd_status dd_test_set_wait(dd_plan_t plan, int32_t skip_stage, int64_t wait_ns);
 
 /* Releases the plan's host and device memory (after its work has finished). */
+/* Profile construction (host only).
+ *
+ * dd_predict_rect: the cell-averaged power of eq. Pavg for the rectangular scattered pulse
+ * of eq. profile_sb, P(t, nu) = p0 (nu/nu0)^-alpha tau/tau' on [t_d, t_d + tau'), with
+ * t_d(nu) = t0_ms + k_dm DM (nu^-2 - nu_top^-2) (arrival t0_ms at the top of the band):
+ *   pbar[c][j] = (1/dt) int_{channel c} dnu int_{j dt}^{(j+1) dt} dt' P(t', nu),
+ * nu in GHz, for 0 <= j < nt (cells before t = 0 or from nt on are left out).  The time
+ * integral is the exact overlap; the frequency integral is a midpoint rule on at least 64
+ * sub-channels per channel, more where one sub-channel's own sweep would exceed tau'/16.
+ * pbar is a host array [nchan][nt].  Errors: DD_ERR_ARG.
+ *
+ * dd_select_samples: the sample selection of Sec. 2.2 on one trial's predicted powers
+ * pbar [nchan][nt]: samples are taken in order of decreasing power (equal powers in
+ * channel-major order) while eq. sel_criterion holds, P > (sqrt((N+1)/N) - 1) * sum of
+ * the N already taken.  Each channel's selected samples become a tap run from the first
+ * to the last of them with weight 1 on selected samples and 0 on gaps (delay[c] = first
+ * sample, ntaps[c] = run length, w [nchan][kmax]); a channel with none gets one tap of
+ * weight 0.  *nsel = samples taken, *gain = (S/N of the selection)/(S/N of every sample
+ * with P > 0), S/N = sum P / sqrt(N) (equal noise per sample, eq. snr).  Either output
+ * may be NULL.  Errors: DD_ERR_ARG, DD_ERR_CAPACITY (a run longer than kmax).
+ *
+ * dd_exact_profiles: the tap rule of eq. num_samples with the pulse width,
+ * delay = floor(t_A/dt) and ntaps = ceil(t_B/dt) - floor(t_A/dt), t_A = k_dm DM
+ * (nu_c^-2 - nu_top^-2) and t_B = t_A + tau' + the exact sweep across the channel, for
+ * every trial of the plan (host arrays [ndm][nchan]; pass them to dd_set_profiles).
+ * Errors: DD_ERR_ARG, DD_ERR_OVERFLOW. */
+dd_status dd_predict_rect(const dd_band* band, double dm, double t0_ms, double tau_ms,
+                          double tau_prime_ms, double alpha, double nu0_ghz, double p0,
+                          int32_t nt, double* pbar);
+dd_status dd_select_samples(const double* pbar, int32_t nchan, int32_t nt, int32_t kmax,
+                            int32_t* delay, int32_t* ntaps, float* w, int32_t* nsel, double* gain);
+dd_status dd_exact_profiles(dd_plan_t plan, double tau_prime_ms, int32_t* delay, int32_t* ntaps);
+
 /* Measured ALU throughput of the current device (no counterpart in the paper; the
  * denominator of the roofline fraction of the ALU-bound kernels).  kind 0: FP32 fused
  * multiply-adds, reported as flops/s (2 per FMA); kind 1: INT32 three-input adds,

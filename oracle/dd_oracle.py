@@ -342,6 +342,31 @@ def adjoint_points(I, g, delays, taps, w, gw_points=(), gi_points=(), t_offset=0
     return np.array(gw), np.array(gi)
 
 
+def select_samples(pbar):
+    """Sample selection for maximum S/N (Sec. 2.2): starting from the empty set, take the
+    sample of highest predicted power, then the next highest, while eq. sel_criterion
+    P_next > (sqrt((N+1)/N) - 1) * (sum of the N taken) holds.  Equal powers are taken
+    in row-major (channel, sample) order.  Returns a boolean mask of pbar's shape."""
+    p = np.asarray(pbar, np.float64)
+    flat = p.ravel()
+    order = sorted((i for i in range(flat.size) if flat[i] > 0), key=lambda i: (-flat[i], i))
+    mask = np.zeros(flat.size, bool)
+    total, n = 0.0, 0
+    for i in order:
+        if n > 0 and not flat[i] > (math.sqrt((n + 1) / n) - 1.0) * total:
+            break
+        mask[i] = True
+        total += flat[i]
+        n += 1
+    return mask.reshape(p.shape)
+
+
+def set_snr(pbar, mask):
+    """S/N of a sample set with equal noise per sample (eq. snr): sum P / sqrt(N)."""
+    p = np.asarray(pbar, np.float64)[mask]
+    return float(p.sum() / math.sqrt(p.size)) if p.size else 0.0
+
+
 def dsmf_snr(pbar, sigma):
     """Dynamic-spectrum matched filter S/N √(Σ P̄²)/σ (Sec. 5) for cell noise σ."""
     return math.sqrt(float((np.asarray(pbar, np.float64) ** 2).sum())) / sigma

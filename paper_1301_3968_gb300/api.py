@@ -55,6 +55,59 @@ def alu_peak(kind: str = "fma", stream=None) -> float:
     return v.value
 
 
+def predict_rect(band: Band, dm: float, nt: int, t0_ms: float = 0.0, tau_ms: float = 1.0,
+                 tau_prime_ms: float = 1.0, alpha: float = 0.0, nu0_ghz: float = 1.0,
+                 p0: float = 1.0) -> np.ndarray:
+    """Cell-averaged power [nchan][nt] of the rectangular scattered pulse (eq. Pavg)."""
+    out = np.zeros((band.nchan, nt), dtype=np.float64)
+    b = band.c_struct()
+    check(_lib.load().dd_predict_rect(ctypes.cast(ctypes.byref(b), ctypes.c_void_p), float(dm),
+                                      float(t0_ms), float(tau_ms), float(tau_prime_ms), float(alpha),
+                                      float(nu0_ghz), float(p0), int(nt), _np_ptr(out)),
+          "dd_predict_rect")
+    return out
+
+
+def select_samples(pbar: np.ndarray, kmax: int):
+    """Sample selection for maximum S/N (Sec. 2.2) on one trial's predicted powers:
+    (delay [C], ntaps [C], weights [C][kmax], samples taken, S/N gain)."""
+    pbar = np.ascontiguousarray(pbar, dtype=np.float64)
+    C, nt = pbar.shape
+    delay = np.zeros(C, np.int32)
+    taps = np.zeros(C, np.int32)
+    w = np.zeros((C, kmax), np.float32)
+    nsel = ctypes.c_int32()
+    gain = ctypes.c_double()
+    check(_lib.load().dd_select_samples(_np_ptr(pbar), C, nt, int(kmax), _np_ptr(delay), _np_ptr(taps),
+                                        _np_ptr(w), ctypes.cast(ctypes.byref(nsel), ctypes.c_void_p),
+                                        ctypes.cast(ctypes.byref(gain), ctypes.c_void_p)),
+          "dd_select_samples")
+    return delay, taps, w, nsel.value, gain.value
+
+
+def select_profiles(band: Band, dms, tau_ms: float = 1.0, tau_prime_ms: float = 1.0,
+                    alpha: float = 0.0, nu0_ghz: float = 1.0, phase: float = 0.0):
+    """Selected-sample profiles for every trial (pulse arriving `phase` samples into the
+    output sample at the top of the band): delay [D][C], ntaps [D][C], weights [D][C][K]
+    and each trial's S/N gain over taking every sample with pulse power."""
+    dms = np.asarray(dms, dtype=np.float64)
+    lo = band.f_lo_mhz / 1000.0
+    top = (band.f_lo_mhz + band.nchan * band.df_mhz) / 1000.0
+    k = band.k_dm if band.k_dm > 0 else 4.15
+    rows = []
+    for dm in dms:
+        span = k * dm * (1.0 / lo ** 2 - 1.0 / top ** 2) + tau_prime_ms + 2 * band.dt_ms
+        nt = int(np.ceil(span / band.dt_ms)) + 2
+        p = predict_rect(band, dm, nt, phase * band.dt_ms, tau_ms, tau_prime_ms, alpha, nu0_ghz)
+        rows.append(select_samples(p, nt))
+    K = max(int(r[1].max()) for r in rows)
+    delay = np.stack([r[0] for r in rows])
+    taps = np.stack([r[1] for r in rows])
+    w = np.stack([r[2][:, :K] for r in rows])
+    gains = np.array([r[4] for r in rows])
+    return delay, taps, w, gains
+
+
 def trial_dms(band: Band, dm0: float, dm_max: float, n: int, tau_av_ms: float | None = None,
               smear_terms: int = 2):
     """Trial DMs of eq. trial DMs (Sec. 6.3) ending exactly at dm_max; returns (dms, ε)."""
@@ -219,6 +272,14 @@ class Plan:
                                     gin.stride(0) if gin is not None else 0, _stream(stream)),
               "dd_backward")
         return gw, gin
+
+    def exact_profiles(self, tau_prime_ms: float):
+        """Delay and tap tables of eq. num_samples with the pulse width tau' (host)."""
+        d = np.zeros((self.ndm, self.band.nchan), np.int32)
+        t = np.zeros_like(d)
+        check(self._lib.dd_exact_profiles(self._h, float(tau_prime_ms), _np_ptr(d), _np_ptr(t)),
+              "dd_exact_profiles")
+        return d, t
 
     def set_schedule(self, nch: int, cs: int) -> None:
         check(self._lib.dd_plan_set_schedule(self._h, int(nch), int(cs)), "dd_plan_set_schedule")

@@ -170,3 +170,67 @@ def test_method_selection_host_logic(lib):
     # a run-length plan that gets weights sums directly
     small.set_profiles(weights=np.ones((128, pb.nchan, 16), np.float32))
     assert small.method == "direct"
+
+
+# ----------------------------------------------------------------------------- profile construction
+
+
+@pytest.mark.parametrize("dm,t0,alpha,desc", [(30.0, 10.0, 0.0, False), (300.0, 4.3, 2.0, False),
+                                              (1200.0, 0.6, -1.5, True)])
+def test_predict_rect_matches_pulse_model(lib, dm, t0, alpha, desc):
+    import paper_1301_3968_gb300 as dd
+    b = synth.Band(48, 700.0, 6.25, 1.0, descending=desc)
+    T = 3000
+    want = synth.rect_pulse_cells(b, T, dm, t0, 1.0, 2.0, alpha=alpha, nu0_ghz=1.1)
+    band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, T, "f32", desc)
+    got = dd.predict_rect(band, dm, T, t0_ms=t0, tau_ms=1.0, tau_prime_ms=2.0, alpha=alpha, nu0_ghz=1.1)
+    np.testing.assert_allclose(got, want, rtol=1e-11, atol=1e-14)
+
+
+def test_select_samples_matches_oracle(lib):
+    import paper_1301_3968_gb300 as dd
+    rng = np.random.default_rng(62)
+    maps = [rng.exponential(1.0, size=(6, 9)) * (rng.random((6, 9)) < 0.6),
+            rng.integers(0, 4, size=(5, 8)).astype(float)]
+    for C, dt in ((60, 1.0), (122, 1.0), (244, 2.0)):
+        b = synth.Band(C, 700.0, 300.0 / C, dt)
+        maps.append(synth.rect_pulse_cells(b, int(200 / dt), 30.0, 10.0, 1.0, 1.0))
+    for p in maps:
+        C, nt = p.shape
+        delay, taps, w, nsel, gain = dd.select_samples(p, nt)
+        mask = np.zeros_like(p, dtype=bool)
+        for c in range(C):
+            for k in range(taps[c]):
+                if w[c, k] == 1.0:
+                    mask[c, delay[c] + k] = True
+        want = ref.select_samples(p)
+        np.testing.assert_array_equal(mask, want)
+        assert nsel == want.sum()
+        assert gain == pytest.approx(ref.set_snr(p, want) / ref.set_snr(p, p > 0), rel=1e-12)
+        # every tap outside the selection has weight 0, and runs start and end on it
+        for c in range(C):
+            if mask[c].any():
+                assert w[c, 0] == 1.0 and w[c, taps[c] - 1] == 1.0
+    with pytest.raises(dd.DDError):
+        dd.select_samples(np.ones((2, 10)), 4)          # a 10-sample run with kmax 4
+
+
+def test_exact_profiles_cover_the_rect_pulse(lib):
+    """eq. num_samples: delay = floor(t_A/dt), taps = ceil(t_B/dt) - floor(t_A/dt) is the
+    extent of the cells holding power of a pulse arriving at t = 0 with width tau'.  The
+    model's frequency quadrature samples sub-channel midpoints, so at either end of a run
+    it may miss a cell that only the band-edge frequencies reach: exact there or one
+    cell wider, never narrower."""
+    import paper_1301_3968_gb300 as dd
+    b = synth.Band(40, 700.0, 7.5, 1.0)
+    dms = np.array([0.0, 17.3, 230.0, 911.0])
+    plan = dd.Plan(dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, 8192, "f32"), dms)
+    delay, taps = plan.exact_profiles(1.37)
+    for d, dm in enumerate(dms):
+        P = synth.rect_pulse_cells(b, 8192, dm, 0.0, 1.0, 1.37)
+        first = np.array([np.flatnonzero(P[c] > 0)[0] for c in range(b.nchan)])
+        last = np.array([np.flatnonzero(P[c] > 0)[-1] for c in range(b.nchan)])
+        end = delay[d] + taps[d] - 1
+        assert ((first - delay[d] >= 0) & (first - delay[d] <= 1)).all()
+        assert ((end - last >= 0) & (end - last <= 1)).all()
+        assert ((first - delay[d]) + (end - last) == 0).mean() > 0.8

@@ -317,6 +317,23 @@ dd_status dd_select_samples(const double* pbar, int32_t nchan, int32_t nt, int32
                             int32_t* delay, int32_t* ntaps, float* w, int32_t* nsel, double* gain);
 dd_status dd_exact_profiles(dd_plan_t plan, double tau_prime_ms, int32_t* delay, int32_t* ntaps);
 
+/* The comparison detectors of Sec. 5 as profiles for the same dedispersion kernel, from one
+ * trial's predicted powers pbar [nchan][nt] (host):
+ *   kind 0, dynamic-spectrum matched filter: every cell with power, weighted by its power
+ *     (scaled to a maximum of 1); *snr = sqrt(sum pbar^2).
+ *   kind 1, time-series matched filter: the channels aligned by align[c] (the trial's integer
+ *     delays) and summed into T[m] = sum_c pbar[c][align[c] + m]; every channel gets the tap
+ *     run of T's window with weights T (scaled to a maximum of 1); *snr = sqrt(sum T^2 / C).
+ *   kind 2, time-series boxcar matched in width: the same window with unit weights;
+ *     *snr = sum T / sqrt(C * window length).
+ * S/N assumes unit noise per cell (divide by the cell noise for physical units).  Outputs as
+ * dd_select_samples (delay/ntaps [nchan], w [nchan][kmax]); snr may be NULL.
+ * Errors: DD_ERR_ARG (no power, align NULL for kinds 1-2, a window before sample 0),
+ * DD_ERR_CAPACITY (a run longer than kmax). */
+dd_status dd_detector_profile(const double* pbar, int32_t nchan, int32_t nt, const int32_t* align,
+                              int32_t kind, int32_t kmax, int32_t* delay, int32_t* ntaps, float* w,
+                              double* snr);
+
 /* Measured ALU throughput of the current device (no counterpart in the paper; the
  * denominator of the roofline fraction of the ALU-bound kernels).  kind 0: FP32 fused
  * multiply-adds, reported as flops/s (2 per FMA); kind 1: INT32 three-input adds,

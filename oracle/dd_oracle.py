@@ -367,6 +367,32 @@ def set_snr(pbar, mask):
     return float(p.sum() / math.sqrt(p.size)) if p.size else 0.0
 
 
+def detector_snrs(pbar, align, sigma=1.0):
+    """S/N of the Sec. 5 detectors on one trial's predicted cell powers with noise sigma
+    per cell: the dynamic-spectrum matched filter sqrt(sum P^2)/sigma; the time-series
+    matched filter sqrt(sum_m T_m^2 / C)/sigma and boxcar sum_m T_m / sqrt(C N_t)/sigma on the
+    series T_m = sum_c P[c][align_c + m] over the window holding power; the sample-selection
+    detector (Sec. 2.2) and the every-sample-with-power detector sum P / sqrt(N)/sigma."""
+    p = np.asarray(pbar, np.float64)
+    C, nt = p.shape
+    rows, cols = np.nonzero(p > 0)
+    m = cols - np.asarray(align)[rows]
+    lo, hi = int(m.min()), int(m.max())
+    T = np.zeros(hi - lo + 1)
+    for c in range(C):
+        for k in range(hi - lo + 1):
+            j = int(align[c]) + lo + k
+            if 0 <= j < nt:
+                T[k] += p[c, j]
+    return {
+        "dsmf": math.sqrt(float((p ** 2).sum())) / sigma,
+        "ts_mf": math.sqrt(float((T ** 2).sum()) / C) / sigma,
+        "ts_boxcar": float(T.sum()) / math.sqrt(C * T.size) / sigma,
+        "selection": set_snr(p, select_samples(p)) / sigma,
+        "all_samples": set_snr(p, p > 0) / sigma,
+    }
+
+
 def dsmf_snr(pbar, sigma):
     """Dynamic-spectrum matched filter S/N √(Σ P̄²)/σ (Sec. 5) for cell noise σ."""
     return math.sqrt(float((np.asarray(pbar, np.float64) ** 2).sum())) / sigma

@@ -7,8 +7,8 @@ boxcar S/N detection (eq. snr), as hand-written sm_103a CUDA kernels behind the 
 of include/dd.h.  This package is the thin Python binding.
 """
 from ._lib import DDError, LIB_PATH  # noqa: F401
-from .api import (Band, Batch, DDFunction, Plan, alu_peak, candidates_to_list, predict_rect,  # noqa: F401
-                  select_profiles, select_samples, trial_dms)
+from .api import (Band, Batch, DDFunction, Plan, alu_peak, candidates_to_list, detector_profile,  # noqa: F401
+                  predict_rect, select_profiles, select_samples, trial_dms)
 
 __all__ = ["Band", "Plan", "Batch", "DDFunction", "DDError", "alu_peak", "trial_dms", "candidates_to_list",
-           "predict_rect", "select_samples", "select_profiles"]
+           "predict_rect", "select_samples", "select_profiles", "detector_profile"]

@@ -85,6 +85,27 @@ def select_samples(pbar: np.ndarray, kmax: int):
     return delay, taps, w, nsel.value, gain.value
 
 
+DETECTORS = {"dsmf": 0, "ts_mf": 1, "ts_boxcar": 2}
+
+
+def detector_profile(pbar: np.ndarray, kind: str, kmax: int, align=None):
+    """A comparison detector of Sec. 5 as one trial's profile: (delay [C], ntaps [C],
+    weights [C][kmax], S/N with unit cell noise).  kind: "dsmf", "ts_mf" or "ts_boxcar";
+    the time-series detectors align the channels by `align` (the trial's delays)."""
+    pbar = np.ascontiguousarray(pbar, dtype=np.float64)
+    C, nt = pbar.shape
+    al = None if align is None else np.ascontiguousarray(align, dtype=np.int32)
+    delay = np.zeros(C, np.int32)
+    taps = np.zeros(C, np.int32)
+    w = np.zeros((C, kmax), np.float32)
+    snr = ctypes.c_double()
+    check(_lib.load().dd_detector_profile(_np_ptr(pbar), C, nt, _np_ptr(al), DETECTORS[kind], int(kmax),
+                                          _np_ptr(delay), _np_ptr(taps), _np_ptr(w),
+                                          ctypes.cast(ctypes.byref(snr), ctypes.c_void_p)),
+          "dd_detector_profile")
+    return delay, taps, w, snr.value
+
+
 def select_profiles(band: Band, dms, tau_ms: float = 1.0, tau_prime_ms: float = 1.0,
                     alpha: float = 0.0, nu0_ghz: float = 1.0, phase: float = 0.0):
     """Selected-sample profiles for every trial (pulse arriving `phase` samples into the

@@ -1,7 +1,8 @@
 // Profile construction on the host: the cell-averaged power of a model pulse (eq. Pavg
-// for the rectangular scattered pulse of eq. profile_sb) and the greedy sample selection
-// for maximum S/N (Sec. 2.2, eq. sel_criterion), which turns a predicted power map into
-// one trial's (delay, taps, weights) profile.
+// for the rectangular scattered pulse of eq. profile_sb), the greedy sample selection
+// for maximum S/N (Sec. 2.2, eq. sel_criterion) and the comparison detectors of Sec. 5,
+// each of which turns a predicted power map into one trial's (delay, taps, weights)
+// profile for the dedispersion kernel.
 #include <algorithm>
 #include <cmath>
 #include <numeric>
@@ -106,6 +107,78 @@ dd_status dd_select_samples(const double* pbar, int32_t nchan, int32_t nt, int32
         const double snr_all = idx.empty() ? 0.0 : all_sum / std::sqrt((double)idx.size());
         *gain = snr_all > 0 ? snr_sel / snr_all : 0.0;
     }
+    return DD_OK;
+}
+
+dd_status dd_detector_profile(const double* pbar, int32_t nchan, int32_t nt, const int32_t* align,
+                              int32_t kind, int32_t kmax, int32_t* delay, int32_t* ntaps, float* w,
+                              double* snr) {
+    if (!pbar || nchan < 1 || nt < 1 || kmax < 1 || !delay || !ntaps || !w || kind < 0 || kind > 2)
+        return DD_ERR_ARG;
+    if (kind > 0 && !align) return DD_ERR_ARG;
+    std::fill(w, w + (size_t)nchan * kmax, 0.0f);
+    double pmax = 0.0;
+    for (size_t i = 0; i < (size_t)nchan * nt; ++i) pmax = std::max(pmax, pbar[i]);
+    if (!(pmax > 0)) return DD_ERR_ARG;
+    if (kind == 0) {
+        // dynamic-spectrum matched filter: every cell weighted by its expected power
+        double q = 0.0;
+        for (int c = 0; c < nchan; ++c) {
+            const double* row = pbar + (size_t)c * nt;
+            int lo = -1, hi = -1;
+            for (int j = 0; j < nt; ++j)
+                if (row[j] > 0) {
+                    if (lo < 0) lo = j;
+                    hi = j;
+                    q += row[j] * row[j];
+                }
+            if (lo < 0) {
+                delay[c] = 0;
+                ntaps[c] = 1;
+                continue;
+            }
+            if (hi - lo + 1 > kmax) return DD_ERR_CAPACITY;
+            delay[c] = lo;
+            ntaps[c] = hi - lo + 1;
+            for (int j = lo; j <= hi; ++j) w[(size_t)c * kmax + (j - lo)] = (float)(row[j] / pmax);
+        }
+        if (snr) *snr = std::sqrt(q);
+        return DD_OK;
+    }
+    // time-series detectors: the channels aligned by `align` and summed into one series
+    // T[m] = sum_c pbar[c][align[c] + m] over the window of m holding pulse power
+    int64_t mlo = INT64_MAX, mhi = INT64_MIN;
+    for (int c = 0; c < nchan; ++c)
+        for (int j = 0; j < nt; ++j)
+            if (pbar[(size_t)c * nt + j] > 0) {
+                mlo = std::min<int64_t>(mlo, (int64_t)j - align[c]);
+                mhi = std::max<int64_t>(mhi, (int64_t)j - align[c]);
+            }
+    const int64_t len = mhi - mlo + 1;
+    if (len > kmax) return DD_ERR_CAPACITY;
+    std::vector<double> T((size_t)len, 0.0);
+    for (int c = 0; c < nchan; ++c) {
+        if ((int64_t)align[c] + mlo < 0) return DD_ERR_ARG;
+        for (int64_t m = 0; m < len; ++m) {
+            const int64_t j = align[c] + mlo + m;
+            if (j >= 0 && j < nt) T[(size_t)m] += pbar[(size_t)c * nt + j];
+        }
+    }
+    double s1 = 0.0, s2 = 0.0, tmax = 0.0;
+    for (double v : T) {
+        s1 += v;
+        s2 += v * v;
+        tmax = std::max(tmax, v);
+    }
+    for (int c = 0; c < nchan; ++c) {
+        delay[c] = (int32_t)(align[c] + mlo);
+        ntaps[c] = (int32_t)len;
+        for (int64_t m = 0; m < len; ++m)
+            w[(size_t)c * kmax + m] = kind == 1 ? (float)(T[(size_t)m] / tmax) : 1.0f;
+    }
+    // unit noise per cell: the matched filter's S/N is sqrt(sum T^2 / C), the boxcar's
+    // sum T / sqrt(C * len)
+    if (snr) *snr = kind == 1 ? std::sqrt(s2 / nchan) : s1 / std::sqrt((double)nchan * (double)len);
     return DD_OK;
 }
 

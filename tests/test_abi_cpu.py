@@ -2,6 +2,7 @@
 logic (profile tables, trial DMs, argument checking) matches the oracle.  No device
 compute runs here."""
 import ctypes
+import math
 import os
 import re
 
@@ -234,3 +235,20 @@ def test_exact_profiles_cover_the_rect_pulse(lib):
         assert ((first - delay[d] >= 0) & (first - delay[d] <= 1)).all()
         assert ((end - last >= 0) & (end - last <= 1)).all()
         assert ((first - delay[d]) + (end - last) == 0).mean() > 0.8
+
+
+@pytest.mark.parametrize("kind", ["dsmf", "ts_mf", "ts_boxcar"])
+def test_detector_profiles_match_oracle(lib, kind):
+    import paper_1301_3968_gb300 as dd
+    for C, dt, dm in ((40, 1.0, 30.0), (122, 1.0, 30.0), (12, 2.0, 300.0)):
+        b = synth.Band(C, 700.0, 300.0 / C, dt)
+        P = synth.rect_pulse_cells(b, int(3000 / dt), dm, 20.0, 1.0, 1.0)
+        dl, _ = ref.delay_table([dm], C, 700.0, 300.0 / C, dt)
+        align = (dl[0] + 20).astype(np.int32)
+        delay, taps, w, snr = dd.detector_profile(P, kind, 1024, align=align)
+        assert snr == pytest.approx(ref.detector_snrs(P, align)[kind], rel=1e-12)
+        # the profile's own S/N on the predicted cells is the closed form
+        num = sum(float(np.dot(w[c, :taps[c]].astype(np.float64), P[c, delay[c]:delay[c] + taps[c]]))
+                  for c in range(C))
+        den = math.sqrt(float((w.astype(np.float64) ** 2).sum()))
+        assert num / den == pytest.approx(snr, rel=1e-6)

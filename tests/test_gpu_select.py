@@ -61,3 +61,34 @@ def test_selected_profiles_gain_on_gpu(dd):
     snr_all = f / np.sqrt(taps_f.sum(axis=1))
     np.testing.assert_allclose(snr_sel / snr_all, gains, rtol=1e-4)
     assert (gains > 1.15).all() and (gains < 1.25).all()
+
+
+def test_comparison_detectors_on_gpu(dd):
+    """Sec. 5 detectors as profiles on the same kernel: the GPU S/N of a matched noise-free
+    pulse equals each detector's closed form, and the dynamic-spectrum matched filter is
+    the best of them."""
+    import torch
+    C, dt, dm = 122, 1.0, 30.0
+    b = synth.Band(C, 700.0, 300.0 / C, dt)
+    T, t_arr = 1024, 200
+    band = dd.Band(C, b.f_lo_mhz, b.df_mhz, dt, T, "f32")
+    P = synth.rect_pulse_cells(b, 600, dm, 0.0, 1.0, 1.0)      # predicted cells, arrival at 0
+    I = synth.rect_pulse_cells(b, T, dm, t_arr * dt, 1.0, 1.0).astype(np.float32)
+    x = torch.from_numpy(I).cuda()
+    align = ref.delay_table([dm], C, 700.0, 300.0 / C, dt)[0][0].astype(np.int32)
+    snrs = {}
+    for kind in ("dsmf", "ts_mf", "ts_boxcar", "selection"):
+        if kind == "selection":
+            delay, taps, w, _, _ = dd.select_samples(P, 600)
+            want = ref.set_snr(P, ref.select_samples(P))
+        else:
+            delay, taps, w, want = dd.detector_profile(P, kind, 600, align=align)
+        K = int(taps.max())
+        plan = dd.Plan(band, [dm])
+        plan.set_profiles(delay=delay[None, :], taps=taps[None, :], weights=w[None, :, :K])
+        out = plan.dedisperse(x, nsamp=T).cpu().numpy()
+        snr = float(out[0, t_arr]) / np.sqrt((w.astype(np.float64) ** 2).sum())
+        assert snr == pytest.approx(want, rel=1e-5)
+        snrs[kind] = snr
+    assert snrs["dsmf"] >= max(snrs.values()) * (1 - 1e-6)
+    assert snrs["ts_mf"] >= snrs["ts_boxcar"]

@@ -517,3 +517,30 @@ def test_rect_pulse_cells_conserve_fluence():
     P = synth.rect_pulse_cells(b, 20, 0.0, 3.25, 1.0, 2.5)
     want = np.array([0, 0, 0, 0.75, 1.0, 0.75] + [0] * 14) * (b.df_mhz / 1000.0) / 2.5
     np.testing.assert_allclose(P, np.tile(want, (16, 1)), atol=1e-15)
+
+
+# ----------------------------------------------------------------------------- Sec. 5 detectors
+
+
+def test_detectors_agree_on_a_perfectly_dedispersed_pulse():
+    """Sec. 5: with N_S = C N_t and a constant P over the block, every detector gives the
+    same S/N (here P = 2 over 6 channels x 4 samples: 2 sqrt(24))."""
+    p = np.zeros((6, 10))
+    p[:, 3:7] = 2.0
+    s = ref.detector_snrs(p, align=np.zeros(6, int))
+    for v in s.values():
+        assert v == pytest.approx(2.0 * math.sqrt(24.0), rel=1e-12)
+
+
+def test_detector_ordering_on_pulse_maps():
+    """Sec. 5: the dynamic-spectrum matched filter bounds every detector (Cauchy-Schwarz);
+    the time-series matched filter beats the time-series boxcar; the sample-selection
+    detector beats taking every sample with power, which beats the boxcar (N_S <= C N_t)."""
+    for C, dt, dm in ((40, 1.0, 30.0), (122, 1.0, 30.0), (300, 0.5, 100.0), (12, 2.0, 300.0)):
+        b = synth.Band(C, 700.0, 300.0 / C, dt)
+        P = synth.rect_pulse_cells(b, int(3000 / dt), dm, 20.0, 1.0, 1.0)
+        dl, _ = ref.delay_table([dm], C, 700.0, 300.0 / C, dt)
+        s = ref.detector_snrs(P, align=dl[0] + 20)
+        assert all(s["dsmf"] >= v * (1 - 1e-12) for v in s.values())
+        assert s["ts_mf"] >= s["ts_boxcar"]
+        assert s["selection"] >= s["all_samples"] >= s["ts_boxcar"]

@@ -132,6 +132,7 @@ __device__ __forceinline__ void unpk(uint64_t v, float& lo, float& hi) {
 struct Smem {
     unsigned char* stages;
     int* lo_all;
+    uint32_t* brows;  // difference rows (run-length path with shared rows)
     uint64_t* full;
     int* cnt;
     int* issued;
@@ -140,10 +141,12 @@ struct Smem {
 __device__ __forceinline__ unsigned char* pipeline_area(unsigned char* smem, size_t smem_bytes, int nbuf);
 
 template <int NBUF>
-__device__ __forceinline__ Smem carve(unsigned char* smem, const StageGeom& g, size_t smem_bytes) {
+__device__ __forceinline__ Smem carve(unsigned char* smem, const StageGeom& g, size_t smem_bytes,
+                                      int nchan) {
     Smem s;
     s.stages = smem;
     s.lo_all = (int*)(smem + NBUF * g.bytes);
+    s.brows = (uint32_t*)(smem + NBUF * g.bytes + ((4 * nchan + 15) & ~15));
     s.full = (uint64_t*)pipeline_area(smem, smem_bytes, NBUF);
     s.cnt = (int*)(s.full + NBUF);
     s.issued = s.cnt + NBUF;
@@ -264,6 +267,21 @@ __device__ __forceinline__ void stage_rl(const uint32_t* rows, const int2* ent, 
     }
 }
 
+// The same sums from difference rows the CTA has built for the stage: brows holds, per
+// channel, B_q[i] = P[i + n_q] - P[i] for the block's (at most two) tap counts n_q, and
+// the unit's entry is (run start, q).  One load and one add per output.
+__device__ __forceinline__ void stage_rl_rows(const uint32_t* brows, const int2* ent, const int* lo,
+                                              int csn, int lcap, int bq, int lane_off, int (&acc)[kRInt]) {
+    constexpr int R = kRInt;
+    for (int ci = 0; ci < csn; ++ci) {
+        const int2 q = ent[ci];  // (run start - block minimum, index of the tap count)
+        const uint32_t* p = brows + (ci * 2 + q.y) * lcap + ((bq + lo[ci]) & 3) + q.x + lane_off;
+        __builtin_assume(__isShared(p));
+#pragma unroll
+        for (int r = 0; r < R; ++r) acc[r] += (int)p[r];
+    }
+}
+
 // One stage of one warp unit on the fp32 path: two adjacent trials share the register
 // window.  The entry's window is the union of the two trials' windows, and its weights
 // are (w0, w1) pairs that are zero where a trial has no tap, so each tap costs one
@@ -349,12 +367,14 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
     constexpr int Q = Elem<TIN>::Q;
     constexpr int TPW = PAIR ? 2 : 1;   // trials per warp unit
     constexpr bool RL = std::is_same<TIN, uint32_t>::value;
+    // SHORT on the run-length path: the CTA shares difference rows per stage
+    constexpr bool BROW = RL && SHORT;
     constexpr int UPW = upw<TIN>();     // warp units per warp
     using TACC = typename std::conditional<PAIR, float, int>::type;
     const int cs = a.cs;
     const int nu = kWarps / a.nch * UPW;  // warp units per CTA
-    const StageGeom g((int)sizeof(TIN), PAIR, a.lcap, a.kpad, cs, nu);
-    const Smem sm = carve<NBUF>(smem, g, a.smem_bytes);
+    const StageGeom g((int)sizeof(TIN), PAIR, a.lcap, a.kpad, cs, nu, BROW);
+    const Smem sm = carve<NBUF>(smem, g, a.smem_bytes, a.nchan);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
     const int wu = warp / a.nch, chunk = warp - wu * a.nch;
@@ -402,12 +422,45 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
         // a one-tile CTA starts every buffer at phase 0; a persistent CTA continues
         const uint32_t parity = (uint32_t)(((MULTI ? ts.uses[b] : 0) + i / NBUF) & 1);
         const bool got = mbar_wait_bounded(&sm.full[b], parity, a.wait_ns);
-        if (!__all_sync(0xffffffffu, got)) {
+        if constexpr (BROW) {
+            // the whole CTA builds the stage's difference rows, so it must agree to go on;
+            // this barrier also keeps the rows of the previous stage until all warps are done
+            if (__syncthreads_or(!got)) {
+                if (tid == 0) atomicExch(a.status, (int)DD_ERR_TIMEOUT);
+                ok = false;
+                break;
+            }
+        } else if (!__all_sync(0xffffffffu, got)) {
             if (lane == 0) atomicExch(a.status, (int)DD_ERR_TIMEOUT);
             ok = false;
             break;
         }
-        if constexpr (RL) {
+        if constexpr (BROW) {
+            const unsigned char* buf = smem + b * g.bytes;
+            const uint32_t* rows = (const uint32_t*)buf;
+            const int2* nlist = (const int2*)(buf + g.rec_off + g.w_off);
+            const int2* ent = (const int2*)(buf + g.rec_off) + dmi * cs;
+            const int* lo_all = (const int*)(smem + NBUF * g.bytes);
+            const int c0 = s * cs;
+            const int csn = min(cs, a.nchan - c0);
+            for (int ci = 0; ci < csn; ++ci) {
+                const int2 nn = nlist[ci];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int n = q ? nn.y : nn.x;
+                    if (n <= 0) continue;
+                    const uint32_t* pr = rows + ci * a.lcap;
+                    uint32_t* br = sm.brows + (ci * 2 + q) * a.lcap;
+                    for (int j = tid; j + n < a.lcap; j += blockDim.x) br[j] = pr[j + n] - pr[j];
+                }
+            }
+            __syncthreads();
+            if (d < a.ndm) stage_rl_rows(sm.brows, ent, lo_all + c0, csn, a.lcap, bq, lane_off, acc0);
+#pragma unroll
+            for (int u = 1; u < UPW; ++u)
+                if (d + u < a.ndm)
+                    stage_rl_rows(sm.brows, ent + u * cs, lo_all + c0, csn, a.lcap, bq, lane_off, accr[u - 1]);
+        } else if constexpr (RL) {
             const unsigned char* buf = smem + b * g.bytes;
             const uint32_t* rows = (const uint32_t*)buf;
             const int2* ent = (const int2*)(buf + g.rec_off) + dmi * cs;
@@ -541,8 +594,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_batched(const DedispA
 // barriers, and at least the output transpose area plus the barriers (which sit at the
 // end and survive the transpose).
 template <typename TIN, bool PAIR, int NBUF>
-size_t smem_for(int lcap, int kpad, int cs, int nch, int nchan) {
-    const StageGeom g((int)sizeof(TIN), PAIR, lcap, kpad, cs, kWarps / nch * upw<TIN>());
+size_t smem_for(int lcap, int kpad, int cs, int nch, int nchan, bool brow = false) {
+    const StageGeom g((int)sizeof(TIN), PAIR, lcap, kpad, cs, kWarps / nch * upw<TIN>(), brow);
     size_t smem = (size_t)dedisp_smem_bytes(g, NBUF, nchan);
     const size_t st = (size_t)kStoreBytes + NBUF * 8 + 2 * NBUF * 4;
     if (smem < st) smem = st;
@@ -552,7 +605,8 @@ size_t smem_for(int lcap, int kpad, int cs, int nch, int nchan) {
 template <typename TIN, bool PAIR, int NBUF, bool SHORT = false>
 dd_status run(DedispArgs a, cudaStream_t s) {
     const int nu = kWarps / a.nch * upw<TIN>();
-    const size_t smem = smem_for<TIN, PAIR, NBUF>(a.lcap, a.kpad, a.cs, a.nch, a.nchan);
+    const size_t smem = smem_for<TIN, PAIR, NBUF>(a.lcap, a.kpad, a.cs, a.nch, a.nchan,
+                                                  std::is_same<TIN, uint32_t>::value && SHORT);
     a.smem_bytes = (uint32_t)smem;
     auto kern = k_dedisp<TIN, PAIR, NBUF, SHORT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -733,7 +787,7 @@ void fill_dedisp_args(const dd_plan_s* p, const void* in, int64_t ld, int64_t t_
 
 size_t dedisp_smem_for(const dd_plan_s* p) {
     const int kp = p->pair ? p->kw : 0;
-    if (p->rl) return smem_for<uint32_t, false, kStagesRl>(p->lcap, 0, p->cs, p->nch, p->nchan);
+    if (p->rl) return smem_for<uint32_t, false, kStagesRl>(p->lcap, 0, p->cs, p->nch, p->nchan, p->rl_b);
     if (!p->pair) return smem_for<uint8_t, false, kStagesInt>(p->lcap, kp, p->cs, p->nch, p->nchan);
     if (p->band.in_type == DD_U8) return smem_for<uint8_t, true, kStagesPair>(p->lcap, kp, p->cs, p->nch, p->nchan);
     return smem_for<float, true, kStagesPair>(p->lcap, kp, p->cs, p->nch, p->nchan);
@@ -773,7 +827,7 @@ dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t
     if (e != cudaSuccess) return cuda_status(e);
     DedispArgs a;
     fill_dedisp_args(p, p->d_prefix, ldp, 0, nsamp - p->dmax, out, out_ld, &a);
-    return run<uint32_t, false, kStagesRl>(a, s);
+    return p->rl_b ? run<uint32_t, false, kStagesRl, true>(a, s) : run<uint32_t, false, kStagesRl>(a, s);
 }
 
 dd_status launch_dedisperse_batched(bool u8, bool pair, bool short_taps, const DedispArgs* d_args,

@@ -41,23 +41,28 @@ constexpr long long kWaitNs = 2000000000;  // bound on any device-side barrier w
 // of the CTA's nu warp units and each of the stage's channels, an entry (window start
 // relative to the block's minimum delay for the channel, taps) and, for fp32 plans,
 // the per-tap weights of the unit's two trials as (w0, w1) pairs (kw pairs per entry).
-// Records are stored in this layout in global memory ([block][stage][rec_bytes]) and
-// staged by one bulk copy.
+// With shared difference rows (run-length path, `brow`) an entry is (run start, index of
+// its tap count in the channel's list) and the record ends with each channel's list of
+// at most two tap counts; the CTA then also holds cs x 2 difference rows of lcap words
+// (`bbytes`, outside the ring).  Records are stored in this layout in global memory
+// ([block][stage][rec_bytes]) and staged by one bulk copy.
 struct StageGeom {
-    int rows_bytes, rec_off, rec_bytes, w_off, bytes;
-    __host__ __device__ StageGeom(int esz, bool has_w, int lcap, int kw, int cs, int nu) {
+    int rows_bytes, rec_off, rec_bytes, w_off, bytes, bbytes;
+    __host__ __device__ StageGeom(int esz, bool has_w, int lcap, int kw, int cs, int nu,
+                                  bool brow = false) {
         rows_bytes = (cs * lcap * esz + 15) & ~15;
         rec_off = rows_bytes;
         w_off = 8 * nu * cs;
-        rec_bytes = (w_off + (has_w ? 8 * nu * cs * kw : 0) + 15) & ~15;
+        rec_bytes = (w_off + (has_w ? 8 * nu * cs * kw : 0) + (brow ? 8 * cs : 0) + 15) & ~15;
         bytes = (rec_off + rec_bytes + 127) & ~127;
+        bbytes = brow ? cs * 2 * lcap * 4 : 0;
     }
 };
 
 // Shared memory of a dedispersion CTA beyond its stages: the block's per-channel
 // minimum delays and the pipeline's barriers and counters.
 __host__ __device__ inline int dedisp_smem_bytes(const StageGeom& g, int nbuf, int nchan) {
-    return nbuf * g.bytes + ((4 * nchan + 15) & ~15) + nbuf * 8 + 2 * nbuf * 4;
+    return nbuf * g.bytes + ((4 * nchan + 15) & ~15) + g.bbytes + nbuf * 8 + 2 * nbuf * 4;
 }
 // The output transpose reuses the stage buffers: one row of 32 * kR values per warp.
 constexpr int kStoreBytes = kWarps * 32 * kRMax * 4;
@@ -159,6 +164,7 @@ struct dd_plan_s {
     // (run-length path; uint8 unit weights), and that path's prefix scratch
     int32_t method = DD_METHOD_AUTO;   // requested
     bool rl = false;                   // in use
+    bool rl_b = false;                 // run-length with difference rows shared by the CTA
     uint32_t* d_prefix = nullptr;
     int64_t prefix_elems = 0;
 };

@@ -121,6 +121,27 @@ int32_t union_taps(const dd_plan_s* p, int db) {
     return (int32_t)std::min<int64_t>(u, INT32_MAX);
 }
 
+// Most distinct tap counts among one trial block's trials on any channel (run-length
+// path): the CTA builds one difference row per distinct count, so at most two fit.
+int max_distinct_taps(const dd_plan_s* p, int db) {
+    const int C = p->nchan;
+    int most = 0;
+    for (int d0 = 0; d0 < p->ndm; d0 += db)
+        for (int c = 0; c < C; ++c) {
+            int a = -1, b = -1, n = 0;
+            for (int d = d0; d < std::min(p->ndm, d0 + db); ++d) {
+                const int t = p->taps[(size_t)d * C + c];
+                if (t == a || t == b) continue;
+                if (a < 0) a = t;
+                else if (b < 0) b = t;
+                ++n;
+                if (n > 2) return n;
+            }
+            most = std::max(most, n);
+        }
+    return most;
+}
+
 // Lays the profile tables out as the kernel stages them: one record per (trial block,
 // channel stage).  Entry (unit j, channel ci) = (window start - block minimum, taps);
 // on the pair path the window is the union of the unit's two trials' windows and the
@@ -132,7 +153,7 @@ void build_records(dd_plan_s* p) {
     const int db = tpw * nu;
     const int nst = (C + p->cs - 1) / p->cs;
     const int kw = p->pair ? p->kw : 0;
-    const dd::StageGeom g(stage_esz(p), p->pair, p->lcap, kw, p->cs, nu);
+    const dd::StageGeom g(stage_esz(p), p->pair, p->lcap, kw, p->cs, nu, p->rl_b);
     p->rec_bytes = g.rec_bytes;
     p->rec.assign((size_t)p->nblk * nst * g.rec_bytes, 0);
     for (int b = 0; b < p->nblk; ++b)
@@ -140,6 +161,20 @@ void build_records(dd_plan_s* p) {
             unsigned char* r = p->rec.data() + ((size_t)b * nst + st) * g.rec_bytes;
             int32_t* ent = (int32_t*)r;
             float* w = (float*)(r + g.w_off);
+            int32_t* nlist = (int32_t*)(r + g.w_off);  // difference rows: (n0, n1) per channel
+            if (p->rl_b)
+                for (int ci = 0; ci < p->cs; ++ci) {
+                    const int c = st * p->cs + ci;
+                    if (c >= C) continue;
+                    int a = 0, bb = 0;
+                    for (int d = b * db; d < std::min(p->ndm, (b + 1) * db); ++d) {
+                        const int t = p->taps[(size_t)d * C + c];
+                        if (a == 0) a = t;
+                        else if (t != a && bb == 0) bb = t;
+                    }
+                    nlist[2 * ci] = a;
+                    nlist[2 * ci + 1] = bb;
+                }
             for (int j = 0; j < nu; ++j)
                 for (int ci = 0; ci < p->cs; ++ci) {
                     const int c = st * p->cs + ci;
@@ -154,6 +189,7 @@ void build_records(dd_plan_s* p) {
                     const int e = j * p->cs + ci;
                     ent[2 * e] = (int32_t)(lo - p->blk_lo[(size_t)b * C + c]);
                     ent[2 * e + 1] = (int32_t)(hi - lo);
+                    if (p->rl_b) ent[2 * e + 1] = (hi - lo) == nlist[2 * ci] ? 0 : 1;
                     if (!p->pair) continue;
                     for (int i = 0; i < tpw && d0 + i < p->ndm; ++i) {
                         const size_t dc = (size_t)(d0 + i) * C + c;
@@ -189,12 +225,13 @@ dd_status build_schedule(dd_plan_s* p) {
             const int db = tpw * nu;
             const int64_t span = block_span(p, db, nullptr);
             p->umax = p->pair ? union_taps(p, db) : 0;
+            p->rl_b = p->rl && max_distinct_taps(p, db) <= 2;
             const int32_t kw = p->pair ? ((p->umax + 1) & ~1) : 0;
             const int64_t need = staged_len(p, nch, span);
             if (need > (1 << 22)) continue;
             int cs = cs_want;
             while (cs >= min_cs[pass] &&
-                   dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu),
+                   dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu, p->rl_b),
                                          nbuf, p->nchan) > budgets[pass])
                 --cs;
             if (cs < min_cs[pass]) continue;
@@ -220,12 +257,14 @@ dd_status build_schedule_fixed(dd_plan_s* p, int nch, int cs) {
     const int db = trials_per_unit(p) * nu;
     const int64_t span = block_span(p, db, nullptr);
     p->umax = p->pair ? union_taps(p, db) : 0;
+    const bool rl_b = p->rl && max_distinct_taps(p, db) <= 2;
     const int32_t kw = p->pair ? ((p->umax + 1) & ~1) : 0;
     const int64_t need = staged_len(p, nch, span);
     if (need > (1 << 22)) return DD_ERR_UNSUPPORTED;
-    if (dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu), stages_of(p),
+    if (dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu, rl_b), stages_of(p),
                               p->nchan) > dd::kSmemBudgetOne)
         return DD_ERR_UNSUPPORTED;
+    p->rl_b = rl_b;
     p->nch = nch;
     p->cs = cs;
     p->kw = kw;

@@ -119,3 +119,27 @@ def test_large_lowband_reduced_sampled(dd):
     d_best = int(np.unravel_index(np.argmax(p), p.shape)[0])
     inside = [q for q in cfg["pulses"] if q["t0_ms"] / b.dt_ms < t_out]
     assert min(abs(cfg["dms"][d_best] - q["dm"]) for q in inside) < 5.0
+
+
+def test_runlength_shared_difference_rows_bit_exact(dd):
+    """Tap counts with at most two values per block of 24 trials and channel let the CTA
+    share difference rows; ragged trial blocks, random delays, streamed offsets."""
+    rng = np.random.default_rng(47)
+    C, T, D = 33, 6000, 50
+    I = rng.integers(0, 256, size=(C, T + 16)).astype(np.uint8)
+    delay = rng.integers(0, 700, size=(D, C)).astype(np.int32)
+    taps = np.zeros((D, C), np.int32)
+    for b0 in range(0, D, 24):
+        for c in range(C):
+            pair = rng.integers(1, 400, size=2)
+            taps[b0:b0 + 24, c] = rng.choice(pair, size=min(24, D - b0))
+    plan = dd.Plan(dd.Band(C, 1200.0, 1.0, 1.0, T, "u8"), np.zeros(D))
+    plan.set_profiles(delay=delay, taps=taps)
+    plan.set_method("runlength")
+    assert plan.schedule()["trials_per_cta"] == 24
+    x = _dev(I)
+    out = plan.dedisperse(x, t_offset=16, nsamp=T).cpu().numpy()
+    want = oracle.c_dedisperse(I, delay, taps, t_offset=16, nsamp=T)
+    np.testing.assert_array_equal(out.astype(np.int64), want)
+    plan.set_method("direct")
+    np.testing.assert_array_equal(plan.dedisperse(x, t_offset=16, nsamp=T).cpu().numpy(), out)

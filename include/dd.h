@@ -218,8 +218,9 @@ dd_status dd_plan_get_schedule(dd_plan_t plan, int32_t* nch, int32_t* cs, int32_
  *   DD_METHOD_AUTO (default): RUNLENGTH for uint8 unit-weight plans whose mean tap count
  *     is at least 12, DIRECT otherwise.
  * dd_plan_set_method rebuilds the schedule (DD_ERR_UNSUPPORTED: RUNLENGTH on a weighted
- * or fp32 plan; the method is then unchanged).  dd_plan_get_method reports the method in
- * use (never AUTO).  Batches (below) take DIRECT plans only. */
+ * or fp32 plan; the method is then unchanged).  A run-length plan that later gets weights
+ * sums directly.  dd_plan_get_method reports the method in use (never AUTO).  Batches
+ * (below) take DIRECT plans only. */
 typedef enum {
     DD_METHOD_AUTO = 0,
     DD_METHOD_DIRECT = 1,
@@ -229,8 +230,9 @@ dd_status dd_plan_set_method(dd_plan_t plan, int32_t method);
 dd_status dd_plan_get_method(dd_plan_t plan, int32_t* method);
 
 /* Autotuner: times the plan's dedispersion on the given buffers (as dd_dedisperse with
- * t_offset 0 and the band's nsamp) for each CTA shape (nch 1, 2) and stage size (fp32:
- * 2, 3, 4, 6, 8 channels; uint8: 4, 8, 12, 16) that fits, keeps the fastest, and appends
+ * t_offset 0 and the band's nsamp) for each CTA shape (nch 1, 2) and stage size (fp32 and
+ * run-length: 2, 3, 4, 6, 8 channels; uint8: 4, 8, 12, 16) that fits, keeps the fastest,
+ * and appends
  * it to the text cache at cache_path (may be NULL) under a key of channel count, input
  * type, path, and the powers of two of the trial-block delay spread and the widest tap
  * run.  A cached key is applied without timing (*best_ms = -1).  Synchronises the
@@ -241,9 +243,9 @@ dd_status dd_plan_autotune(dd_plan_t plan, const void* d_in, int64_t in_ld, void
 /* Many beams in one persistent launch (uneven lengths and trial lists; no counterpart in
  * the paper, which describes one beam).  Each beam has its own plan (same input type and
  * path for all, DD_METHOD_DIRECT, else DD_ERR_UNSUPPORTED; the plans must outlive the
- * batch); a beam's block is the band's nsamp samples from column 0.  The work list has one item per CTA tile (beam, trial block,
- * time tile), sorted by estimated cost, largest first; the kernel's CTAs take items
- * from an atomic counter that each launch resets. */
+ * batch); a beam's block is the band's nsamp samples from column 0.  The work list has
+ * one item per CTA tile (beam, trial block, time tile), sorted by estimated cost, largest
+ * first; the kernel's CTAs take items from an atomic counter that each launch resets. */
 typedef struct dd_batch_s* dd_batch_t;
 dd_status dd_batch_create(dd_batch_t* batch, const dd_plan_t* plans, int32_t nbeams);
 /* Binds each beam's device input [nchan][in_ld] and output [ndm][out_ld] (host arrays of

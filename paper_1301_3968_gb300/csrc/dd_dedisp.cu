@@ -3,29 +3,33 @@
 //   out[d][t] = sum_c sum_{k < n_dc} w_dck * I[c][t_offset + t + delta_dc + k]
 //
 // Work decomposition (sm_103a):
-//   * A CTA has kWarps = 8 warps covering 8 / nch warp units x nch time chunks.  On the
+//   * A CTA has kWarps = 8 warps covering 8 / nch warp-groups x nch time chunks.  On the
 //     fp32 path a warp unit sums two adjacent trials from one shared register window
 //     (their delays and tap counts differ by at most a sample or so on a trial list of
-//     eq. trial DMs); on the exact integer path it sums one trial.  A chunk is 32 * kR
-//     outputs and lane l owns outputs chunk_start + l*kR + r, r < kR.  The plan picks
-//     the most trials per CTA whose staged window fits in shared memory.
+//     eq. trial DMs); on the exact integer path a warp sums one trial, on the run-length
+//     path three.  A chunk is 32 * R outputs and lane l owns outputs chunk_start + l*R + r,
+//     r < R (R = kRPair on the pair path, kRInt otherwise).  The plan picks the most
+//     trials per CTA whose staged window fits in shared memory.
 //   * Channels are streamed in stages of cs rows through a ring of NBUF shared-memory
-//     buffers.  For each channel the CTA stages the window that all its trials read --
-//     [T0 + min delta, T0 + tile + max(delta + n)) rounded to 16-byte chunks -- with one
-//     bulk copy (cp.async.bulk, the TMA engine), plus one bulk copy of the stage's
-//     profile record (delays, taps, weights).  Each buffer has a full mbarrier that
-//     counts the copied bytes.
+//     buffers (two on the pair and run-length paths, four on the integer path).  For each
+//     channel the CTA stages the window that all its trials read -- [T0 + min delta,
+//     T0 + tile + max(delta + n)) rounded to 16-byte chunks -- with one bulk copy
+//     (cp.async.bulk, the TMA engine), plus one bulk copy of the stage's profile record
+//     (window starts, taps, weights).  Each buffer has a full mbarrier that counts the
+//     copied bytes.
 //   * Warps do not synchronise with each other per stage: after consuming a buffer each
 //     warp increments the buffer's counter, and the last of the 8 refills it with the
-//     stage NBUF ahead.  A warp can run up to NBUF-1 stages ahead of the slowest one.
+//     stage NBUF ahead.  A warp can run up to NBUF-1 stages ahead of the slowest one.  (The
+//     run-length path with shared difference rows is the exception: the CTA builds the
+//     rows together, with one barrier per stage.)
 //   * Every wait is bounded by time; a wait that runs out records DD_ERR_TIMEOUT in the
 //     plan's status word, the CTA drains its own copies in flight and returns.
-//   * Inner loop: a register window of kR samples slides along the taps; each tap
-//     costs one shared-memory load, one weight-pair broadcast and kR packed pair FMAs
-//     (fma.rn.f32x2: 2 x kR fp32 FMAs; or one load and kR exact int32 adds for uint8
-//     unit-weight plans, or, on the run-length path, two loads and one add per output
-//     whatever the tap count).  kR is odd, so the
-//     lane-strided loads hit 32 distinct banks.
+//   * Inner loop: a register window of R samples slides along the taps.  Pair path: per
+//     tap one shared-memory load, one weight-pair broadcast and R packed FMAs
+//     (fma.rn.f32x2, 2 x R fp32 FMAs).  Integer path: per two taps one load and R
+//     three-input adds.  Run-length path: per output two loads and one add (one load with
+//     shared difference rows), whatever the tap count.  R is odd, so the lane-strided
+//     loads hit 32 distinct banks.
 //   * Sums run over channels, then taps, in a fixed order, so results are
 //     deterministic.
 //   * Results are transposed through shared memory so that global stores coalesce.
@@ -36,8 +40,6 @@
 
 namespace dd {
 namespace {
-
-
 
 __device__ __forceinline__ uint32_t su32(const void* p) {
     return (uint32_t)__cvta_generic_to_shared(p);
@@ -285,9 +287,9 @@ __device__ __forceinline__ void stage_rl_rows(const uint32_t* brows, const int2*
 // One stage of one warp unit on the fp32 path: two adjacent trials share the register
 // window.  The entry's window is the union of the two trials' windows, and its weights
 // are (w0, w1) pairs that are zero where a trial has no tap, so each tap costs one
-// window load, one weight-pair broadcast and kR packed FMAs (2 x kR fp32 FMAs).  The
+// window load, one weight-pair broadcast and R packed FMAs (2 x R fp32 FMAs).  The
 // window keeps each sample duplicated in both halves of a 64-bit register.  SHORT: the
-// plan's union windows are at most kR taps, so the taps are one unrolled pass.  Sums
+// plan's union windows are at most R taps, so the taps are one unrolled pass.  Sums
 // run over channels, then taps, in a fixed order (deterministic); single-precision
 // accumulation of the ~10^3-10^4 terms of an output stays orders of magnitude inside
 // the 1e-5 scale-aware bound.

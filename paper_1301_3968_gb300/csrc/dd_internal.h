@@ -64,7 +64,7 @@ struct StageGeom {
 __host__ __device__ inline int dedisp_smem_bytes(const StageGeom& g, int nbuf, int nchan) {
     return nbuf * g.bytes + ((4 * nchan + 15) & ~15) + g.bbytes + nbuf * 8 + 2 * nbuf * 4;
 }
-// The output transpose reuses the stage buffers: one row of 32 * kR values per warp.
+// The output transpose reuses the stage buffers: one row of 32 * R values per warp.
 constexpr int kStoreBytes = kWarps * 32 * kRMax * 4;
 
 // Arguments of one dedispersion launch (one plan, one input block); the batched

@@ -19,6 +19,7 @@
 
 #include "dd_async.cuh"
 #include "dd_internal.h"
+#include "dd_packed.cuh"
 
 namespace dd {
 namespace {
@@ -118,9 +119,11 @@ __global__ void __launch_bounds__(256, 2) k_bwd_w(const float* in, int64_t ld, i
         cp_async_commit();
     };
     for (int kc = 0; kc < kout; kc += kLags) {
-        float acc[kLags];
+        // lags in packed pairs (k, k + 16), k < 16
+        constexpr int H = kLags / 2;
+        uint64_t acc2[H];
 #pragma unroll
-        for (int k = 0; k < kLags; ++k) acc[k] = 0.f;
+        for (int k = 0; k < H; ++k) acc2[k] = 0ull;
         stage(0, buf0);
         for (int it = 0; it < ntile; ++it) {
             if (it + 1 < ntile) {
@@ -134,20 +137,25 @@ __global__ void __launch_bounds__(256, 2) k_bwd_w(const float* in, int64_t ld, i
                 const float* xs = (it & 1) ? buf1 : buf0;
                 const float* x = xs + off + kc + lane * kSeg;
                 const float* gv = xs + xstride + warp * kTileW + lane * kSeg;
-                float win[kLags];
+                // window of sample pairs (x[p], x[p + 16]) for positions p = tt .. tt + 15,
+                // position p in register p mod 16; lag pair k reads position tt + k
+                uint64_t win[H];
 #pragma unroll
-                for (int k = 0; k < kLags; ++k) win[k] = x[k];
+                for (int k = 0; k < H; ++k) win[k] = pk2(x[k], x[k + H]);
 #pragma unroll
                 for (int tt = 0; tt < kSeg; ++tt) {
-                    const float gt = gv[tt];
+                    const uint64_t gt = pk_dup(gv[tt]);
 #pragma unroll
-                    for (int k = 0; k < kLags; ++k) acc[k] = fmaf(gt, win[(k + tt) % kLags], acc[k]);
-                    win[tt % kLags] = x[tt + kLags];
+                    for (int k = 0; k < H; ++k) fma2(acc2[k], gt, win[(k + tt) % H]);
+                    win[tt % H] = pk2(x[tt + H], x[tt + kLags]);
                 }
             }
             __syncthreads();  // this buffer is restaged by the next iteration but one
         }
         if (active) {
+            float acc[kLags];
+#pragma unroll
+            for (int k = 0; k < H; ++k) unpk(acc2[k], acc[k], acc[k + H]);
 #pragma unroll
             for (int k = 0; k < kLags; ++k) {
                 const float v = warp_sum(acc[k]);

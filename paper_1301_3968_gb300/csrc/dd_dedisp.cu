@@ -37,6 +37,7 @@
 #include <type_traits>
 
 #include "dd_internal.h"
+#include "dd_packed.cuh"
 
 namespace dd {
 namespace {
@@ -116,20 +117,9 @@ __device__ __forceinline__ TACC cvt(TIN v) {
     return (TACC)v;
 }
 
-// Packed pairs for the fp32 pair units: one 64-bit register holds (trial 0, trial 1)
-// accumulators or weights, or a window sample duplicated in both halves, and one
-// fma.rn.f32x2 performs both trials' fused multiply-adds (each exactly fmaf).
-__device__ __forceinline__ uint64_t pk_dup(float x) {
-    uint64_t r;
-    asm("mov.b64 %0, {%1, %1};" : "=l"(r) : "f"(x));
-    return r;
-}
-__device__ __forceinline__ void fma2(uint64_t& acc, uint64_t w, uint64_t x) {
-    asm("fma.rn.f32x2 %0, %1, %2, %0;" : "+l"(acc) : "l"(w), "l"(x));
-}
-__device__ __forceinline__ void unpk(uint64_t v, float& lo, float& hi) {
-    asm("mov.b64 {%0, %1}, %2;" : "=f"(lo), "=f"(hi) : "l"(v));
-}
+// Packed pairs for the fp32 pair units (dd_packed.cuh): one 64-bit register holds
+// (trial 0, trial 1) accumulators or weights, or a window sample duplicated in both
+// halves, and one fma.rn.f32x2 performs both trials' fused multiply-adds.
 
 struct Smem {
     unsigned char* stages;

@@ -205,7 +205,7 @@ __device__ void issue_stage(const DedispArgs& a, const StageGeom& g, const Smem&
 // after the tap, sample k (no longer needed) is replaced by sample k + R.  Taps go two
 // at a time, one three-input add per output (the second tap's last output reads sample
 // R + k, loaded before the add).  SHORT: no tap run is longer than R, one unrolled pass.
-template <typename TIN, bool SHORT>
+template <typename TIN, int SHORT>
 __device__ __forceinline__ void stage_int(const TIN* rows, const int2* ent, const int* lo,
                                           int csn, int lcap, int bq, int lane_off,
                                           int (&acc)[kRInt]) {
@@ -219,7 +219,7 @@ __device__ __forceinline__ void stage_int(const TIN* rows, const int2* ent, cons
         int win[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) win[j] = (int)p[j];
-        for (int k0 = 0; k0 < (SHORT ? 1 : n); k0 += R) {
+        for (int k0 = 0; k0 < (SHORT == 1 ? 1 : n); k0 += R) {
 #pragma unroll
             for (int kk = 0; kk < R; kk += 2) {
                 if (k0 + kk >= n) break;
@@ -283,7 +283,7 @@ __device__ __forceinline__ void stage_rl_rows(const uint32_t* brows, const int2*
 // run over channels, then taps, in a fixed order (deterministic); single-precision
 // accumulation of the ~10^3-10^4 terms of an output stays orders of magnitude inside
 // the 1e-5 scale-aware bound.
-template <typename TIN, bool SHORT>
+template <typename TIN, int SHORT>
 __device__ __forceinline__ void stage_pair(const TIN* rows, const int2* ent, const float2* wts,
                                            const int* lo, int csn, int lcap, int kw, int bq,
                                            int lane_off, uint64_t (&acc)[kRPair]) {
@@ -299,7 +299,7 @@ __device__ __forceinline__ void stage_pair(const TIN* rows, const int2* ent, con
         uint64_t win[R];
 #pragma unroll
         for (int j = 0; j < R; ++j) win[j] = pk_dup((float)p[j]);
-        if constexpr (SHORT) {
+        if constexpr (SHORT == 1) {
 #pragma unroll
             for (int kk = 0; kk < R; ++kk) {
                 if (kk >= n) break;
@@ -307,6 +307,18 @@ __device__ __forceinline__ void stage_pair(const TIN* rows, const int2* ent, con
 #pragma unroll
                 for (int r = 0; r < R; ++r) fma2(acc[r], w, win[(r + kk) % R]);
                 win[kk] = pk_dup((float)p[R + kk]);
+            }
+        } else if constexpr (SHORT == 2) {  // at most 2R taps: two unrolled passes
+#pragma unroll
+            for (int h = 0; h < 2; ++h) {
+#pragma unroll
+                for (int kk = 0; kk < R; ++kk) {
+                    if (h * R + kk >= n) break;
+                    const uint64_t w = wk[h * R + kk];
+#pragma unroll
+                    for (int r = 0; r < R; ++r) fma2(acc[r], w, win[(r + kk) % R]);
+                    win[kk] = pk_dup((float)p[R + h * R + kk]);
+                }
             }
         } else {
             for (int k0 = 0; k0 < n; k0 += R) {
@@ -351,7 +363,7 @@ struct TileState {
 // Returns false (on every thread) if a bounded wait ran out.
 // `a` is taken by value: with a reference to the kernel parameter the compiler picked
 // a register allocation for the FMA loop that ran 11 % slower.
-template <typename TIN, bool PAIR, int NBUF, bool MULTI, bool SHORT>
+template <typename TIN, bool PAIR, int NBUF, bool MULTI, int SHORT>
 __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* smem, int blk,
                                             int tx, TileState& ts) {
     constexpr int R = lane_r(PAIR);
@@ -360,7 +372,7 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
     constexpr int TPW = PAIR ? 2 : 1;   // trials per warp unit
     constexpr bool RL = std::is_same<TIN, uint32_t>::value;
     // SHORT on the run-length path: the CTA shares difference rows per stage
-    constexpr bool BROW = RL && SHORT;
+    constexpr bool BROW = RL && SHORT != 0;
     constexpr int UPW = upw<TIN>();     // warp units per warp
     using TACC = typename std::conditional<PAIR, float, int>::type;
     const int cs = a.cs;
@@ -545,7 +557,7 @@ __device__ __forceinline__ unsigned char* pipeline_area(unsigned char* smem, siz
     return smem + smem_bytes - (size_t)(nbuf * 8 + 2 * nbuf * 4);
 }
 
-template <typename TIN, bool PAIR, int NBUF, bool SHORT>
+template <typename TIN, bool PAIR, int NBUF, int SHORT>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ TileState ts;
@@ -557,7 +569,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
 // Persistent form: each CTA takes work items (beam, trial block, time tile) from an
 // atomic counter until none remain.  Items are sorted by estimated cost, largest
 // first, so the uneven beams finish together.  The counter is reset before each launch.
-template <typename TIN, bool PAIR, int NBUF, bool SHORT>
+template <typename TIN, bool PAIR, int NBUF, int SHORT>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_batched(const DedispArgs* beams,
                                                                     const BatchItem* items,
                                                                     int32_t nitems, int32_t* counter,
@@ -594,11 +606,11 @@ size_t smem_for(int lcap, int kpad, int cs, int nch, int nchan, bool brow = fals
     return (smem + 15) & ~(size_t)15;
 }
 
-template <typename TIN, bool PAIR, int NBUF, bool SHORT = false>
+template <typename TIN, bool PAIR, int NBUF, int SHORT = 0>
 dd_status run(DedispArgs a, cudaStream_t s) {
     const int nu = kWarps / a.nch * upw<TIN>();
     const size_t smem = smem_for<TIN, PAIR, NBUF>(a.lcap, a.kpad, a.cs, a.nch, a.nchan,
-                                                  std::is_same<TIN, uint32_t>::value && SHORT);
+                                                  std::is_same<TIN, uint32_t>::value && SHORT != 0);
     a.smem_bytes = (uint32_t)smem;
     auto kern = k_dedisp<TIN, PAIR, NBUF, SHORT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -612,7 +624,7 @@ dd_status run(DedispArgs a, cudaStream_t s) {
     return cuda_status(cudaGetLastError());
 }
 
-template <typename TIN, bool PAIR, int NBUF, bool SHORT = false>
+template <typename TIN, bool PAIR, int NBUF, int SHORT = 0>
 dd_status run_batched(const DedispArgs* d_args, const BatchItem* d_items, int32_t nitems,
                       int32_t* d_counter, size_t smem, int grid, cudaStream_t s) {
     auto kern = k_dedisp_batched<TIN, PAIR, NBUF, SHORT>;
@@ -624,7 +636,7 @@ dd_status run_batched(const DedispArgs* d_args, const BatchItem* d_items, int32_
     return cuda_status(cudaGetLastError());
 }
 
-template <typename TIN, bool PAIR, int NBUF, bool SHORT = false>
+template <typename TIN, bool PAIR, int NBUF, int SHORT = 0>
 int blocks_per_sm(size_t smem) {
     int n = 0;
     auto kern = k_dedisp_batched<TIN, PAIR, NBUF, SHORT>;
@@ -794,10 +806,17 @@ dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_
     a.split_ld = split_ld;
     const bool u8 = p->band.in_type == DD_U8;
     if (!p->pair)
-        return p->kmax <= kRInt ? run<uint8_t, false, kStagesInt, true>(a, s) : run<uint8_t, false, kStagesInt>(a, s);
-    const bool short_taps = p->umax <= kRPair;
-    if (u8) return short_taps ? run<uint8_t, true, kStagesPair, true>(a, s) : run<uint8_t, true, kStagesPair>(a, s);
-    return short_taps ? run<float, true, kStagesPair, true>(a, s) : run<float, true, kStagesPair>(a, s);
+        return p->kmax <= kRInt ? run<uint8_t, false, kStagesInt, 1>(a, s) : run<uint8_t, false, kStagesInt>(a, s);
+    // union windows of at most R taps: one unrolled pass; at most 2R: two; longer: a loop
+    const int passes = p->umax <= kRPair ? 1 : (p->umax <= 2 * kRPair ? 2 : 0);
+    if (u8) {
+        if (passes == 1) return run<uint8_t, true, kStagesPair, 1>(a, s);
+        if (passes == 2) return run<uint8_t, true, kStagesPair, 2>(a, s);
+        return run<uint8_t, true, kStagesPair>(a, s);
+    }
+    if (passes == 1) return run<float, true, kStagesPair, 1>(a, s);
+    if (passes == 2) return run<float, true, kStagesPair, 2>(a, s);
+    return run<float, true, kStagesPair>(a, s);
 }
 
 // Run-length path: prefix sums of columns t_offset .. t_offset + nsamp - 1 into the
@@ -819,26 +838,26 @@ dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t
     if (e != cudaSuccess) return cuda_status(e);
     DedispArgs a;
     fill_dedisp_args(p, p->d_prefix, ldp, 0, nsamp - p->dmax, out, out_ld, &a);
-    return p->rl_b ? run<uint32_t, false, kStagesRl, true>(a, s) : run<uint32_t, false, kStagesRl>(a, s);
+    return p->rl_b ? run<uint32_t, false, kStagesRl, 1>(a, s) : run<uint32_t, false, kStagesRl>(a, s);
 }
 
 dd_status launch_dedisperse_batched(bool u8, bool pair, bool short_taps, const DedispArgs* d_args,
                                     const BatchItem* d_items, int32_t nitems, int32_t* d_counter,
                                     size_t smem, int grid, cudaStream_t s) {
     if (!pair)
-        return short_taps ? run_batched<uint8_t, false, kStagesInt, true>(d_args, d_items, nitems, d_counter, smem, grid, s)
+        return short_taps ? run_batched<uint8_t, false, kStagesInt, 1>(d_args, d_items, nitems, d_counter, smem, grid, s)
                           : run_batched<uint8_t, false, kStagesInt>(d_args, d_items, nitems, d_counter, smem, grid, s);
     if (u8)
-        return short_taps ? run_batched<uint8_t, true, kStagesPair, true>(d_args, d_items, nitems, d_counter, smem, grid, s)
+        return short_taps ? run_batched<uint8_t, true, kStagesPair, 1>(d_args, d_items, nitems, d_counter, smem, grid, s)
                           : run_batched<uint8_t, true, kStagesPair>(d_args, d_items, nitems, d_counter, smem, grid, s);
-    return short_taps ? run_batched<float, true, kStagesPair, true>(d_args, d_items, nitems, d_counter, smem, grid, s)
+    return short_taps ? run_batched<float, true, kStagesPair, 1>(d_args, d_items, nitems, d_counter, smem, grid, s)
                       : run_batched<float, true, kStagesPair>(d_args, d_items, nitems, d_counter, smem, grid, s);
 }
 
 int dedisp_batched_blocks_per_sm(bool u8, bool pair, bool short_taps, size_t smem) {
-    if (!pair) return short_taps ? blocks_per_sm<uint8_t, false, kStagesInt, true>(smem) : blocks_per_sm<uint8_t, false, kStagesInt>(smem);
-    if (u8) return short_taps ? blocks_per_sm<uint8_t, true, kStagesPair, true>(smem) : blocks_per_sm<uint8_t, true, kStagesPair>(smem);
-    return short_taps ? blocks_per_sm<float, true, kStagesPair, true>(smem) : blocks_per_sm<float, true, kStagesPair>(smem);
+    if (!pair) return short_taps ? blocks_per_sm<uint8_t, false, kStagesInt, 1>(smem) : blocks_per_sm<uint8_t, false, kStagesInt>(smem);
+    if (u8) return short_taps ? blocks_per_sm<uint8_t, true, kStagesPair, 1>(smem) : blocks_per_sm<uint8_t, true, kStagesPair>(smem);
+    return short_taps ? blocks_per_sm<float, true, kStagesPair, 1>(smem) : blocks_per_sm<float, true, kStagesPair>(smem);
 }
 
 }  // namespace dd

@@ -455,7 +455,8 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
                     if (n <= 0) continue;
                     const uint32_t* pr = rows + ci * a.lcap;
                     uint32_t* br = sm.brows + (ci * 2 + q) * a.lcap;
-                    for (int j = tid; j + n < a.lcap; j += blockDim.x) br[j] = pr[j + n] - pr[j];
+#pragma unroll 4
+                    for (int j = tid; j + n < a.lcap; j += kWarps * 32) br[j] = pr[j + n] - pr[j];
                 }
             }
             __syncthreads();

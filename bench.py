@@ -437,8 +437,15 @@ def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, 
             plan.dedisperse(x, t_offset=t0, nsamp=n + dmax, out=out)
             plan.boxcar_snr(out, widths, mean, sd, t_len=n)
 
+    def fused_all():
+        for t0 in starts:
+            n = min(chunk, t_out - t0)
+            plan.dedisperse_boxcar(x, widths, mean, sd, t_offset=t0, nsamp=n + dmax)
+
     dd_ms = _ev_time(dedisp_all, 2, flush, stream)
     st_ms = _ev_time(step_all, 2, flush, stream)
+    fu_ms = _ev_time(fused_all, 2, flush, stream)
+    fu_status = plan.device_status()
     units = float(plan.ndm) * t_out
     dct = units * b.nchan
     # graded work of exact unit-weight sums: min(n, 2) additions per (trial, channel,
@@ -454,6 +461,8 @@ def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, 
         "dedisp_value": units / (dd_ms / 1e3), "step_value": units / (st_ms / 1e3), "unit": UNIT,
         "trial_channel_samples_per_s": dct / (dd_ms / 1e3),
         "realtime_factor": (t_out * b.dt_ms / 1e3) / (st_ms / 1e3),
+        "fused_step_ms": fu_ms, "fused_over_step": fu_ms / st_ms, "fused_status": fu_status,
+        "fused_series_bytes_not_stored": plan.ndm * chunk * 4,
         "graded_adds_per_block": graded,
         "graded_tops": graded / (dd_ms / 1e3) / 1e12,
         "bound": "shared-memory loads (2 per trial, channel and output; see profiles)",

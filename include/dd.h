@@ -28,7 +28,8 @@
  *   - No call here allocates device memory except dd_plan_create / dd_set_profiles /
  *     the first device call on a plan (tables), dd_boxcar_snr when the width count
  *     grows (normaliser workspace), dd_dedisperse on a run-length plan when nsamp
- *     grows (prefix scratch) and the first dd_backward (adjoint workspace).
+ *     grows (prefix scratch), dd_dedisperse_boxcar when its scratch grows, and the
+ *     first dd_backward (adjoint workspace).
  */
 #ifndef DD_H
 #define DD_H
@@ -185,6 +186,33 @@ dd_status dd_boxcar_snr_noalloc(dd_plan_t plan, const void* d_series, int64_t ld
                                 float thresh, dd_candidate* d_cands, int32_t cap,
                                 int32_t* d_ncands, void* stream);
 
+/* eq. p_dedisp fused with the boxcar S/N of dd_boxcar_snr (eq. snr; Sec. 5): the same
+ * results as dd_dedisperse(plan, d_in, in_ld, t_offset, nsamp, x, ...) followed by
+ * dd_boxcar_snr(plan, x, ..., nsamp - d_max, widths, ...), bit for bit, but the
+ * dedispersed series x is never written to device memory: the dedispersion CTAs scan
+ * their finished tiles in shared memory (a few C = wmax - 1 outputs per strip boundary
+ * go through plan-owned scratch).  For a caller that only needs the detections.
+ * Limits (DD_ERR_UNSUPPORTED otherwise): integer plans (uint8 input, unit weights; both
+ * tap-sum methods), contiguous widths (w_j = w_0 + j), wmax - 1 <= 992 * nch (the
+ * schedule's tile), and nsamp <= 2^24 on the run-length path.  Every boxcar sum of
+ * x - o_d (o_d the normaliser's per-trial integer offset) must fit int32: the kernel
+ * checks wmax * |x - o_d| < 2^31 per output and otherwise records DD_ERR_OVERFLOW in
+ * the plan's device status word (dd_get_device_status), the results of that call being
+ * undefined; dd_boxcar_snr on the stored series handles that case with 64-bit sums.
+ * Other arguments, outputs and errors as dd_dedisperse and dd_boxcar_snr.  Allocates
+ * plan-owned device scratch when the sizes grow: the merged maxima (8 bytes per trial
+ * and width), the carried outputs (4 C bytes per trial and strip) and the seams (8 C
+ * bytes per trial and strip boundary). */
+dd_status dd_dedisperse_boxcar(dd_plan_t plan, const void* d_in, int64_t in_ld, int64_t t_offset,
+                               int64_t nsamp, const int32_t* widths, int32_t nw,
+                               const double* d_chan_mean, const double* d_chan_std,
+                               float* d_peak_snr, int32_t* d_peak_t, float thresh,
+                               dd_candidate* d_cands, int32_t cap, int32_t* d_ncands, void* stream);
+
+/* Test hook: the number of time strips of the next dd_dedisperse_boxcar calls (capped
+ * at the number of tiles; 0 restores the automatic choice).  Errors: DD_ERR_ARG. */
+dd_status dd_test_set_fused_strips(dd_plan_t plan, int32_t nstrip);
+
 /* Adjoint of the weighted map of eq. p_dedisp (no counterpart in the paper): given
  * g = d(loss)/d(out) (d_gout [ndm][gout_ld] fp32, nsamp - d_max valid columns),
  *   d_gw [ndm][nchan][kmax] : gw_dck   = sum_t g[d][t] I[c][t_offset + t + delta + k]
@@ -285,7 +313,6 @@ dd_status dd_get_device_status(dd_plan_t plan, int32_t* code, void* stream);
  * Errors: DD_ERR_ARG. */
 dd_status dd_test_set_wait(dd_plan_t plan, int32_t skip_stage, int64_t wait_ns);
 
-/* Releases the plan's host and device memory (after its work has finished). */
 /* Profile construction (host only).
  *
  * dd_predict_rect: the cell-averaged power of eq. Pavg for the rectangular scattered pulse
@@ -344,6 +371,7 @@ dd_status dd_detector_profile(const double* pbar, int32_t nchan, int32_t nt, con
  * Errors: DD_ERR_ARG, DD_ERR_OOM, DD_ERR_CUDA. */
 dd_status dd_alu_peak(int32_t kind, double* ops_per_s, void* stream);
 
+/* Releases the plan's host and device memory (after its work has finished). */
 dd_status dd_plan_destroy(dd_plan_t plan);
 
 /* Static, human-readable name of a status code. */

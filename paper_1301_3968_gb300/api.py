@@ -277,6 +277,35 @@ class Plan:
                                               _ptr(cands), cap, _ptr(ncand), _stream(stream)),
               "dd_boxcar_snr_noalloc")
 
+    def dedisperse_boxcar(self, x: torch.Tensor, widths, mean: torch.Tensor, sd: torch.Tensor,
+                          t_offset: int = 0, nsamp: int | None = None, thresh: float | None = None,
+                          cap: int = 0, stream=None):
+        """eq. p_dedisp fused with the boxcar S/N (dd_dedisperse_boxcar): the results of
+        dedisperse() followed by boxcar_snr() on its output, without storing the dedispersed
+        series.  Returns (peak_snr [D][W], peak_t [D][W], cands)."""
+        ld = self._check_input(x)
+        nsamp = (x.shape[1] - t_offset) if nsamp is None else nsamp
+        wl = np.ascontiguousarray(widths, dtype=np.int32)
+        dev = x.device
+        peak = torch.empty((self.ndm, len(wl)), dtype=torch.float32, device=dev)
+        arg = torch.empty((self.ndm, len(wl)), dtype=torch.int32, device=dev)
+        cands = ncand = None
+        if thresh is not None and cap > 0:
+            cands = torch.zeros((cap, 4), dtype=torch.int32, device=dev)
+            ncand = torch.zeros(1, dtype=torch.int32, device=dev)
+        check(self._lib.dd_dedisperse_boxcar(self._h, _ptr(x), ld, t_offset, nsamp, _np_ptr(wl), len(wl),
+                                             _ptr(mean), _ptr(sd), _ptr(peak), _ptr(arg),
+                                             float(thresh if thresh is not None else np.inf),
+                                             _ptr(cands), int(cap), _ptr(ncand), _stream(stream)),
+              "dd_dedisperse_boxcar")
+        if cands is None:
+            return peak, arg, None
+        return peak, arg, (cands, ncand)
+
+    def test_set_fused_strips(self, nstrip: int) -> None:
+        """Test hook: time strips of the fused launches (0 = automatic)."""
+        check(self._lib.dd_test_set_fused_strips(self._h, int(nstrip)), "dd_test_set_fused_strips")
+
     def backward(self, x: torch.Tensor, gout: torch.Tensor, t_offset: int = 0,
                  nsamp: int | None = None, want_gw: bool = True, want_gin: bool = True,
                  stream=None):

@@ -19,7 +19,7 @@ OUT_DIR = os.path.join(HERE, "_build")
 LIB = os.path.join(OUT_DIR, "libdd.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["dd_plan.cpp", "dd_dedisp.cu", "dd_boxcar.cu", "dd_adjoint.cu", "dd_noalloc.cu", "dd_batch.cpp",
-           "dd_peak.cu", "dd_select.cpp"]
+           "dd_peak.cu", "dd_select.cpp", "dd_fused.cu"]
 
 
 def _nvcc() -> str:

@@ -681,10 +681,9 @@ dd_status launch_boxcar_scratch(dd_plan_s* p, const void* x, int64_t ld, int64_t
     return dispatch_boxcar(p, a, widths, nw, s, false);
 }
 
-dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
-                        const int32_t* widths, int32_t nw, const double* mean, const double* sd,
-                        float* peak, int32_t* arg, float thresh, dd_candidate* cands, int32_t cap,
-                        int32_t* ncands, cudaStream_t s) {
+// The normaliser of the plan's trials for a width list: dev.off, dev.mu, dev.isd.
+dd_status launch_norm(dd_plan_s* p, const int32_t* widths, int32_t nw, const double* mean,
+                      const double* sd, cudaStream_t s) {
     dd_status st = ensure_norm_ws(p, nw);
     if (st != DD_OK) return st;
     cudaError_t e = cudaSuccess;
@@ -705,8 +704,15 @@ dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
     k_norm<<<p->ndm, 256, red, s>>>(p->dev.taps, p->unit ? nullptr : p->dev.w, p->kpad, p->nchan,
                                     mean, sd, p->dev.widths, nw, p->out_int ? 1 : 0, p->dev.off,
                                     p->dev.mu, p->dev.isd);
-    e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(cudaGetLastError());
+}
+
+dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
+                        const int32_t* widths, int32_t nw, const double* mean, const double* sd,
+                        float* peak, int32_t* arg, float thresh, dd_candidate* cands, int32_t cap,
+                        int32_t* ncands, cudaStream_t s) {
+    const dd_status st = launch_norm(p, widths, nw, mean, sd, s);
+    if (st != DD_OK) return st;
     BoxArgs a;
     a.x = x;
     a.ld = ld;

@@ -33,11 +33,13 @@
 //   * Sums run over channels, then taps, in a fixed order, so results are
 //     deterministic.
 //   * Results are transposed through shared memory so that global stores coalesce.
+#include <algorithm>
 #include <cstdint>
 #include <type_traits>
 
 #include "dd_internal.h"
 #include "dd_packed.cuh"
+#include "dd_fused_scan.cuh"
 
 namespace dd {
 namespace {
@@ -363,9 +365,12 @@ struct TileState {
 // Returns false (on every thread) if a bounded wait ran out.
 // `a` is taken by value: with a reference to the kernel parameter the compiler picked
 // a register allocation for the FMA loop that ran 11 % slower.
-template <typename TIN, bool PAIR, int NBUF, bool MULTI, int SHORT>
+// FUSED: instead of storing the tile, scan it for boxcar maxima (fa: the scan's
+// arguments; the CTA's strip is tiles tx0 .. tx1 - 1, index `strip`).
+template <typename TIN, bool PAIR, int NBUF, bool MULTI, int SHORT, bool FUSED = false>
 __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* smem, int blk,
-                                            int tx, TileState& ts) {
+                                            int tx, TileState& ts, const FusedArgs* fa = nullptr,
+                                            int strip = 0, int tx0 = 0, int tx1 = 0) {
     constexpr int R = lane_r(PAIR);
     constexpr int TT = 32 * R;          // outputs per warp time chunk
     constexpr int Q = Elem<TIN>::Q;
@@ -516,6 +521,12 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
     if (MULTI && tid == 0)
         for (int b = 0; b < NBUF && b < nloc; ++b) ts.uses[b] += (nloc - b + NBUF - 1) / NBUF;
 
+    if constexpr (FUSED) {
+        static_assert(!PAIR, "the fused scan takes integer sums");
+        fused::epilogue<UPW, RL ? UPW - 1 : 1>(a, *fa, smem, blk, wu, chunk, lane, d, t0, strip, tx,
+                                               tx0, tx1, acc0, accr);
+        return true;
+    }
     // transpose through shared memory and store coalesced, one trial row at a time
     TACC* out = (TACC*)a.out + (int64_t)split * a.split_ld;
     float acc1[PAIR ? R : 1];
@@ -595,6 +606,21 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_batched(const DedispA
     }
 }
 
+// Fused dedispersion + boxcar scan: CTA (strip, trial block) walks the strip's tiles.
+template <typename TIN, int NBUF, int SHORT>
+__global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_fused(DedispArgs a, const FusedArgs f) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ TileState ts;
+    if (threadIdx.x == 0) init_pipeline<NBUF>(pipeline_area(smem, a.smem_bytes, NBUF), ts);
+    __syncthreads();
+    const int strip = blockIdx.x;
+    const int tx0 = (int)((int64_t)strip * f.tiles / f.nstrip);
+    const int tx1 = (int)((int64_t)(strip + 1) * f.tiles / f.nstrip);
+    for (int tx = tx0; tx < tx1; ++tx)
+        if (!dedisp_tile<TIN, false, NBUF, true, SHORT, true>(a, smem, blockIdx.y, tx, ts, &f, strip, tx0, tx1))
+            break;
+}
+
 // Dynamic shared memory of a launch: the plan's stages, per-channel minima and
 // barriers, and at least the output transpose area plus the barriers (which sit at the
 // end and survive the transpose).
@@ -635,6 +661,29 @@ dd_status run_batched(const DedispArgs* d_args, const BatchItem* d_items, int32_
     if (e != cudaSuccess) return cuda_status(e);
     kern<<<grid, kWarps * 32, smem, s>>>(d_args, d_items, nitems, d_counter, (uint32_t)smem);
     return cuda_status(cudaGetLastError());
+}
+
+template <typename TIN, int NBUF, int SHORT>
+dd_status run_fused(DedispArgs a, const FusedArgs& f, size_t smem, cudaStream_t s) {
+    a.smem_bytes = (uint32_t)smem;
+    auto kern = k_dedisp_fused<TIN, NBUF, SHORT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int tpc = kWarps / a.nch * upw<TIN>();
+    dim3 grid((unsigned)f.nstrip, (unsigned)((a.ndm + tpc - 1) / tpc));
+    if (grid.y > 65535) return DD_ERR_UNSUPPORTED;
+    kern<<<grid, kWarps * 32, smem, s>>>(a, f);
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename TIN, int NBUF, int SHORT>
+int fused_bps(size_t smem) {
+    int n = 0;
+    auto kern = k_dedisp_fused<TIN, NBUF, SHORT>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kWarps * 32, smem) != cudaSuccess) return 0;
+    return n;
 }
 
 template <typename TIN, bool PAIR, int NBUF, int SHORT = 0>
@@ -822,9 +871,10 @@ dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_
 
 // Run-length path: prefix sums of columns t_offset .. t_offset + nsamp - 1 into the
 // plan's scratch, then the run-length sums over them.
-dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
-                               int64_t nsamp, void* out, int64_t out_ld, cudaStream_t s) {
+dd_status launch_prefix(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset, int64_t nsamp,
+                        int64_t* ldp_out, cudaStream_t s) {
     const int64_t ldp = (nsamp + 1 + 3) & ~(int64_t)3;
+    *ldp_out = ldp;
     const int64_t need = ldp * p->nchan;
     if (need > p->prefix_elems) {
         cudaFree(p->d_prefix);
@@ -835,8 +885,14 @@ dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t
         p->prefix_elems = need;
     }
     k_prefix<<<p->nchan, 256, 0, s>>>((const uint8_t*)in, ld, t_offset, nsamp, p->d_prefix, ldp);
-    cudaError_t e = cudaGetLastError();
-    if (e != cudaSuccess) return cuda_status(e);
+    return cuda_status(cudaGetLastError());
+}
+
+dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
+                               int64_t nsamp, void* out, int64_t out_ld, cudaStream_t s) {
+    int64_t ldp = 0;
+    const dd_status st = launch_prefix(p, in, ld, t_offset, nsamp, &ldp, s);
+    if (st != DD_OK) return st;
     DedispArgs a;
     fill_dedisp_args(p, p->d_prefix, ldp, 0, nsamp - p->dmax, out, out_ld, &a);
     return p->rl_b ? run<uint32_t, false, kStagesRl, 1>(a, s) : run<uint32_t, false, kStagesRl>(a, s);
@@ -853,6 +909,25 @@ dd_status launch_dedisperse_batched(bool u8, bool pair, bool short_taps, const D
                           : run_batched<uint8_t, true, kStagesPair>(d_args, d_items, nitems, d_counter, smem, grid, s);
     return short_taps ? run_batched<float, true, kStagesPair, 1>(d_args, d_items, nitems, d_counter, smem, grid, s)
                       : run_batched<float, true, kStagesPair>(d_args, d_items, nitems, d_counter, smem, grid, s);
+}
+
+size_t fused_smem_for(const dd_plan_s* p, int rowlen) {
+    const int nbuf = p->rl ? kStagesRl : kStagesInt;
+    const size_t rows = (size_t)(kWarps / p->nch) * rowlen * 4 + nbuf * 8 + 2 * nbuf * 4;
+    return (std::max(dedisp_smem_for(p), rows) + 15) & ~(size_t)15;
+}
+
+int fused_blocks_per_sm(const dd_plan_s* p, size_t smem) {
+    if (p->rl) return p->rl_b ? fused_bps<uint32_t, kStagesRl, 1>(smem) : fused_bps<uint32_t, kStagesRl, 0>(smem);
+    return p->kmax <= kRInt ? fused_bps<uint8_t, kStagesInt, 1>(smem) : fused_bps<uint8_t, kStagesInt, 0>(smem);
+}
+
+dd_status launch_dedisperse_fused(const dd_plan_s* p, DedispArgs a, const FusedArgs& f, size_t smem,
+                                  cudaStream_t s) {
+    if (p->rl)
+        return p->rl_b ? run_fused<uint32_t, kStagesRl, 1>(a, f, smem, s) : run_fused<uint32_t, kStagesRl, 0>(a, f, smem, s);
+    return p->kmax <= kRInt ? run_fused<uint8_t, kStagesInt, 1>(a, f, smem, s)
+                            : run_fused<uint8_t, kStagesInt, 0>(a, f, smem, s);
 }
 
 int dedisp_batched_blocks_per_sm(bool u8, bool pair, bool short_taps, size_t smem) {

@@ -1,0 +1,210 @@
+// Dedispersion fused with the boxcar S/N scan (eq. p_dedisp followed by eq. snr with
+// boxcars, Sec. 5) for integer plans: the dedispersed series never leaves the chip.
+// The dedispersion CTAs scan their tiles in shared memory (dd_fused_scan.cuh); this
+// file holds the launcher, the pass over the windows that cross strip boundaries and
+// the pass that turns the merged maxima into S/N.  Results equal dd_dedisperse followed
+// by dd_boxcar_snr bit for bit: both take the maximum of the same exact integer sums
+// around the same per-trial offset, with the earliest start, and convert it with the
+// same normaliser.
+#include <algorithm>
+#include <climits>
+#include <cstdint>
+
+#include "dd_internal.h"
+
+namespace dd {
+namespace {
+
+// Windows that cross strip boundary b (start t < B < t + w, t + w <= t_out), one CTA
+// per (boundary, trial): the 2C outputs around B, a prefix over them, and per width the
+// largest sum with its earliest start, merged into the key.
+__global__ void __launch_bounds__(256) k_fused_seam(const FusedArgs f, int32_t L, int32_t t_out) {
+    extern __shared__ uint32_t pf[];  // [2C + 1]
+    const int b = blockIdx.x, d = blockIdx.y;
+    const int C = f.C;
+    const int32_t* v = f.seam + ((int64_t)d * (f.nstrip - 1) + b) * 2 * C;
+    const int64_t B = ((int64_t)(b + 1) * f.tiles / f.nstrip) * L;  // first output of strip b + 1
+    const int tid = threadIdx.x, lane = tid & 31;
+    if (tid < 32) {
+        uint32_t carry = 0;
+        if (lane == 0) pf[0] = 0;
+        for (int k0 = 0; k0 < 2 * C; k0 += 32) {
+            const int k = k0 + lane;
+            uint32_t x = k < 2 * C ? (uint32_t)v[k] : 0u;
+#pragma unroll
+            for (int o = 1; o < 32; o <<= 1) {
+                const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+                if (lane >= o) x += y;
+            }
+            if (k < 2 * C) pf[k + 1] = carry + x;
+            carry += __shfl_sync(0xffffffffu, x, 31);
+        }
+    }
+    __syncthreads();
+    const int64_t base = B - C;  // output of index 0 of the seam
+    for (int j = tid; j < f.nw; j += blockDim.x) {
+        const int w = f.w0 + j;
+        int best = INT_MIN, bt = -1;
+        for (int64_t t = B - w + 1; t < B; ++t) {
+            if (t + w > t_out) break;
+            const int k = (int)(t - base);
+            const int val = (int)(pf[k + w] - pf[k]);
+            if (val > best) {
+                best = val;
+                bt = (int)t;
+            }
+        }
+        if (bt >= 0) atomicMax(f.key + (int64_t)d * f.nw + j, fused_key(best, bt));
+    }
+}
+
+// Merged (value, start) -> S/N exactly as the unfused boxcar kernel converts it.
+__global__ void __launch_bounds__(256) k_fused_final(const unsigned long long* key, int32_t ndm, int32_t nw,
+                                                     const float* mu, const float* isd, float* peak,
+                                                     int32_t* arg, float thresh, dd_candidate* cands,
+                                                     int32_t cap, int32_t* ncands) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ndm * nw) return;
+    const unsigned long long k = key[i];
+    const int b = (int)((uint32_t)(k >> 32) ^ 0x80000000u);
+    const int t = k ? (int)(0xffffffffu - (uint32_t)k) : -1;
+    const float snr = (float)(((double)b - (double)mu[i]) * (double)isd[i]);
+    peak[i] = snr;
+    arg[i] = t;
+    if (cands && snr > thresh) {
+        const int c = atomicAdd(ncands, 1);
+        if (c < cap) {
+            dd_candidate cd;
+            cd.dm_index = (int32_t)(i / nw);
+            cd.width_index = (int32_t)(i % nw);
+            cd.t = t;
+            cd.snr = snr;
+            cands[c] = cd;
+        }
+    }
+}
+
+template <typename T>
+dd_status grow(T** buf, int64_t* have, int64_t need) {
+    if (need <= *have) return DD_OK;
+    cudaFree(*buf);
+    *buf = nullptr;
+    *have = 0;
+    cudaError_t e = cudaMalloc((void**)buf, (size_t)std::max<int64_t>(need, 1) * sizeof(T));
+    if (e != cudaSuccess) return cuda_status(e);
+    *have = need;
+    return DD_OK;
+}
+
+// Strips per trial block: whole waves of CTAs (slots = resident CTAs on the device)
+// and strips of equal length count most; each extra strip costs a seam of 2C outputs.
+int choose_strips(int64_t nblk, int tiles, int64_t slots, int C, int L) {
+    double best = -1.0;
+    int pick = 1;
+    for (int ns = 1; ns <= tiles; ++ns) {
+        const int64_t ctas = nblk * ns;
+        const int64_t waves = (ctas + slots - 1) / slots;
+        const double fill = (double)ctas / (double)(waves * slots);
+        const int per = (tiles + ns - 1) / ns;
+        const double even = ((double)tiles / ns) / per;
+        const double seam = (double)tiles * L / ((double)tiles * L + 2.0 * C * (ns - 1));
+        const double score = fill * even * seam;
+        if (score > best + 1e-9) {
+            best = score;
+            pick = ns;
+        }
+    }
+    return pick;
+}
+
+bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+}  // namespace
+}  // namespace dd
+
+extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t in_ld, int64_t t_offset,
+                                          int64_t nsamp, const int32_t* widths, int32_t nw,
+                                          const double* mean, const double* sd, float* peak,
+                                          int32_t* arg, float thresh, dd_candidate* cands,
+                                          int32_t cap, int32_t* ncands, void* stream) {
+    using namespace dd;
+    if (!p || !in || !widths || nw < 1 || !mean || !sd || !peak || !arg) return DD_ERR_ARG;
+    if (cands && (!ncands || cap < 0)) return DD_ERR_ARG;
+    if (nsamp <= 0) nsamp = p->band.nsamp;
+    if (t_offset < 0 || nsamp <= p->dmax || t_offset + nsamp > in_ld) return DD_ERR_ARG;
+    const int64_t t_out = nsamp - p->dmax;
+    for (int i = 0; i < nw; ++i) {
+        if (widths[i] < 1 || widths[i] > t_out) return DD_ERR_ARG;
+        if (i && widths[i] <= widths[i - 1]) return DD_ERR_ARG;
+    }
+    if (p->band.in_type != DD_U8 || !p->out_int || p->pair) return DD_ERR_UNSUPPORTED;
+    if (widths[nw - 1] - widths[0] != nw - 1) return DD_ERR_UNSUPPORTED;  // w_j = w_0 + j only
+    const int L = chunk_t(false) * p->nch;
+    const int C = widths[nw - 1] - 1;
+    if (C > L) return DD_ERR_UNSUPPORTED;
+    if (!aligned16(in) || in_ld % 16 != 0) return DD_ERR_ARG;
+    if (t_out > INT32_MAX - chunk_t(false) * kWarps || in_ld > (int64_t)1 << 40) return DD_ERR_OVERFLOW;
+    if (p->rl && nsamp > ((int64_t)1 << 24)) return DD_ERR_UNSUPPORTED;
+    cudaStream_t s = (cudaStream_t)stream;
+    dd_status st = upload_tables(p);
+    if (st != DD_OK) return st;
+    if ((st = launch_norm(p, widths, nw, mean, sd, s)) != DD_OK) return st;
+
+    DedispArgs a;
+    if (p->rl) {
+        int64_t ldp = 0;
+        if ((st = launch_prefix(p, in, in_ld, t_offset, nsamp, &ldp, s)) != DD_OK) return st;
+        fill_dedisp_args(p, p->d_prefix, ldp, 0, t_out, nullptr, 0, &a);
+    } else {
+        fill_dedisp_args(p, in, in_ld, t_offset, t_out, nullptr, 0, &a);
+    }
+    const int tiles = (int)((t_out + L - 1) / L);
+    const int tpc = kWarps / p->nch * (p->rl ? kRlUnits : 1);
+    const int64_t nblk = (p->ndm + tpc - 1) / tpc;
+    // row: C carried outputs, the tile, and room for the reads of the last tile's extra
+    // starts (up to C more) plus one window of widths past the end
+    const int rowlen = L + 2 * C + 64;
+    const size_t smem = fused_smem_for(p, rowlen);
+    int dev = 0, nsm = 0;
+    cudaError_t e = cudaGetDevice(&dev);
+    if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
+    if (e != cudaSuccess) return cuda_status(e);
+    const int bps = fused_blocks_per_sm(p, smem);
+    if (bps < 1) return DD_ERR_UNSUPPORTED;
+    int ns = p->debug_fused_strips > 0 ? std::min(p->debug_fused_strips, tiles)
+                                       : choose_strips(nblk, tiles, (int64_t)bps * nsm, C, L);
+
+    FusedArgs f;
+    f.w0 = widths[0];
+    f.nw = nw;
+    f.C = C;
+    f.rowlen = rowlen;
+    f.nstrip = ns;
+    f.tiles = tiles;
+    f.mlim = INT_MAX / widths[nw - 1];
+    f.off = p->dev.off;
+    if ((st = grow(&p->d_fkey, &p->fkey_elems, (int64_t)p->ndm * nw)) != DD_OK) return st;
+    if ((st = grow(&p->d_fcarry, &p->fcarry_elems, nblk * ns * tpc * (int64_t)C)) != DD_OK) return st;
+    if ((st = grow(&p->d_fseam, &p->fseam_elems, (int64_t)p->ndm * (ns - 1) * 2 * C)) != DD_OK) return st;
+    f.key = p->d_fkey;
+    f.carry = p->d_fcarry;
+    f.seam = p->d_fseam;
+    e = cudaMemsetAsync(f.key, 0, (size_t)p->ndm * nw * sizeof(unsigned long long), s);
+    if (e != cudaSuccess) return cuda_status(e);
+    if ((st = launch_dedisperse_fused(p, a, f, smem, s)) != DD_OK) return st;
+    if (ns > 1 && C > 0) {
+        k_fused_seam<<<dim3((unsigned)(ns - 1), (unsigned)p->ndm), 256, (size_t)(2 * C + 1) * 4, s>>>(
+            f, L, (int32_t)t_out);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    }
+    const int64_t n = (int64_t)p->ndm * nw;
+    k_fused_final<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f.key, p->ndm, nw, p->dev.mu, p->dev.isd,
+                                                              peak, arg, thresh, cands, cap, ncands);
+    return cuda_status(cudaGetLastError());
+}
+
+extern "C" dd_status dd_test_set_fused_strips(dd_plan_t p, int32_t nstrip) {
+    if (!p || nstrip < 0) return DD_ERR_ARG;
+    p->debug_fused_strips = nstrip;
+    return DD_OK;
+}

@@ -1,0 +1,198 @@
+// Boxcar scan of finished dedispersion tiles inside the dedispersion CTA: the fused
+// path of dd_dedisperse_boxcar (integer plans, contiguous widths w0 .. w0 + nw - 1).
+// Included by dd_dedisp.cu only.
+//
+// A CTA walks the tiles of its time strip in order.  After a tile's channel sum, each
+// warp group writes its trial's outputs, minus the trial's offset o_d, into a shared-
+// memory row behind the last C = wmax - 1 outputs of the previous tile (the carry), so
+// that the row holds x[T0 - C .. T0 + L).  The tile then owns the window starts
+// t in [T0 - C, T0 + L - C): every window of width <= wmax from such a start lies in
+// the row.  The strip's first tile has no carry and starts at the strip start; its last
+// tile also takes the starts up to the strip end, with windows cut off there; windows
+// that cross a strip boundary are left to the seam pass (dd_fused.cu).
+//
+// Lane l of a warp owns the kRInt starts i0 = l * kRInt + s of a row segment and walks
+// them for G widths at a time with a rotating register window of prefix sums: one
+// subtract and one max per (start, width), in uint32 arithmetic whose differences are
+// exact while every window sum of x - o fits int32 (checked per output against mlim;
+// DD_ERR_OVERFLOW otherwise).  A warp reduction gives the tile's maximum per width;
+// only where it beats (or ties from an earlier start) the merged maximum read from
+// `key` does the first lane holding it rescan its segment for the earliest start and
+// merge (value, start) with one 64-bit atomicMax.
+#pragma once
+
+#include <climits>
+
+#include "dd_internal.h"
+
+namespace dd {
+namespace fused {
+namespace {
+
+constexpr int G = 16;  // widths per register window
+
+// S = kRInt starts of one lane segment (x = row + i0) for widths w0g + j, j < G.
+// q = sum_{k < w0g} x[k] on entry.  !FULL: starts outside [i_lo, i_hi) and windows
+// ending past row index e_hi are left out.
+template <bool FULL>
+__device__ __forceinline__ void scan_segment(const int* x, uint32_t q, int w0g, int i0, int i_lo,
+                                             int i_hi, int e_hi, int (&seg)[G]) {
+    constexpr int S = kRInt;
+    uint32_t win[G];
+    win[0] = q;
+#pragma unroll
+    for (int j = 1; j < G; ++j) win[j] = win[j - 1] + (uint32_t)x[w0g + j - 1];
+    uint32_t p = 0;
+#pragma unroll
+    for (int s = 0; s < S; ++s) {
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            int v = (int)(win[(j + s) % G] - p);
+            if (!FULL) v = (i0 + s >= i_lo && i0 + s < i_hi && i0 + s + w0g + j <= e_hi) ? v : INT_MIN;
+            seg[j] = max(seg[j], v);
+        }
+        p += (uint32_t)x[s];
+        win[s % G] = win[(s + G - 1) % G] + (uint32_t)x[s + w0g + G - 1];
+    }
+}
+
+// Earliest start s of the segment whose width-w sum equals m (the same arithmetic as
+// scan_segment), or -1.
+__device__ __noinline__ int find_start(const int* x, int w, int m, int i0, int i_lo, int i_hi, int e_hi) {
+    uint32_t r = 0, p = 0;
+    for (int k = 0; k < w; ++k) r += (uint32_t)x[k];
+    for (int s = 0; s < kRInt; ++s) {
+        const int i = i0 + s;
+        if (i >= i_lo && i < i_hi && i + w <= e_hi && (int)(r - p) == m) return s;
+        p += (uint32_t)x[s];
+        r += (uint32_t)x[s + w];
+    }
+    return -1;
+}
+
+// Maximum over the warp of seg[j] for all j at once (each exchange level halves the
+// values a lane keeps): lanes 2j and 2j + 1 return the maximum for j.
+__device__ __forceinline__ int warp_max16(const int (&seg)[G], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    int v8[8], v4[4], v2[2];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        v8[j] = max(b4 ? seg[j + 8] : seg[j], __shfl_xor_sync(0xffffffffu, b4 ? seg[j] : seg[j + 8], 16));
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        v4[j] = max(b3 ? v8[j + 4] : v8[j], __shfl_xor_sync(0xffffffffu, b3 ? v8[j] : v8[j + 4], 8));
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+        v2[j] = max(b2 ? v4[j + 2] : v4[j], __shfl_xor_sync(0xffffffffu, b2 ? v4[j] : v4[j + 2], 4));
+    int v = max(b1 ? v2[1] : v2[0], __shfl_xor_sync(0xffffffffu, b1 ? v2[0] : v2[1], 2));
+    return max(v, __shfl_xor_sync(0xffffffffu, v, 1));
+}
+
+// The fused epilogue of one tile (every thread of the CTA calls it).  NU trials per
+// warp group (acc0, then accr[0 .. NU - 2]); d = the group's first trial, T0 = the
+// tile's first output, tiles tx0 .. tx1 - 1 form the CTA's strip.
+template <int NU, int NX>
+__device__ __forceinline__ void epilogue(const DedispArgs& a, const FusedArgs& f, unsigned char* smem,
+                                         int blk, int wu, int chunk, int lane, int d, int64_t T0,
+                                         int strip, int tx, int tx0, int tx1,
+                                         const int (&acc0)[kRInt], const int (&accr)[NX][kRInt]) {
+    constexpr int R = kRInt, TT = 32 * R;
+    const int L = TT * a.nch;
+    const int C = f.C;
+    int* row = (int*)smem + wu * f.rowlen;
+    const int64_t S1 = min((int64_t)tx1 * L, (int64_t)a.t_out);
+    const bool first = tx == tx0, last = tx == tx1 - 1;
+    // row index i holds output T0 - C + i
+    const int i_lo = first ? C : 0;             // first start owned by the tile
+    const int e_hi = (int)(S1 - T0) + C;        // windows end at or before this index
+    const int i_hi = last ? e_hi - f.w0 + 1 : L;  // starts below this index
+    const int tpc = kWarps / a.nch * NU;
+    const int ng = (f.nw + G - 1) / G;
+    const int jl = lane >> 1;
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        __syncthreads();  // the rows are free (stages consumed, or the previous trial scanned)
+        const int du = d + u;
+        const bool live = du < a.ndm;
+        const int o = live ? (int)f.off[du] : 0;
+        const int ib = C + chunk * TT + lane * R;
+        const int64_t tb = T0 + chunk * TT + lane * R;
+        int m = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int v = (u == 0 ? acc0[r] : accr[u > 0 ? u - 1 : 0][r]) - o;
+            row[ib + r] = v;
+            if (tb + r < S1) m = max(m, abs(v));
+        }
+        if (live && m > f.mlim) atomicExch(a.status, (int)DD_ERR_OVERFLOW);
+        const int64_t cb = (((int64_t)blk * f.nstrip + strip) * tpc + wu * NU + u) * C;
+        if (live && chunk == 0 && !first)
+            for (int k = lane; k < C; k += 32) row[k] = f.carry[cb + k];
+        __syncthreads();  // the row and its carry are complete
+        if (!live) continue;
+        if (chunk == 0) {
+            if (!last)
+                for (int k = lane; k < C; k += 32) f.carry[cb + k] = row[L + k];
+            int32_t* sm = f.seam + (int64_t)du * (f.nstrip - 1) * 2 * C;
+            if (first && strip > 0)
+                for (int k = lane; k < C; k += 32) sm[(int64_t)(strip - 1) * 2 * C + C + k] = row[C + k];
+            if (last && strip < f.nstrip - 1)
+                for (int k = lane; k < C; k += 32) sm[(int64_t)strip * 2 * C + k] = row[e_hi - C + k];
+        }
+        unsigned long long* keyrow = f.key + (int64_t)du * f.nw;
+        for (int k = chunk; k * TT < i_hi; k += a.nch) {
+            const int i0 = k * TT + lane * R;
+            const int* x = row + i0;
+            const bool any = i0 + R > i_lo && i0 < i_hi;
+            const bool inner = i0 >= i_lo && i0 + R <= i_hi;
+            const int t_lo = (int)(T0 - C) + max(k * TT, i_lo);  // earliest start of the pass
+            // lanes without a start here read nothing (their segment may lie past the row)
+            uint32_t q = 0;
+            if (any)
+                for (int kk = 0; kk < f.w0; ++kk) q += (uint32_t)x[kk];
+            for (int g = 0; g < ng; ++g) {
+                const int w0g = f.w0 + g * G;
+                const int cnt = min(G, f.nw - g * G);
+                unsigned long long bk = 0;
+                if (!(lane & 1) && jl < cnt) bk = __ldcg(keyrow + g * G + jl);
+                int seg[G];
+#pragma unroll
+                for (int j = 0; j < G; ++j) seg[j] = INT_MIN;
+                if (inner && i0 + R - 1 + w0g + cnt - 1 <= e_hi)
+                    scan_segment<true>(x, q, w0g, i0, i_lo, i_hi, e_hi, seg);
+                else if (any)
+                    scan_segment<false>(x, q, w0g, i0, i_lo, i_hi, e_hi, seg);
+                const int mx = warp_max16(seg, lane);
+                const int bv = (int)((uint32_t)(bk >> 32) ^ 0x80000000u);
+                const int bt = (int)(0xffffffffu - (uint32_t)bk);
+                const bool better = !(lane & 1) && jl < cnt && mx > INT_MIN &&
+                                    (mx > bv || (mx == bv && t_lo < bt));
+                unsigned need = __ballot_sync(0xffffffffu, better);
+                while (need) {  // warp-uniform
+                    const int hl = __ffs(need) - 1;
+                    need &= need - 1;
+                    const int j = hl >> 1;
+                    const int mj = __shfl_sync(0xffffffffu, mx, hl);
+                    int sj = INT_MIN;
+#pragma unroll
+                    for (int jj = 0; jj < G; ++jj) sj = jj == j ? seg[jj] : sj;
+                    const unsigned hit = __ballot_sync(0xffffffffu, any && sj == mj);
+                    if (lane == __ffs(hit) - 1) {
+                        const int s = find_start(x, w0g + j, mj, i0, i_lo, i_hi, e_hi);
+                        if (s >= 0) atomicMax(keyrow + g * G + j, fused_key(mj, (int)(T0 - C) + i0 + s));
+                    }
+                }
+                if (any)
+#pragma unroll
+                    for (int kk = 0; kk < G; ++kk) q += (uint32_t)x[w0g + kk];
+            }
+        }
+    }
+    // the next tile's bulk copies overwrite the rows
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+}
+
+}  // namespace
+}  // namespace fused
+}  // namespace dd

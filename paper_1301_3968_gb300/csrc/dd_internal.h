@@ -92,6 +92,33 @@ struct DedispArgs {
     uint32_t smem_bytes;  // dynamic shared memory of the launch
 };
 
+// The boxcar scan fused into the dedispersion CTAs (integer plans, contiguous widths
+// w0 .. w0 + nw - 1; dd_fused.cu).  The launch's time tiles are cut into nstrip strips;
+// CTA (strip, block) walks its strip's tiles in order and scans each finished tile in
+// shared memory, with the last C = wmax - 1 outputs of the previous tile carried in
+// front of it (through `carry`, a per-CTA global buffer).  Windows that cross a strip
+// boundary are scanned afterwards from `seam`, which holds C outputs on each side of
+// every boundary.  Maxima are merged in `key` as (value, earliest start) packed into
+// one 64-bit word.
+struct FusedArgs {
+    int32_t w0, nw;
+    int32_t C;          // wmax - 1
+    int32_t rowlen;     // shared-memory row stride (ints)
+    int32_t nstrip;
+    int32_t tiles;
+    int32_t mlim;       // largest |x - o| for which every width-wmax sum fits int32
+    const double* off;  // [ndm] per-trial offsets (integer valued)
+    unsigned long long* key;  // [ndm][nw]
+    int32_t* carry;     // [nblk][nstrip][trials per CTA][C]
+    int32_t* seam;      // [ndm][nstrip - 1][2 C]
+};
+
+// Packs a boxcar sum and its start so that the larger sum, then the earlier start,
+// compares larger; 0 stands for "no window".
+__host__ __device__ inline unsigned long long fused_key(int v, int t) {
+    return ((unsigned long long)((uint32_t)v ^ 0x80000000u) << 32) | (unsigned long long)(0xffffffffu - (uint32_t)t);
+}
+
 // One work item of the batched dedispersion kernel: a CTA tile of one beam.
 struct BatchItem {
     int32_t beam;
@@ -167,6 +194,14 @@ struct dd_plan_s {
     bool rl_b = false;                 // run-length with difference rows shared by the CTA
     uint32_t* d_prefix = nullptr;
     int64_t prefix_elems = 0;
+    // fused dedispersion + boxcar scratch: merged maxima, per-CTA carries, strip seams
+    unsigned long long* d_fkey = nullptr;
+    int64_t fkey_elems = 0;
+    int32_t* d_fcarry = nullptr;
+    int64_t fcarry_elems = 0;
+    int32_t* d_fseam = nullptr;
+    int64_t fseam_elems = 0;
+    int32_t debug_fused_strips = 0;    // test hook: strips of a fused launch (0 = automatic)
 };
 
 namespace dd {
@@ -201,6 +236,16 @@ dd_status launch_boxcar_scratch(dd_plan_s* p, const void* x, int64_t ld, int64_t
                                 const double* mean, const double* sd, double* off, float* mu,
                                 float* isd, float* peak, int32_t* arg, float thresh,
                                 dd_candidate* cands, int32_t cap, int32_t* ncands, cudaStream_t s);
+dd_status launch_prefix(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset, int64_t nsamp,
+                        int64_t* ldp, cudaStream_t s);
+dd_status launch_norm(dd_plan_s* p, const int32_t* widths, int32_t nw, const double* mean,
+                      const double* sd, cudaStream_t s);
+// fused dedispersion + boxcar: dynamic shared memory of the launch (stages, or the scan
+// rows plus the pipeline barriers, whichever is larger), its CTAs per SM, and the launch
+size_t fused_smem_for(const dd_plan_s* p, int rowlen);
+int fused_blocks_per_sm(const dd_plan_s* p, size_t smem);
+dd_status launch_dedisperse_fused(const dd_plan_s* p, DedispArgs a, const FusedArgs& f, size_t smem,
+                                  cudaStream_t s);
 dd_status launch_backward(dd_plan_s* p, const float* in, int64_t ld, int64_t t_offset,
                           int64_t t_out, const float* g, int64_t gld, float* gw, float* gin,
                           int64_t gin_ld, cudaStream_t s);

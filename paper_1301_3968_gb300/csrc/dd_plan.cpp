@@ -404,6 +404,9 @@ void destroy_plan(dd_plan_s* p) {
     if (p->d_gpad) cudaFree(p->d_gpad);
     if (p->d_gsplit) cudaFree(p->d_gsplit);
     if (p->d_prefix) cudaFree(p->d_prefix);
+    if (p->d_fkey) cudaFree(p->d_fkey);
+    if (p->d_fcarry) cudaFree(p->d_fcarry);
+    if (p->d_fseam) cudaFree(p->d_fseam);
     free_dev(p);
     delete p;
 }

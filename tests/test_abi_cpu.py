@@ -133,6 +133,34 @@ def test_argument_errors(lib):
     assert lib.dd_plan_destroy(h) == 0
 
 
+def test_fused_argument_checks(lib):
+    """dd_dedisperse_boxcar refuses, before any device work, what its kernels do not cover:
+    fp32 or weighted plans, non-contiguous widths, widths longer than a tile plus one, and
+    the usual argument errors."""
+    import paper_1301_3968_gb300 as dd
+    fake = ctypes.c_void_p(1 << 20)
+
+    def call(plan, wl, ld=2048, nsamp=2048, t_offset=0, x=fake):
+        wl = np.ascontiguousarray(wl, np.int32)
+        return lib.dd_dedisperse_boxcar(plan._h, x, ld, t_offset, nsamp, wl.ctypes.data, len(wl), fake,
+                                        fake, fake, fake, ctypes.c_float(1.0), None, 0, None, None)
+
+    f32 = dd.Plan(dd.Band(8, 1200.0, 1.0, 1.0, 2048, "f32"), np.zeros(4))
+    assert call(f32, [1, 2, 3]) == 8
+    u8 = dd.Plan(dd.Band(8, 1200.0, 1.0, 1.0, 2048, "u8"), np.zeros(4))
+    assert u8.schedule()["nch"] == 1
+    assert call(u8, [1, 2, 4]) == 8                       # not contiguous
+    assert call(u8, np.arange(1, 995)) == 8               # wmax - 1 > 992
+    assert call(u8, [3, 2]) == 1                          # not increasing
+    assert call(u8, [1, 2049]) == 1                       # longer than the series
+    assert call(u8, [1, 2], x=None) == 1
+    assert call(u8, [1, 2], ld=2047, nsamp=2047) == 1     # leading dimension not 16-byte aligned
+    assert call(u8, [1, 2], t_offset=16) == 1             # runs past the row
+    weighted = dd.Plan(dd.Band(8, 1200.0, 1.0, 1.0, 2048, "u8"), np.zeros(4))
+    weighted.set_profiles(weights=np.full((4, 8, 1), 0.5, np.float32))
+    assert call(weighted, [1, 2]) == 8
+
+
 def test_int32_overflow_is_refused(lib):
     """A uint8 plan whose sums could exceed int32 is rejected (DD_ERR_OVERFLOW)."""
     import paper_1301_3968_gb300 as dd

@@ -1,0 +1,171 @@
+"""Dedispersion fused with the boxcar S/N (dd_dedisperse_boxcar) through the C ABI: the
+same peak S/N (bit for bit) and earliest start as dd_dedisperse followed by dd_boxcar_snr,
+on both integer tap-sum methods, across strip counts (seams between strips), ragged tiles,
+offsets and width ranges; against the oracle's dedispersion and boxcar scan; the large
+low-band configuration at reduced length; and the overflow status."""
+import numpy as np
+import pytest
+
+import oracle
+from oracle import ref
+import synth
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def dd():
+    import torch
+    from paper_1301_3968_gb300 import build
+    build.build()
+    import paper_1301_3968_gb300 as m
+    torch.cuda.set_device(0)
+    return m
+
+
+def _dev(a):
+    import torch
+    return torch.from_numpy(np.ascontiguousarray(a)).cuda()
+
+
+def _plan(dd, rng, C, T, D, maxdel, maxtap, method):
+    plan = dd.Plan(dd.Band(C, 1200.0, 1.0, 1.0, T, "u8"), np.zeros(D))
+    delay = rng.integers(0, maxdel + 1, size=(D, C)).astype(np.int32)
+    taps = rng.integers(1, maxtap + 1, size=(D, C)).astype(np.int32)
+    plan.set_profiles(delay=delay, taps=taps)
+    plan.set_method(method)
+    return plan, delay, taps
+
+
+def _unfused(plan, x, widths, mean, sd, t_offset, nsamp, thresh=None, cap=0):
+    out = plan.dedisperse(x, t_offset=t_offset, nsamp=nsamp)
+    return plan.boxcar_snr(out, widths, mean, sd, thresh=thresh, cap=cap)
+
+
+@pytest.mark.parametrize("method", ["direct", "runlength"])
+@pytest.mark.parametrize("seed,C,T,D,maxdel,maxtap,t_off,w0,w1,strips", [
+    (61, 24, 5000, 30, 300, 20, 0, 1, 32, 0),       # automatic strips
+    (62, 37, 7100, 27, 900, 60, 16, 1, 256, 3),     # three strips: seams, ragged last tile
+    (63, 16, 4200, 9, 100, 5, 0, 5, 40, 4),         # widths from 5, one strip per tile
+    (64, 12, 3300, 25, 50, 3, 32, 1, 1, 2),         # width 1 only: no carry
+    (65, 40, 9000, 50, 2000, 200, 0, 100, 160, 5),  # long runs, widths 100-160
+])
+def test_fused_equals_unfused(dd, method, seed, C, T, D, maxdel, maxtap, t_off, w0, w1, strips):
+    rng = np.random.default_rng(seed)
+    ld = (T + t_off + 15) // 16 * 16
+    I = np.zeros((C, ld), np.uint8)
+    I[:, :T + t_off] = np.clip(rng.normal(128, 20, size=(C, T + t_off)), 0, 255).astype(np.uint8)
+    plan, delay, taps = _plan(dd, rng, C, T, D, maxdel, maxtap, method)
+    x = _dev(I)
+    mean, sd = plan.channel_stats(x, t_offset=t_off, nsamp=T)
+    widths = np.arange(w0, w1 + 1, dtype=np.int32)
+    plan.test_set_fused_strips(strips)
+    p0, a0, _ = _unfused(plan, x, widths, mean, sd, t_off, T)
+    p1, a1, _ = plan.dedisperse_boxcar(x, widths, mean, sd, t_offset=t_off, nsamp=T)
+    assert plan.device_status() == 0
+    np.testing.assert_array_equal(a1.cpu().numpy(), a0.cpu().numpy())
+    np.testing.assert_array_equal(p1.cpu().numpy(), p0.cpu().numpy())
+
+
+@pytest.mark.parametrize("method", ["direct", "runlength"])
+def test_fused_against_oracle(dd, method):
+    """A pulse on noise: the oracle's dedispersion and boxcar scan (int64 sums, float64
+    S/N) give the same earliest starts and S/N within 1e-5."""
+    rng = np.random.default_rng(66)
+    C, T, D = 32, 6000, 20
+    I = np.clip(rng.normal(100, 15, size=(C, T)), 0, 255).astype(np.uint8)
+    plan, delay, taps = _plan(dd, rng, C, T, D, 400, 40, method)
+    for c in range(C):  # a bright run along trial 7's profile
+        s = 2500 + delay[7, c]
+        I[c, s:s + taps[7, c]] = np.minimum(255, I[c, s:s + taps[7, c]].astype(int) + 60)
+    x = _dev(I)
+    mean, sd = plan.channel_stats(x, nsamp=T)
+    widths = np.arange(1, 65, dtype=np.int32)
+    plan.test_set_fused_strips(3)
+    peak, arg, _ = plan.dedisperse_boxcar(x, widths, mean, sd, nsamp=T)
+    xo = oracle.c_dedisperse(I, delay, taps, nsamp=T)
+    mu, sdw = ref.boxcar_norm(taps, widths, *ref.channel_stats(I, nsamp=T))
+    opeak, oarg, _ = ref.boxcar_snr(xo, widths, mu, sdw)
+    np.testing.assert_array_equal(arg.cpu().numpy(), oarg)
+    np.testing.assert_allclose(peak.cpu().numpy(), opeak, rtol=1e-5, atol=1e-5)
+    assert int(np.argmax(peak.cpu().numpy().max(axis=1))) == 7
+
+
+def test_fused_candidates_match(dd):
+    import torch
+    rng = np.random.default_rng(67)
+    C, T, D = 20, 4000, 33
+    I = np.clip(rng.normal(128, 20, size=(C, T)), 0, 255).astype(np.uint8)
+    plan, _, _ = _plan(dd, rng, C, T, D, 200, 30, "runlength")
+    x = _dev(I)
+    mean, sd = plan.channel_stats(x, nsamp=T)
+    widths = np.arange(1, 17, dtype=np.int32)
+    _, _, (c0, n0) = _unfused(plan, x, widths, mean, sd, 0, T, thresh=3.0, cap=4096)
+    _, _, (c1, n1) = plan.dedisperse_boxcar(x, widths, mean, sd, nsamp=T, thresh=3.0, cap=4096)
+    n = int(n0.item())
+    assert 0 < n <= 4096 and int(n1.item()) == n
+    key = lambda c: sorted(map(tuple, c[:n].cpu().numpy().tolist()))
+    assert key(c1) == key(c0)
+
+
+def test_fused_large_lowband_reduced(dd):
+    """Large low-band band and trial list (1024 ch over 700-1000 MHz, dt 64 us, 8192 DMs
+    to 2000, widths 1-256) on 2^18 samples: fused = unfused for every trial and width,
+    and sampled trials against the oracle."""
+    cfg = synth.make_large(nsamp=1 << 18)
+    b = cfg["band"]
+    T = cfg["nsamp"]
+    plan = dd.Plan(dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, T, "u8"), cfg["dms"])
+    assert plan.method == "runlength"
+    x = _dev(cfg["data"])
+    mean, sd = plan.channel_stats(x, nsamp=T)
+    widths = np.arange(1, 257, dtype=np.int32)
+    p1, a1, _ = plan.dedisperse_boxcar(x, widths, mean, sd, nsamp=T)
+    assert plan.device_status() == 0
+    out = plan.dedisperse(x, nsamp=T)
+    p0, a0, _ = plan.boxcar_snr(out, widths, mean, sd)
+    np.testing.assert_array_equal(a1.cpu().numpy(), a0.cpu().numpy())
+    np.testing.assert_array_equal(p1.cpu().numpy(), p0.cpu().numpy())
+    delay, taps = plan.tables()
+    rows = [0, 1234, 5000, 8191]
+    want = oracle.c_dedisperse(cfg["data"], delay, taps, nsamp=T, rows=rows)
+    mu, sdw = ref.boxcar_norm(taps[rows], widths, *ref.channel_stats(cfg["data"], nsamp=T))
+    opeak, oarg, _ = ref.boxcar_snr(want, widths, mu, sdw)
+    np.testing.assert_array_equal(a1.cpu().numpy()[rows], oarg)
+    np.testing.assert_allclose(p1.cpu().numpy()[rows], opeak, rtol=1e-5, atol=1e-5)
+
+
+def test_fused_overflow_is_reported(dd):
+    """Sums that cannot fit int32 around the offset (all samples 255, zero channel means
+    passed in) are reported through the device status, not returned silently."""
+    import torch
+    C, T, D = 128, 3008, 8
+    I = np.full((C, T), 255, np.uint8)
+    plan = dd.Plan(dd.Band(C, 1200.0, 1.0, 1.0, T, "u8"), np.zeros(D))
+    plan.set_profiles(delay=np.zeros((D, C), np.int32), taps=np.full((D, C), 70, np.int32))
+    x = _dev(I)
+    zero = torch.zeros(C, dtype=torch.float64, device="cuda")
+    widths = np.arange(1, 994, dtype=np.int32)
+    plan.device_status()
+    plan.dedisperse_boxcar(x, widths, zero, zero + 1.0, nsamp=T)
+    assert plan.device_status() == 2  # DD_ERR_OVERFLOW
+    mean, sd = plan.channel_stats(x, nsamp=T)
+    plan.dedisperse_boxcar(x, widths, mean, sd + 1.0, nsamp=T)
+    assert plan.device_status() == 0
+
+
+def test_fused_refuses_what_it_does_not_cover(dd):
+    import torch
+    rng = np.random.default_rng(68)
+    C, T, D = 8, 2048, 4
+    f32 = dd.Plan(dd.Band(C, 1200.0, 1.0, 1.0, T, "f32"), np.zeros(D))
+    xf = torch.zeros((C, T), dtype=torch.float32, device="cuda")
+    m = torch.zeros(C, dtype=torch.float64, device="cuda")
+    with pytest.raises(dd.DDError):
+        f32.dedisperse_boxcar(xf, np.arange(1, 5, dtype=np.int32), m, m + 1)
+    u8 = dd.Plan(dd.Band(C, 1200.0, 1.0, 1.0, T, "u8"), np.zeros(D))
+    xu = torch.zeros((C, T), dtype=torch.uint8, device="cuda")
+    with pytest.raises(dd.DDError):
+        u8.dedisperse_boxcar(xu, np.array([1, 2, 4], np.int32), m, m + 1)   # not contiguous
+    with pytest.raises(dd.DDError):
+        u8.dedisperse_boxcar(xu, np.arange(1, 1000, dtype=np.int32), m, m + 1)  # wmax - 1 > tile

@@ -190,8 +190,9 @@ dd_status dd_boxcar_snr_noalloc(dd_plan_t plan, const void* d_series, int64_t ld
  * results as dd_dedisperse(plan, d_in, in_ld, t_offset, nsamp, x, ...) followed by
  * dd_boxcar_snr(plan, x, ..., nsamp - d_max, widths, ...), bit for bit, but the
  * dedispersed series x is never written to device memory: the dedispersion CTAs scan
- * their finished tiles in shared memory (a few C = wmax - 1 outputs per strip boundary
- * go through plan-owned scratch).  For a caller that only needs the detections.
+ * their finished tiles in shared memory (C = wmax - 1 outputs per tile and trial are
+ * carried to the CTA's next tile, and 2C per part boundary go to a seam pass, through
+ * plan-owned scratch).  For a caller that only needs the detections.
  * Limits (DD_ERR_UNSUPPORTED otherwise): integer plans (uint8 input, unit weights; both
  * tap-sum methods), contiguous widths (w_j = w_0 + j), wmax - 1 <= 992 * nch (the
  * schedule's tile), and nsamp <= 2^24 on the run-length path.  Every boxcar sum of
@@ -201,17 +202,19 @@ dd_status dd_boxcar_snr_noalloc(dd_plan_t plan, const void* d_series, int64_t ld
  * undefined; dd_boxcar_snr on the stored series handles that case with 64-bit sums.
  * Other arguments, outputs and errors as dd_dedisperse and dd_boxcar_snr.  Allocates
  * plan-owned device scratch when the sizes grow: the merged maxima (8 bytes per trial
- * and width), the carried outputs (4 C bytes per trial and strip) and the seams (8 C
- * bytes per trial and strip boundary). */
+ * and width) and, per resident CTA, its carried outputs and seams (12 C bytes per trial
+ * of a CTA's block). */
 dd_status dd_dedisperse_boxcar(dd_plan_t plan, const void* d_in, int64_t in_ld, int64_t t_offset,
                                int64_t nsamp, const int32_t* widths, int32_t nw,
                                const double* d_chan_mean, const double* d_chan_std,
                                float* d_peak_snr, int32_t* d_peak_t, float thresh,
                                dd_candidate* d_cands, int32_t cap, int32_t* d_ncands, void* stream);
 
-/* Test hook: the number of time strips of the next dd_dedisperse_boxcar calls (capped
- * at the number of tiles; 0 restores the automatic choice).  Errors: DD_ERR_ARG. */
-dd_status dd_test_set_fused_strips(dd_plan_t plan, int32_t nstrip);
+/* Test hook: the number of parts (CTAs, each a contiguous run of the launch's (trial
+ * block, time tile) items) of the next dd_dedisperse_boxcar calls, capped at the number
+ * of items; 0 restores the automatic choice (eight per CTA resident on the device).
+ * Errors: DD_ERR_ARG. */
+dd_status dd_test_set_fused_parts(dd_plan_t plan, int32_t nparts);
 
 /* Adjoint of the weighted map of eq. p_dedisp (no counterpart in the paper): given
  * g = d(loss)/d(out) (d_gout [ndm][gout_ld] fp32, nsamp - d_max valid columns),

@@ -60,7 +60,7 @@ SIGNATURES = {
                                       c_f32, c_vp, c_i32, c_vp, c_vp]),
     "dd_dedisperse_boxcar": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_i64, c_vp, c_i32, c_vp, c_vp, c_vp, c_vp,
                                      c_f32, c_vp, c_i32, c_vp, c_vp]),
-    "dd_test_set_fused_strips": (c_i32, [c_vp, c_i32]),
+    "dd_test_set_fused_parts": (c_i32, [c_vp, c_i32]),
     "dd_backward": (c_i32, [c_vp, c_vp, c_i64, c_i64, c_i64, c_vp, c_i64, c_vp, c_vp, c_i64, c_vp]),
     "dd_plan_set_schedule": (c_i32, [c_vp, c_i32, c_i32]),
     "dd_plan_get_schedule": (c_i32, [c_vp, c_vp, c_vp, c_vp]),

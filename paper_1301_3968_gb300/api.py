@@ -302,9 +302,9 @@ class Plan:
             return peak, arg, None
         return peak, arg, (cands, ncand)
 
-    def test_set_fused_strips(self, nstrip: int) -> None:
-        """Test hook: time strips of the fused launches (0 = automatic)."""
-        check(self._lib.dd_test_set_fused_strips(self._h, int(nstrip)), "dd_test_set_fused_strips")
+    def test_set_fused_parts(self, nparts: int) -> None:
+        """Test hook: CTAs (parts) of the fused launches (0 = automatic)."""
+        check(self._lib.dd_test_set_fused_parts(self._h, int(nparts)), "dd_test_set_fused_parts")
 
     def backward(self, x: torch.Tensor, gout: torch.Tensor, t_offset: int = 0,
                  nsamp: int | None = None, want_gw: bool = True, want_gin: bool = True,

@@ -366,11 +366,11 @@ struct TileState {
 // `a` is taken by value: with a reference to the kernel parameter the compiler picked
 // a register allocation for the FMA loop that ran 11 % slower.
 // FUSED: instead of storing the tile, scan it for boxcar maxima (fa: the scan's
-// arguments; the CTA's strip is tiles tx0 .. tx1 - 1, index `strip`).
+// arguments, ft: the strip the tile belongs to).
 template <typename TIN, bool PAIR, int NBUF, bool MULTI, int SHORT, bool FUSED = false>
 __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* smem, int blk,
                                             int tx, TileState& ts, const FusedArgs* fa = nullptr,
-                                            int strip = 0, int tx0 = 0, int tx1 = 0) {
+                                            const fused::FusedTile* ft = nullptr) {
     constexpr int R = lane_r(PAIR);
     constexpr int TT = 32 * R;          // outputs per warp time chunk
     constexpr int Q = Elem<TIN>::Q;
@@ -523,8 +523,7 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
 
     if constexpr (FUSED) {
         static_assert(!PAIR, "the fused scan takes integer sums");
-        fused::epilogue<UPW, RL ? UPW - 1 : 1>(a, *fa, smem, blk, wu, chunk, lane, d, t0, strip, tx,
-                                               tx0, tx1, acc0, accr);
+        fused::epilogue<UPW, RL ? UPW - 1 : 1>(a, *fa, smem, wu, chunk, lane, d, t0, *ft, acc0, accr);
         return true;
     }
     // transpose through shared memory and store coalesced, one trial row at a time
@@ -606,19 +605,38 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_batched(const DedispA
     }
 }
 
-// Fused dedispersion + boxcar scan: CTA (strip, trial block) walks the strip's tiles.
+// Fused dedispersion + boxcar scan, one CTA per part: part s walks the
+// items (trial block, time tile) starts[s] .. starts[s + 1] - 1 in order (block-major),
+// a strip per trial block it touches.
 template <typename TIN, int NBUF, int SHORT>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_fused(DedispArgs a, const FusedArgs f) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ TileState ts;
     if (threadIdx.x == 0) init_pipeline<NBUF>(pipeline_area(smem, a.smem_bytes, NBUF), ts);
     __syncthreads();
-    const int strip = blockIdx.x;
-    const int tx0 = (int)((int64_t)strip * f.tiles / f.nstrip);
-    const int tx1 = (int)((int64_t)(strip + 1) * f.tiles / f.nstrip);
-    for (int tx = tx0; tx < tx1; ++tx)
-        if (!dedisp_tile<TIN, false, NBUF, true, SHORT, true>(a, smem, blockIdx.y, tx, ts, &f, strip, tx0, tx1))
-            break;
+    const int s = blockIdx.x;
+    const int64_t i0 = f.starts[s], i1 = f.starts[s + 1];
+    const int tpc = kWarps / a.nch * upw<TIN>();
+    const int L = chunk_t(false) * a.nch;
+    for (int64_t it = i0; it < i1;) {
+        const int blk = (int)(it / f.tiles);
+        const int tx0 = (int)(it - (int64_t)blk * f.tiles);
+        const int tx1 = (int)min((int64_t)f.tiles, tx0 + (i1 - it));
+        fused::FusedTile ft;
+        ft.s1 = min((int64_t)tx1 * L, (int64_t)a.t_out);
+        ft.carry = f.carry + (int64_t)s * tpc * f.C;
+        ft.seam_in = (it == i0 && tx0 > 0) ? f.seam + (int64_t)s * tpc * 2 * f.C : nullptr;
+        ft.seam_out = (it + (tx1 - tx0) == i1 && tx1 < f.tiles) ? f.seam + (int64_t)(s + 1) * tpc * 2 * f.C
+                                                                 : nullptr;
+        bool ok = true;
+        for (int tx = tx0; tx < tx1 && ok; ++tx) {
+            ft.first = tx == tx0;
+            ft.last = tx == tx1 - 1;
+            ok = dedisp_tile<TIN, false, NBUF, true, SHORT, true>(a, smem, blk, tx, ts, &f, &ft);
+        }
+        if (!ok) break;
+        it += tx1 - tx0;
+    }
 }
 
 // Dynamic shared memory of a launch: the plan's stages, per-channel minima and
@@ -669,10 +687,7 @@ dd_status run_fused(DedispArgs a, const FusedArgs& f, size_t smem, cudaStream_t 
     auto kern = k_dedisp_fused<TIN, NBUF, SHORT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
-    const int tpc = kWarps / a.nch * upw<TIN>();
-    dim3 grid((unsigned)f.nstrip, (unsigned)((a.ndm + tpc - 1) / tpc));
-    if (grid.y > 65535) return DD_ERR_UNSUPPORTED;
-    kern<<<grid, kWarps * 32, smem, s>>>(a, f);
+    kern<<<(unsigned)f.nparts, kWarps * 32, smem, s>>>(a, f);
     return cuda_status(cudaGetLastError());
 }
 
@@ -911,9 +926,10 @@ dd_status launch_dedisperse_batched(bool u8, bool pair, bool short_taps, const D
                       : run_batched<float, true, kStagesPair>(d_args, d_items, nitems, d_counter, smem, grid, s);
 }
 
-size_t fused_smem_for(const dd_plan_s* p, int rowlen) {
+size_t fused_smem_for(const dd_plan_s* p, int rowlen, int C) {
     const int nbuf = p->rl ? kStagesRl : kStagesInt;
-    const size_t rows = (size_t)(kWarps / p->nch) * rowlen * 4 + nbuf * 8 + 2 * nbuf * 4;
+    const int spill = p->rl ? kWarps * (kRlUnits - 1) * chunk_t(false) : 0;
+    const size_t rows = (size_t)(fused_rows_ints(kWarps / p->nch, rowlen, C) + spill) * 4 + nbuf * 8 + 2 * nbuf * 4;
     return (std::max(dedisp_smem_for(p), rows) + 15) & ~(size_t)15;
 }
 

@@ -15,15 +15,22 @@
 namespace dd {
 namespace {
 
-// Windows that cross strip boundary b (start t < B < t + w, t + w <= t_out), one CTA
-// per (boundary, trial): the 2C outputs around B, a prefix over them, and per width the
-// largest sum with its earliest start, merged into the key.
-__global__ void __launch_bounds__(256) k_fused_seam(const FusedArgs f, int32_t L, int32_t t_out) {
+// Windows that cross the boundary between parts k-1 and k inside a trial block (start
+// t < B < t + w, t + w <= t_out), one CTA per (boundary, trial of the block): the 2C
+// outputs around B, a prefix over them, and per width the largest sum with its earliest
+// start, merged into the key.
+__global__ void __launch_bounds__(256) k_fused_seam(const FusedArgs f, int32_t L, int32_t t_out,
+                                                    int32_t ndm, int32_t tpc) {
     extern __shared__ uint32_t pf[];  // [2C + 1]
-    const int b = blockIdx.x, d = blockIdx.y;
+    const int k = blockIdx.x + 1, local = blockIdx.y;
+    const int64_t item = f.starts[k];
+    const int blk = (int)(item / f.tiles);
+    const int tx = (int)(item - (int64_t)blk * f.tiles);
+    const int d = blk * tpc + local;
+    if (tx == 0 || d >= ndm) return;  // a part boundary between blocks has no seam
     const int C = f.C;
-    const int32_t* v = f.seam + ((int64_t)d * (f.nstrip - 1) + b) * 2 * C;
-    const int64_t B = ((int64_t)(b + 1) * f.tiles / f.nstrip) * L;  // first output of strip b + 1
+    const int32_t* v = f.seam + ((int64_t)k * tpc + local) * 2 * C;
+    const int64_t B = (int64_t)tx * L;  // first output of part k in this block
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid < 32) {
         uint32_t carry = 0;
@@ -96,25 +103,30 @@ dd_status grow(T** buf, int64_t* have, int64_t need) {
     return DD_OK;
 }
 
-// Strips per trial block: whole waves of CTAs (slots = resident CTAs on the device)
-// and strips of equal length count most; each extra strip costs a seam of 2C outputs.
-int choose_strips(int64_t nblk, int tiles, int64_t slots, int C, int L) {
-    double best = -1.0;
-    int pick = 1;
-    for (int ns = 1; ns <= tiles; ++ns) {
-        const int64_t ctas = nblk * ns;
-        const int64_t waves = (ctas + slots - 1) / slots;
-        const double fill = (double)ctas / (double)(waves * slots);
-        const int per = (tiles + ns - 1) / ns;
-        const double even = ((double)tiles / ns) / per;
-        const double seam = (double)tiles * L / ((double)tiles * L + 2.0 * C * (ns - 1));
-        const double score = fill * even * seam;
-        if (score > best + 1e-9) {
-            best = score;
-            pick = ns;
-        }
+// Cuts the items (block-major, `tiles` per block) into nparts contiguous, non-empty
+// parts of about equal cost.  A tile of block b costs cost[b] (the last tile of every
+// block `last_frac` of that); parts start where the cumulative cost crosses s / nparts
+// of the total.
+std::vector<int64_t> cut_parts(const std::vector<double>& cost, int tiles, double last_frac, int nparts) {
+    const int64_t nblk = (int64_t)cost.size();
+    const int64_t n = nblk * tiles;
+    std::vector<double> cum(nblk + 1, 0.0);
+    const double per_blk_tiles = tiles - 1 + last_frac;
+    for (int64_t b = 0; b < nblk; ++b) cum[b + 1] = cum[b] + cost[b] * per_blk_tiles;
+    std::vector<int64_t> st(nparts + 1);
+    st[0] = 0;
+    st[nparts] = n;
+    int64_t b = 0;
+    for (int s = 1; s < nparts; ++s) {
+        const double target = cum[nblk] * s / nparts;
+        while (b + 1 < nblk && cum[b + 1] <= target) ++b;
+        const double in = cost[b] > 0 ? (target - cum[b]) / cost[b] : 0.0;
+        int64_t it = b * tiles + std::min<int64_t>(tiles - 1, std::max<int64_t>(0, (int64_t)(in + 0.5)));
+        it = std::max(it, st[s - 1] + 1);
+        it = std::min(it, n - (nparts - s));
+        st[s] = it;
     }
-    return pick;
+    return st;
 }
 
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
@@ -161,40 +173,72 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
     const int tiles = (int)((t_out + L - 1) / L);
     const int tpc = kWarps / p->nch * (p->rl ? kRlUnits : 1);
     const int64_t nblk = (p->ndm + tpc - 1) / tpc;
-    // row: C carried outputs, the tile, and room for the reads of the last tile's extra
-    // starts (up to C more) plus one window of widths past the end
-    const int rowlen = L + 2 * C + 64;
-    const size_t smem = fused_smem_for(p, rowlen);
+    // row: C carried outputs, the tile and 32 spare; the last tile's extra starts read up
+    // to C + 14 past a row, into the next one or the padding behind the last
+    const int rowlen = L + C + 32;
+    const size_t smem = fused_smem_for(p, rowlen, C);
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&nsm, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return cuda_status(e);
     const int bps = fused_blocks_per_sm(p, smem);
     if (bps < 1) return DD_ERR_UNSUPPORTED;
-    int ns = p->debug_fused_strips > 0 ? std::min(p->debug_fused_strips, tiles)
-                                       : choose_strips(nblk, tiles, (int64_t)bps * nsm, C, L);
+    const int64_t nitems = nblk * tiles;
+    // eight parts per resident CTA: short enough runs that the CTAs on the device work on
+    // neighbouring blocks and time spans (as the plain kernel's tiles do), long enough that
+    // the seams stay a small share (measured on the large low-band block: 2.4k-2.7k parts
+    // beat 300 and 11k)
+    int64_t np = p->debug_fused_parts > 0 ? p->debug_fused_parts : (int64_t)8 * bps * nsm;
+    const int nparts = (int)std::min<int64_t>(np, nitems);
+    // cost of a tile: constant on the run-length path, the block's taps (plus a per-
+    // channel constant) on the direct path
+    std::vector<double> cost((size_t)nblk, 1.0);
+    if (!p->rl)
+        for (int64_t b = 0; b < nblk; ++b) {
+            double c = 0.0;
+            for (int64_t d = b * tpc; d < std::min<int64_t>((b + 1) * tpc, p->ndm); ++d)
+                for (int ch = 0; ch < p->nchan; ++ch) c += p->taps[(size_t)d * p->nchan + ch] + 4.0;
+            cost[(size_t)b] = c;
+        }
+    const double last_frac = (double)(t_out - (int64_t)(tiles - 1) * L) / L;
+    std::vector<int64_t> starts = cut_parts(cost, tiles, last_frac, nparts);
 
     FusedArgs f;
     f.w0 = widths[0];
     f.nw = nw;
     f.C = C;
     f.rowlen = rowlen;
-    f.nstrip = ns;
+    f.nparts = nparts;
     f.tiles = tiles;
     f.mlim = INT_MAX / widths[nw - 1];
     f.off = p->dev.off;
+    int64_t have_starts = (int64_t)p->fstarts.size();
+    if (starts != p->fstarts) {
+        if ((int64_t)starts.size() > have_starts || !p->d_fstarts) {
+            cudaFree(p->d_fstarts);
+            p->d_fstarts = nullptr;
+            p->fstarts.clear();
+            if ((e = cudaMalloc((void**)&p->d_fstarts, starts.size() * sizeof(int64_t))) != cudaSuccess)
+                return cuda_status(e);
+        }
+        e = cudaMemcpyAsync(p->d_fstarts, starts.data(), starts.size() * sizeof(int64_t), cudaMemcpyHostToDevice, s);
+        if (e == cudaSuccess) e = cudaStreamSynchronize(s);
+        if (e != cudaSuccess) return cuda_status(e);
+        p->fstarts = starts;
+    }
+    f.starts = p->d_fstarts;
     if ((st = grow(&p->d_fkey, &p->fkey_elems, (int64_t)p->ndm * nw)) != DD_OK) return st;
-    if ((st = grow(&p->d_fcarry, &p->fcarry_elems, nblk * ns * tpc * (int64_t)C)) != DD_OK) return st;
-    if ((st = grow(&p->d_fseam, &p->fseam_elems, (int64_t)p->ndm * (ns - 1) * 2 * C)) != DD_OK) return st;
+    if ((st = grow(&p->d_fcarry, &p->fcarry_elems, (int64_t)nparts * tpc * C)) != DD_OK) return st;
+    if ((st = grow(&p->d_fseam, &p->fseam_elems, (int64_t)nparts * tpc * 2 * C)) != DD_OK) return st;
     f.key = p->d_fkey;
     f.carry = p->d_fcarry;
     f.seam = p->d_fseam;
     e = cudaMemsetAsync(f.key, 0, (size_t)p->ndm * nw * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_status(e);
     if ((st = launch_dedisperse_fused(p, a, f, smem, s)) != DD_OK) return st;
-    if (ns > 1 && C > 0) {
-        k_fused_seam<<<dim3((unsigned)(ns - 1), (unsigned)p->ndm), 256, (size_t)(2 * C + 1) * 4, s>>>(
-            f, L, (int32_t)t_out);
+    if (nparts > 1 && C > 0) {
+        k_fused_seam<<<dim3((unsigned)(nparts - 1), (unsigned)tpc), 256, (size_t)(2 * C + 1) * 4, s>>>(
+            f, L, (int32_t)t_out, p->ndm, tpc);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     const int64_t n = (int64_t)p->ndm * nw;
@@ -203,8 +247,8 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
     return cuda_status(cudaGetLastError());
 }
 
-extern "C" dd_status dd_test_set_fused_strips(dd_plan_t p, int32_t nstrip) {
-    if (!p || nstrip < 0) return DD_ERR_ARG;
-    p->debug_fused_strips = nstrip;
+extern "C" dd_status dd_test_set_fused_parts(dd_plan_t p, int32_t nparts) {
+    if (!p || nparts < 0) return DD_ERR_ARG;
+    p->debug_fused_parts = nparts;
     return DD_OK;
 }

@@ -88,83 +88,77 @@ __device__ __forceinline__ int warp_max16(const int (&seg)[G], int lane) {
     return max(v, __shfl_xor_sync(0xffffffffu, v, 1));
 }
 
-// The fused epilogue of one tile (every thread of the CTA calls it).  NU trials per
-// warp group (acc0, then accr[0 .. NU - 2]); d = the group's first trial, T0 = the
-// tile's first output, tiles tx0 .. tx1 - 1 form the CTA's strip.
-template <int NU, int NX>
-__device__ __forceinline__ void epilogue(const DedispArgs& a, const FusedArgs& f, unsigned char* smem,
-                                         int blk, int wu, int chunk, int lane, int d, int64_t T0,
-                                         int strip, int tx, int tx0, int tx1,
-                                         const int (&acc0)[kRInt], const int (&accr)[NX][kRInt]) {
+// Upper bound of every sum the FULL scan of one width group would form:
+// max_{s, j} P[s + w0g + j] - min_s P[s] <= Q + Mrel, with P the prefix of the segment,
+// Q = P[w0g] - min_s P[s] and Mrel = max(0, max_m sum_{k=w0g}^{w0g+m} x[k]), m < cnt + 29.
+// Q is a window sum of at most wmax values and Mrel one of at most 45, so both are exact
+// in int32 when wmax >= 46 (every such sum fits, by the overflow check).
+__device__ __forceinline__ long long group_bound(const int* x, uint32_t q, uint32_t pmin, int w0g, int cnt) {
+    int r = 0, mrel = 0;
+    for (int m = 0; m < cnt + 29; ++m) {
+        r += x[w0g + m];
+        mrel = max(mrel, r);
+    }
+    return (long long)(int)(q - pmin) + mrel;
+}
+
+// Width groups from kPruneW on skip the scan of segments whose group_bound is below
+// the smallest merged maximum of the group (strictly: a tie from an earlier start could
+// still win), which on noise-like series is most of them.
+constexpr int kPruneW = 64;
+
+// The scan of one row for one trial (warp-uniform arguments; see epilogue).
+__device__ __forceinline__ void scan_row(const FusedArgs& f, const int* row, unsigned long long* keyrow,
+                                      int64_t T0, int C, int chunk, int nch, int lane, int i_lo,
+                                      int i_hi, int e_hi) {
     constexpr int R = kRInt, TT = 32 * R;
-    const int L = TT * a.nch;
-    const int C = f.C;
-    int* row = (int*)smem + wu * f.rowlen;
-    const int64_t S1 = min((int64_t)tx1 * L, (int64_t)a.t_out);
-    const bool first = tx == tx0, last = tx == tx1 - 1;
-    // row index i holds output T0 - C + i
-    const int i_lo = first ? C : 0;             // first start owned by the tile
-    const int e_hi = (int)(S1 - T0) + C;        // windows end at or before this index
-    const int i_hi = last ? e_hi - f.w0 + 1 : L;  // starts below this index
-    const int tpc = kWarps / a.nch * NU;
+    __builtin_assume(__isShared(row));
     const int ng = (f.nw + G - 1) / G;
     const int jl = lane >> 1;
-#pragma unroll
-    for (int u = 0; u < NU; ++u) {
-        __syncthreads();  // the rows are free (stages consumed, or the previous trial scanned)
-        const int du = d + u;
-        const bool live = du < a.ndm;
-        const int o = live ? (int)f.off[du] : 0;
-        const int ib = C + chunk * TT + lane * R;
-        const int64_t tb = T0 + chunk * TT + lane * R;
-        int m = 0;
-#pragma unroll
-        for (int r = 0; r < R; ++r) {
-            const int v = (u == 0 ? acc0[r] : accr[u > 0 ? u - 1 : 0][r]) - o;
-            row[ib + r] = v;
-            if (tb + r < S1) m = max(m, abs(v));
+    for (int k = chunk; k * TT < i_hi; k += nch) {
+        const int i0 = k * TT + lane * R;
+        const int* x = row + i0;
+        const bool any = i0 + R > i_lo && i0 < i_hi;
+        const bool inner = i0 >= i_lo && i0 + R <= i_hi;
+        const int t_lo = (int)(T0 - C) + max(k * TT, i_lo);  // earliest start of the pass
+        // lanes without a start here read nothing (their segment may lie past the row)
+        uint32_t q = 0, pmin = 0;
+        if (any) {
+            for (int kk = 0; kk < f.w0; ++kk) q += (uint32_t)x[kk];
+            if (inner) {  // min_s P[s] over the segment's starts (sums of <= 30 values)
+                int r = 0, mn = 0;
+                for (int s = 0; s < R - 1; ++s) {
+                    r += x[s];
+                    mn = min(mn, r);
+                }
+                pmin = (uint32_t)mn;
+            }
         }
-        if (live && m > f.mlim) atomicExch(a.status, (int)DD_ERR_OVERFLOW);
-        const int64_t cb = (((int64_t)blk * f.nstrip + strip) * tpc + wu * NU + u) * C;
-        if (live && chunk == 0 && !first)
-            for (int k = lane; k < C; k += 32) row[k] = f.carry[cb + k];
-        __syncthreads();  // the row and its carry are complete
-        if (!live) continue;
-        if (chunk == 0) {
-            if (!last)
-                for (int k = lane; k < C; k += 32) f.carry[cb + k] = row[L + k];
-            int32_t* sm = f.seam + (int64_t)du * (f.nstrip - 1) * 2 * C;
-            if (first && strip > 0)
-                for (int k = lane; k < C; k += 32) sm[(int64_t)(strip - 1) * 2 * C + C + k] = row[C + k];
-            if (last && strip < f.nstrip - 1)
-                for (int k = lane; k < C; k += 32) sm[(int64_t)strip * 2 * C + k] = row[e_hi - C + k];
-        }
-        unsigned long long* keyrow = f.key + (int64_t)du * f.nw;
-        for (int k = chunk; k * TT < i_hi; k += a.nch) {
-            const int i0 = k * TT + lane * R;
-            const int* x = row + i0;
-            const bool any = i0 + R > i_lo && i0 < i_hi;
-            const bool inner = i0 >= i_lo && i0 + R <= i_hi;
-            const int t_lo = (int)(T0 - C) + max(k * TT, i_lo);  // earliest start of the pass
-            // lanes without a start here read nothing (their segment may lie past the row)
-            uint32_t q = 0;
-            if (any)
-                for (int kk = 0; kk < f.w0; ++kk) q += (uint32_t)x[kk];
-            for (int g = 0; g < ng; ++g) {
-                const int w0g = f.w0 + g * G;
-                const int cnt = min(G, f.nw - g * G);
-                unsigned long long bk = 0;
-                if (!(lane & 1) && jl < cnt) bk = __ldcg(keyrow + g * G + jl);
+        for (int g = 0; g < ng; ++g) {
+            const int w0g = f.w0 + g * G;
+            const int cnt = min(G, f.nw - g * G);
+            unsigned long long bk = 0;
+            if (!(lane & 1) && jl < cnt) bk = __ldcg(keyrow + g * G + jl);
+            const int bv = (int)((uint32_t)(bk >> 32) ^ 0x80000000u);
+            const int bt = (int)(0xffffffffu - (uint32_t)bk);
+            const bool full = inner && i0 + R - 1 + w0g + cnt - 1 <= e_hi;
+            bool scan = any;
+            if (w0g >= kPruneW) {
+                // the smallest merged maximum over the group's widths
+                int thr = (!(lane & 1) && jl < cnt) ? bv : INT_MAX;
+#pragma unroll
+                for (int o = 16; o > 0; o >>= 1) thr = min(thr, __shfl_xor_sync(0xffffffffu, thr, o));
+                if (full && group_bound(x, q, pmin, w0g, cnt) < (long long)thr) scan = false;
+            }
+            if (__any_sync(0xffffffffu, scan)) {
                 int seg[G];
 #pragma unroll
                 for (int j = 0; j < G; ++j) seg[j] = INT_MIN;
-                if (inner && i0 + R - 1 + w0g + cnt - 1 <= e_hi)
+                if (scan && full)
                     scan_segment<true>(x, q, w0g, i0, i_lo, i_hi, e_hi, seg);
-                else if (any)
+                else if (scan)
                     scan_segment<false>(x, q, w0g, i0, i_lo, i_hi, e_hi, seg);
                 const int mx = warp_max16(seg, lane);
-                const int bv = (int)((uint32_t)(bk >> 32) ^ 0x80000000u);
-                const int bt = (int)(0xffffffffu - (uint32_t)bk);
                 const bool better = !(lane & 1) && jl < cnt && mx > INT_MIN &&
                                     (mx > bv || (mx == bv && t_lo < bt));
                 unsigned need = __ballot_sync(0xffffffffu, better);
@@ -176,17 +170,88 @@ __device__ __forceinline__ void epilogue(const DedispArgs& a, const FusedArgs& f
                     int sj = INT_MIN;
 #pragma unroll
                     for (int jj = 0; jj < G; ++jj) sj = jj == j ? seg[jj] : sj;
-                    const unsigned hit = __ballot_sync(0xffffffffu, any && sj == mj);
+                    const unsigned hit = __ballot_sync(0xffffffffu, scan && sj == mj);
                     if (lane == __ffs(hit) - 1) {
-                        const int s = find_start(x, w0g + j, mj, i0, i_lo, i_hi, e_hi);
-                        if (s >= 0) atomicMax(keyrow + g * G + j, fused_key(mj, (int)(T0 - C) + i0 + s));
+                        const int st = find_start(x, w0g + j, mj, i0, i_lo, i_hi, e_hi);
+                        if (st >= 0) atomicMax(keyrow + g * G + j, fused_key(mj, (int)(T0 - C) + i0 + st));
                     }
                 }
-                if (any)
-#pragma unroll
-                    for (int kk = 0; kk < G; ++kk) q += (uint32_t)x[w0g + kk];
             }
+            if (any)
+#pragma unroll
+                for (int kk = 0; kk < G; ++kk) q += (uint32_t)x[w0g + kk];
         }
+    }
+}
+
+// Where a strip of one trial block starts and ends, and what its CTA carries and passes
+// on.  seam_in / seam_out: the strip starts / ends inside the block, so its first /
+// last C outputs go to that seam ([trial in block][2C], second / first half).
+struct FusedTile {
+    int64_t s1;         // end of the strip (exclusive), at most t_out
+    bool first, last;   // first / last tile of the strip
+    int32_t* carry;     // [trials per CTA][C]
+    int32_t* seam_in;
+    int32_t* seam_out;
+};
+
+// The fused epilogue of one tile (every thread of the CTA calls it).  NU trials per
+// warp group (acc0, then accr[0 .. NU - 2]); d = the group's first trial, T0 = the
+// tile's first output.
+
+template <int NU, int NX>
+__device__ __forceinline__ void epilogue(const DedispArgs& a, const FusedArgs& f, unsigned char* smem,
+                                         int wu, int chunk, int lane, int d, int64_t T0,
+                                         const FusedTile& ft,
+                                         const int (&acc0)[kRInt], const int (&accr)[NX][kRInt]) {
+    constexpr int R = kRInt, TT = 32 * R;
+    const int L = TT * a.nch;
+    const int C = f.C;
+    int* row = (int*)smem + wu * f.rowlen;
+    const int64_t S1 = ft.s1;
+    const bool first = ft.first, last = ft.last;
+    // row index i holds output T0 - C + i
+    const int i_lo = first ? C : 0;             // first start owned by the tile
+    const int e_hi = (int)(S1 - T0) + C;        // windows end at or before this index
+    const int i_hi = last ? e_hi - f.w0 + 1 : L;  // starts below this index
+    // the other trials' sums wait in shared memory behind the rows, so that no
+    // accumulator stays live across a scan
+    int* spill = (int*)smem + fused_rows_ints(kWarps / a.nch, f.rowlen, C) +
+                 (threadIdx.x >> 5) * (NU - 1) * TT + lane * R;
+#pragma unroll
+    for (int u = 1; u < NU; ++u)
+#pragma unroll
+        for (int r = 0; r < R; ++r) spill[(u - 1) * TT + r] = accr[u - 1][r];
+#pragma unroll
+    for (int u = 0; u < NU; ++u) {
+        __syncthreads();  // the rows are free (stages consumed, or the previous trial scanned)
+        const int du = d + u;
+        const bool live = du < a.ndm;
+        const int o = live ? (int)f.off[du] : 0;
+        const int ib = C + chunk * TT + lane * R;
+        const int64_t tb = T0 + chunk * TT + lane * R;
+        int m = 0;
+#pragma unroll
+        for (int r = 0; r < R; ++r) {
+            const int v = (u == 0 ? acc0[r] : spill[(u - 1) * TT + r]) - o;
+            row[ib + r] = v;
+            if (tb + r < S1) m = max(m, abs(v));
+        }
+        if (live && m > f.mlim) atomicExch(a.status, (int)DD_ERR_OVERFLOW);
+        const int64_t cb = (int64_t)(wu * NU + u) * C;  // this trial's carry and seam rows
+        if (live && chunk == 0 && !first)
+            for (int k = lane; k < C; k += 32) row[k] = ft.carry[cb + k];
+        __syncthreads();  // the row and its carry are complete
+        if (!live) continue;
+        if (chunk == 0) {
+            if (!last)
+                for (int k = lane; k < C; k += 32) ft.carry[cb + k] = row[L + k];
+            if (first && ft.seam_in)
+                for (int k = lane; k < C; k += 32) ft.seam_in[2 * cb + C + k] = row[C + k];
+            if (last && ft.seam_out)
+                for (int k = lane; k < C; k += 32) ft.seam_out[2 * cb + k] = row[e_hi - C + k];
+        }
+        scan_row(f, row, f.key + (int64_t)du * f.nw, T0, C, chunk, a.nch, lane, i_lo, i_hi, e_hi);
     }
     // the next tile's bulk copies overwrite the rows
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");

@@ -93,25 +93,32 @@ struct DedispArgs {
 };
 
 // The boxcar scan fused into the dedispersion CTAs (integer plans, contiguous widths
-// w0 .. w0 + nw - 1; dd_fused.cu).  The launch's time tiles are cut into nstrip strips;
-// CTA (strip, block) walks its strip's tiles in order and scans each finished tile in
-// shared memory, with the last C = wmax - 1 outputs of the previous tile carried in
-// front of it (through `carry`, a per-CTA global buffer).  Windows that cross a strip
-// boundary are scanned afterwards from `seam`, which holds C outputs on each side of
-// every boundary.  Maxima are merged in `key` as (value, earliest start) packed into
-// one 64-bit word.
+// w0 .. w0 + nw - 1; dd_fused.cu).  The launch's items (trial block, time tile), block-
+// major, are cut into nparts contiguous parts of about equal cost, one CTA each.  A
+// CTA walks its items in order and scans each finished tile in shared memory,
+// with the last C = wmax - 1 outputs of the previous tile of the same block carried in
+// front of it (through `carry`, a per-CTA global buffer).  Windows that cross a part
+// boundary inside a trial block are scanned afterwards from `seam`, which holds C
+// outputs on each side of such a boundary.  Maxima are merged in `key` as (value,
+// earliest start) packed into one 64-bit word.
 struct FusedArgs {
     int32_t w0, nw;
     int32_t C;          // wmax - 1
     int32_t rowlen;     // shared-memory row stride (ints)
-    int32_t nstrip;
-    int32_t tiles;
+    int32_t nparts;
+    int32_t tiles;      // time tiles per trial block; item = block * tiles + tile
     int32_t mlim;       // largest |x - o| for which every width-wmax sum fits int32
-    const double* off;  // [ndm] per-trial offsets (integer valued)
+    const int64_t* starts;    // [nparts + 1] first item of each part
+    const double* off;        // [ndm] per-trial offsets (integer valued)
     unsigned long long* key;  // [ndm][nw]
-    int32_t* carry;     // [nblk][nstrip][trials per CTA][C]
-    int32_t* seam;      // [ndm][nstrip - 1][2 C]
+    int32_t* carry;     // [nparts][trials per CTA][C]
+    int32_t* seam;      // [nparts][trials per CTA][2 C]; entry s: boundary between parts s-1, s
 };
+
+// Shared-memory rows of the fused scan: nrow rows of `rowlen` ints (C carried outputs,
+// the tile, 32 spare), then C + 48 ints that the last row's reads may run into; the
+// run-length path's other trials' sums follow (fused_smem_for).
+__host__ __device__ inline int fused_rows_ints(int nrow, int rowlen, int C) { return nrow * rowlen + C + 48; }
 
 // Packs a boxcar sum and its start so that the larger sum, then the earlier start,
 // compares larger; 0 stands for "no window".
@@ -201,7 +208,9 @@ struct dd_plan_s {
     int64_t fcarry_elems = 0;
     int32_t* d_fseam = nullptr;
     int64_t fseam_elems = 0;
-    int32_t debug_fused_strips = 0;    // test hook: strips of a fused launch (0 = automatic)
+    int64_t* d_fstarts = nullptr;
+    std::vector<int64_t> fstarts;      // the parts of the last fused launch (host copy)
+    int32_t debug_fused_parts = 0;     // test hook: parts of a fused launch (0 = automatic)
 };
 
 namespace dd {
@@ -242,7 +251,7 @@ dd_status launch_norm(dd_plan_s* p, const int32_t* widths, int32_t nw, const dou
                       const double* sd, cudaStream_t s);
 // fused dedispersion + boxcar: dynamic shared memory of the launch (stages, or the scan
 // rows plus the pipeline barriers, whichever is larger), its CTAs per SM, and the launch
-size_t fused_smem_for(const dd_plan_s* p, int rowlen);
+size_t fused_smem_for(const dd_plan_s* p, int rowlen, int C);
 int fused_blocks_per_sm(const dd_plan_s* p, size_t smem);
 dd_status launch_dedisperse_fused(const dd_plan_s* p, DedispArgs a, const FusedArgs& f, size_t smem,
                                   cudaStream_t s);

@@ -407,6 +407,7 @@ void destroy_plan(dd_plan_s* p) {
     if (p->d_fkey) cudaFree(p->d_fkey);
     if (p->d_fcarry) cudaFree(p->d_fcarry);
     if (p->d_fseam) cudaFree(p->d_fseam);
+    if (p->d_fstarts) cudaFree(p->d_fstarts);
     free_dev(p);
     delete p;
 }

@@ -1,8 +1,9 @@
 """Dedispersion fused with the boxcar S/N (dd_dedisperse_boxcar) through the C ABI: the
 same peak S/N (bit for bit) and earliest start as dd_dedisperse followed by dd_boxcar_snr,
-on both integer tap-sum methods, across strip counts (seams between strips), ragged tiles,
-offsets and width ranges; against the oracle's dedispersion and boxcar scan; the large
-low-band configuration at reduced length; and the overflow status."""
+on both integer tap-sum methods, across part counts (part boundaries inside and between
+trial blocks, seams), ragged tiles, offsets and width ranges (with and without the pruned
+wide groups); against the oracle's dedispersion and boxcar scan; the large low-band
+configuration at reduced length; and the overflow status."""
 import numpy as np
 import pytest
 
@@ -43,14 +44,15 @@ def _unfused(plan, x, widths, mean, sd, t_offset, nsamp, thresh=None, cap=0):
 
 
 @pytest.mark.parametrize("method", ["direct", "runlength"])
-@pytest.mark.parametrize("seed,C,T,D,maxdel,maxtap,t_off,w0,w1,strips", [
-    (61, 24, 5000, 30, 300, 20, 0, 1, 32, 0),       # automatic strips
-    (62, 37, 7100, 27, 900, 60, 16, 1, 256, 3),     # three strips: seams, ragged last tile
-    (63, 16, 4200, 9, 100, 5, 0, 5, 40, 4),         # widths from 5, one strip per tile
+@pytest.mark.parametrize("seed,C,T,D,maxdel,maxtap,t_off,w0,w1,parts", [
+    (61, 24, 5000, 30, 300, 20, 0, 1, 32, 0),       # automatic parts
+    (62, 37, 7100, 27, 900, 60, 16, 1, 256, 3),     # parts end inside blocks, ragged last tile
+    (63, 16, 4200, 9, 100, 5, 0, 5, 40, 1000),      # one tile per part: a seam at every tile
     (64, 12, 3300, 25, 50, 3, 32, 1, 1, 2),         # width 1 only: no carry
-    (65, 40, 9000, 50, 2000, 200, 0, 100, 160, 5),  # long runs, widths 100-160
+    (65, 40, 9000, 50, 2000, 200, 0, 100, 160, 7),  # long runs, widths 100-160 (pruned groups)
+    (69, 30, 12000, 60, 500, 40, 0, 1, 300, 11),    # widths 1-300: a partial last group
 ])
-def test_fused_equals_unfused(dd, method, seed, C, T, D, maxdel, maxtap, t_off, w0, w1, strips):
+def test_fused_equals_unfused(dd, method, seed, C, T, D, maxdel, maxtap, t_off, w0, w1, parts):
     rng = np.random.default_rng(seed)
     ld = (T + t_off + 15) // 16 * 16
     I = np.zeros((C, ld), np.uint8)
@@ -59,7 +61,7 @@ def test_fused_equals_unfused(dd, method, seed, C, T, D, maxdel, maxtap, t_off, 
     x = _dev(I)
     mean, sd = plan.channel_stats(x, t_offset=t_off, nsamp=T)
     widths = np.arange(w0, w1 + 1, dtype=np.int32)
-    plan.test_set_fused_strips(strips)
+    plan.test_set_fused_parts(parts)
     p0, a0, _ = _unfused(plan, x, widths, mean, sd, t_off, T)
     p1, a1, _ = plan.dedisperse_boxcar(x, widths, mean, sd, t_offset=t_off, nsamp=T)
     assert plan.device_status() == 0
@@ -81,7 +83,7 @@ def test_fused_against_oracle(dd, method):
     x = _dev(I)
     mean, sd = plan.channel_stats(x, nsamp=T)
     widths = np.arange(1, 65, dtype=np.int32)
-    plan.test_set_fused_strips(3)
+    plan.test_set_fused_parts(3)
     peak, arg, _ = plan.dedisperse_boxcar(x, widths, mean, sd, nsamp=T)
     xo = oracle.c_dedisperse(I, delay, taps, nsamp=T)
     mu, sdw = ref.boxcar_norm(taps, widths, *ref.channel_stats(I, nsamp=T))

@@ -105,7 +105,7 @@ __device__ __forceinline__ long long group_bound(const int* x, uint32_t q, uint3
 // Width groups from kPruneW on skip the scan of segments whose group_bound is below
 // the smallest merged maximum of the group (strictly: a tie from an earlier start could
 // still win), which on noise-like series is most of them.
-constexpr int kPruneW = 64;
+constexpr int kPruneW = 48;
 
 // The scan of one row for one trial (warp-uniform arguments; see epilogue).
 __device__ __forceinline__ void scan_row(const FusedArgs& f, const int* row, unsigned long long* keyrow,

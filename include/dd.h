@@ -212,7 +212,8 @@ dd_status dd_dedisperse_boxcar(dd_plan_t plan, const void* d_in, int64_t in_ld, 
 
 /* Test hook: the number of parts (CTAs, each a contiguous run of the launch's (trial
  * block, time tile) items) of the next dd_dedisperse_boxcar calls, capped at the number
- * of items; 0 restores the automatic choice (eight per CTA resident on the device).
+ * of items; 0 restores the automatic choice (one to eight per CTA resident on the device,
+ * parts of at least ~16 tiles).
  * Errors: DD_ERR_ARG. */
 dd_status dd_test_set_fused_parts(dd_plan_t plan, int32_t nparts);
 

@@ -11,9 +11,10 @@
 //
 // gw is a correlation of each trial's gradient row with the shifted channel row, for
 // the tap lags k: k_bwd_w gives each warp one (trial, channel) pair and its 32 lags in
-// registers; lanes own 33 consecutive samples (odd, so lane-strided shared loads are
-// conflict free) and slide a 32-sample register window along them; the lanes' partial
-// sums are added in a fixed order at the end.  Both paths are deterministic.
+// registers, as 16 packed lag pairs (k, k + 16) updated by fma.rn.f32x2; lanes own 33
+// consecutive samples (odd, so lane-strided shared loads are conflict free) and slide a
+// window of 16 sample pairs (x[p], x[p + 16]) along them; the lanes' partial sums are
+// added in a fixed order at the end.  Both paths are deterministic.
 #include <algorithm>
 #include <cstdint>
 

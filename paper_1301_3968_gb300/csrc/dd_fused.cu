@@ -184,11 +184,14 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
     const int bps = fused_blocks_per_sm(p, smem);
     if (bps < 1) return DD_ERR_UNSUPPORTED;
     const int64_t nitems = nblk * tiles;
-    // eight parts per resident CTA: short enough runs that the CTAs on the device work on
-    // neighbouring blocks and time spans (as the plain kernel's tiles do), long enough that
-    // the seams stay a small share (measured on the large low-band block: 2.4k-2.7k parts
-    // beat 300 and 11k)
-    int64_t np = p->debug_fused_parts > 0 ? p->debug_fused_parts : (int64_t)8 * bps * nsm;
+    // k parts per resident CTA, k = items / (16 x resident CTAs) clamped to 1..8: parts of
+    // at least ~16 tiles, so that the seams and carry-less first tiles stay a small share,
+    // and on large launches short enough runs that the CTAs on the device work on
+    // neighbouring blocks and time spans (measured on the large low-band block: 2.4k-2.7k
+    // parts beat 300 and 11k)
+    const int64_t slots = (int64_t)bps * nsm;
+    const int64_t k_per = std::max<int64_t>(1, std::min<int64_t>(8, nblk * tiles / (16 * slots)));
+    int64_t np = p->debug_fused_parts > 0 ? p->debug_fused_parts : k_per * slots;
     const int nparts = (int)std::min<int64_t>(np, nitems);
     // cost of a tile: constant on the run-length path, the block's taps (plus a per-
     // channel constant) on the direct path

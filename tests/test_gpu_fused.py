@@ -69,6 +69,28 @@ def test_fused_equals_unfused(dd, method, seed, C, T, D, maxdel, maxtap, t_off, 
     np.testing.assert_array_equal(p1.cpu().numpy(), p0.cpu().numpy())
 
 
+@pytest.mark.parametrize("method,nch", [("direct", 2), ("runlength", 2), ("direct", 4)])
+def test_fused_multi_chunk_ctas(dd, method, nch):
+    """CTA shapes with several time chunks (a trial's row is written by nch warps and
+    scanned by all of them): fused = unfused."""
+    rng = np.random.default_rng(70 + nch)
+    C, T, D = 20, 9008, 40
+    I = np.clip(rng.normal(128, 20, size=(C, T)), 0, 255).astype(np.uint8)
+    plan, _, _ = _plan(dd, rng, C, T, D, 600, 50, method)
+    plan.set_schedule(nch, 2)
+    assert plan.schedule()["nch"] == nch
+    x = _dev(I)
+    mean, sd = plan.channel_stats(x, nsamp=T)
+    widths = np.arange(1, 200, dtype=np.int32)
+    for parts in (0, 5):
+        plan.test_set_fused_parts(parts)
+        p0, a0, _ = _unfused(plan, x, widths, mean, sd, 0, T)
+        p1, a1, _ = plan.dedisperse_boxcar(x, widths, mean, sd, nsamp=T)
+        assert plan.device_status() == 0
+        np.testing.assert_array_equal(a1.cpu().numpy(), a0.cpu().numpy())
+        np.testing.assert_array_equal(p1.cpu().numpy(), p0.cpu().numpy())
+
+
 @pytest.mark.parametrize("method", ["direct", "runlength"])
 def test_fused_against_oracle(dd, method):
     """A pulse on noise: the oracle's dedispersion and boxcar scan (int64 sums, float64

@@ -23,6 +23,7 @@ import os
 import statistics
 import subprocess
 import sys
+import tempfile
 import time
 
 import numpy as np
@@ -92,7 +93,7 @@ class ClockSampler:
     def __init__(self, index: int):
         self.index = index
         self.proc = None
-        self.path = os.path.join(ROOT, "gpurun_out", f"clocks_bench_{os.getpid()}.csv")
+        self.path = os.path.join(tempfile.gettempdir(), f"clocks_bench_{os.getpid()}.csv")
 
     def start(self):
         try:
@@ -461,7 +462,8 @@ def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, 
         "dedisp_value": units / (dd_ms / 1e3), "step_value": units / (st_ms / 1e3), "unit": UNIT,
         "trial_channel_samples_per_s": dct / (dd_ms / 1e3),
         "realtime_factor": (t_out * b.dt_ms / 1e3) / (st_ms / 1e3),
-        "fused_step_ms": fu_ms, "fused_over_step": fu_ms / st_ms, "fused_status": fu_status,
+        "fused_step_ms": fu_ms, "fused_value": units / (fu_ms / 1e3), "fused_over_step": fu_ms / st_ms,
+        "fused_status": fu_status,
         "fused_series_bytes_not_stored": plan.ndm * chunk * 4,
         "graded_adds_per_block": graded,
         "graded_tops": graded / (dd_ms / 1e3) / 1e12,

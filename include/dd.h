@@ -202,8 +202,11 @@ dd_status dd_boxcar_snr_noalloc(dd_plan_t plan, const void* d_series, int64_t ld
  * undefined; dd_boxcar_snr on the stored series handles that case with 64-bit sums.
  * Other arguments, outputs and errors as dd_dedisperse and dd_boxcar_snr.  Allocates
  * plan-owned device scratch when the sizes grow: the merged maxima (8 bytes per trial
- * and width) and, per resident CTA, its carried outputs and seams (12 C bytes per trial
- * of a CTA's block). */
+ * and width) and, per part, its carried outputs and seams (12 C bytes per trial of a
+ * CTA's block).  A call with a new width list or a new launch geometry copies small
+ * host tables to the device synchronously, so make one such call before capturing the
+ * stream in a CUDA graph.  Calls on one plan share its scratch: order them on one
+ * stream. */
 dd_status dd_dedisperse_boxcar(dd_plan_t plan, const void* d_in, int64_t in_ld, int64_t t_offset,
                                int64_t nsamp, const int32_t* widths, int32_t nw,
                                const double* d_chan_mean, const double* d_chan_std,

@@ -408,13 +408,16 @@ def batched_extra(dd, dev, flush, stream, reps=3):
     }
 
 
-def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, iadd_tops=None):
+def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, iadd_tops=None,
+                sm_mhz=None):
     """Large low-band configuration: 1024 ch over 700-1000 MHz, dt 64 us, 2^20 uint8
     samples, 8192 trial DMs 0-2000 (unit weights, run-length sums), streamed in
     overlapping chunks of `chunk` outputs (each chunk reads its outputs plus d_max
     samples), int32 out, then boxcar S/N over widths 1-256 per chunk."""
     import torch
     import synth
+    if sm_mhz is None:
+        sm_mhz = float(_peaks()[0].get("sm_max_mhz", 2070.0))
     cfg = synth.make_large(nsamp=nsamp)
     b, T = cfg["band"], cfg["nsamp"]
     dms = cfg["dms"] if ndm == len(cfg["dms"]) else np.linspace(0.0, cfg["dms"][-1], ndm)
@@ -465,10 +468,18 @@ def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, 
         "fused_step_ms": fu_ms, "fused_value": units / (fu_ms / 1e3), "fused_over_step": fu_ms / st_ms,
         "fused_status": fu_status,
         "fused_series_bytes_not_stored": plan.ndm * chunk * 4,
+        # the run-length kernel's bound: shared-memory reads, one 4-byte word per (trial,
+        # channel, output) from the CTA's difference rows (two without them), against
+        # 152 SMs x 128 B/clk at the measured clock
+        "smem_read_bytes_per_block": 4.0 * dct,
+        "smem_read_tbps": 4.0 * dct / (dd_ms / 1e3) / 1e12,
+        "smem_peak_tbps": N_SM * 128 * sm_mhz * 1e6 / 1e12,
         "graded_adds_per_block": graded,
         "graded_tops": graded / (dd_ms / 1e3) / 1e12,
-        "bound": "shared-memory loads (2 per trial, channel and output; see profiles)",
+        "bound": "shared-memory reads (1 word per trial, channel and output with the CTA's difference rows; see profiles)",
     }
+    res["smem_read_frac"] = res["smem_read_tbps"] / res["smem_peak_tbps"]
+    res["smem_peak_kind"] = f"derived: {N_SM} SMs x 128 B/clk x {sm_mhz:.0f} MHz"
     if iadd_tops:
         res["graded_frac_of_measured_iadd"] = res["graded_tops"] / iadd_tops
     plan.close()

@@ -79,6 +79,40 @@ def test_large_lowband_full_size_streamed(dd):
         np.testing.assert_array_equal(got.astype(np.int64), want)
 
 
+def test_large_lowband_full_size_fused(dd):
+    """The bench's large low-band block through the fused call, chunk by chunk (2^20
+    samples, 8192 trials, widths 1-256, 4 overlapping chunks of 2^18 outputs): every peak
+    and start equal to dedispersion + boxcar on the stored chunk, and sampled trials of
+    one chunk equal to the oracle's dedispersion and scan."""
+    import torch
+    cfg = synth.make_large()
+    b, T = cfg["band"], cfg["nsamp"]
+    plan = dd.Plan(dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, T, "u8"), cfg["dms"])
+    x = _dev(cfg["data"])
+    dmax = plan.d_max
+    t_out = T - dmax
+    chunk = 1 << 18
+    widths = np.arange(1, 257, dtype=np.int32)
+    mean, sd = plan.channel_stats(x, nsamp=T)
+    out = torch.empty((plan.ndm, chunk), dtype=torch.int32, device="cuda")
+    delay, taps = plan.tables()
+    rows = [3, 4100, 8190]
+    for t0 in range(0, t_out, chunk):
+        n = min(chunk, t_out - t0)
+        p1, a1, _ = plan.dedisperse_boxcar(x, widths, mean, sd, t_offset=t0, nsamp=n + dmax)
+        assert plan.device_status() == 0
+        plan.dedisperse(x, t_offset=t0, nsamp=n + dmax, out=out)
+        p0, a0, _ = plan.boxcar_snr(out, widths, mean, sd, t_len=n)
+        np.testing.assert_array_equal(a1.cpu().numpy(), a0.cpu().numpy())
+        np.testing.assert_array_equal(p1.cpu().numpy(), p0.cpu().numpy())
+        if t0 == chunk:
+            want = oracle.c_dedisperse(cfg["data"], delay, taps, t_offset=t0, nsamp=n + dmax, rows=rows)
+            mu, sdw = ref.boxcar_norm(taps[rows], widths, *ref.channel_stats(cfg["data"], nsamp=T))
+            opeak, oarg, _ = ref.boxcar_snr(want, widths, mu, sdw)
+            np.testing.assert_array_equal(a1.cpu().numpy()[rows], oarg)
+            np.testing.assert_allclose(p1.cpu().numpy()[rows], opeak, rtol=1e-5, atol=1e-5)
+
+
 def test_differentiable_full_size_gradients(dd):
     """336 channels, 16384 fp32 samples, 1024 trials, 32 learnable taps: forward rows and
     sampled weight and input gradients through the adjoint kernels against the oracle

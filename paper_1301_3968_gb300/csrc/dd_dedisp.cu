@@ -614,28 +614,28 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_fused(DedispArgs a, c
     __shared__ TileState ts;
     if (threadIdx.x == 0) init_pipeline<NBUF>(pipeline_area(smem, a.smem_bytes, NBUF), ts);
     __syncthreads();
+    // the tile's strip, kept in shared memory so that no per-strip state stays live in
+    // registers across the channel sums (thread 0 writes it before each tile; the tile's
+    // barriers order it, and the epilogue's last barrier ends its readers)
+    __shared__ fused::FusedTile ft;
     const int s = blockIdx.x;
-    const int64_t i0 = f.starts[s], i1 = f.starts[s + 1];
-    const int tpc = kWarps / a.nch * upw<TIN>();
-    const int L = chunk_t(false) * a.nch;
-    for (int64_t it = i0; it < i1;) {
-        const int blk = (int)(it / f.tiles);
-        const int tx0 = (int)(it - (int64_t)blk * f.tiles);
-        const int tx1 = (int)min((int64_t)f.tiles, tx0 + (i1 - it));
-        fused::FusedTile ft;
-        ft.s1 = min((int64_t)tx1 * L, (int64_t)a.t_out);
-        ft.carry = f.carry + (int64_t)s * tpc * f.C;
-        ft.seam_in = (it == i0 && tx0 > 0) ? f.seam + (int64_t)s * tpc * 2 * f.C : nullptr;
-        ft.seam_out = (it + (tx1 - tx0) == i1 && tx1 < f.tiles) ? f.seam + (int64_t)(s + 1) * tpc * 2 * f.C
-                                                                 : nullptr;
-        bool ok = true;
-        for (int tx = tx0; tx < tx1 && ok; ++tx) {
+    const int i0 = (int)f.starts[s], i1 = (int)f.starts[s + 1];  // items < 2^31 (host check)
+    for (int it = i0; it < i1; ++it) {
+        const int blk = it / f.tiles;
+        const int tx = it - blk * f.tiles;
+        if (threadIdx.x == 0) {
+            const int L = chunk_t(false) * a.nch;
+            const int tpc = kWarps / a.nch * upw<TIN>();
+            const int tx0 = it - tx <= i0 ? i0 - (it - tx) : 0;                    // strip start
+            const int tx1 = i1 - (it - tx) < f.tiles ? i1 - (it - tx) : f.tiles;  // strip end
             ft.first = tx == tx0;
             ft.last = tx == tx1 - 1;
-            ok = dedisp_tile<TIN, false, NBUF, true, SHORT, true>(a, smem, blk, tx, ts, &f, &ft);
+            ft.s1 = min((int64_t)tx1 * L, (int64_t)a.t_out);
+            ft.carry = f.carry + (int64_t)s * tpc * f.C;
+            ft.seam_in = tx0 > 0 ? f.seam + (int64_t)s * tpc * 2 * f.C : nullptr;
+            ft.seam_out = tx1 < f.tiles ? f.seam + (int64_t)(s + 1) * tpc * 2 * f.C : nullptr;
         }
-        if (!ok) break;
-        it += tx1 - tx0;
+        if (!dedisp_tile<TIN, false, NBUF, true, SHORT, true>(a, smem, blk, tx, ts, &f, &ft)) break;
     }
 }
 

@@ -184,6 +184,7 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
     const int bps = fused_blocks_per_sm(p, smem);
     if (bps < 1) return DD_ERR_UNSUPPORTED;
     const int64_t nitems = nblk * tiles;
+    if (nitems >= INT32_MAX) return DD_ERR_UNSUPPORTED;
     // k parts per resident CTA, k = items / (16 x resident CTAs) clamped to 1..8: parts of
     // at least ~16 tiles, so that the seams and carry-less first tiles stay a small share,
     // and on large launches short enough runs that the CTAs on the device work on

@@ -2,7 +2,8 @@
 // path of dd_dedisperse_boxcar (integer plans, contiguous widths w0 .. w0 + nw - 1).
 // Included by dd_dedisp.cu only.
 //
-// A CTA walks the tiles of its time strip in order.  After a tile's channel sum, each
+// A CTA walks its part of the launch's (trial block, time tile) items in order, a strip
+// of consecutive tiles per trial block it touches.  After a tile's channel sum, each
 // warp group writes its trial's outputs, minus the trial's offset o_d, into a shared-
 // memory row behind the last C = wmax - 1 outputs of the previous tile (the carry), so
 // that the row holds x[T0 - C .. T0 + L).  The tile then owns the window starts

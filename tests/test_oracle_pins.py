@@ -51,6 +51,55 @@ def test_hand_boxcar():
     assert arg[0, 0] == bc["peak_t"] and best[0, 0] == bc["peak_B"]
 
 
+def test_abs_scale_hand_values():
+    """The fp32 tolerance scale Σ_c Σ_k |w_dck|·|I[c][t+δ+k]| on a hand-worked case with
+    inputs and weights of both signs (tests/golden/abs_scale.json): the signed sums
+    differ from it, so dropping either absolute value fails."""
+    g = _gold("abs_scale.json")
+    I = np.array(g["I"], np.float32)
+    dl = np.array(g["delays"], np.int32)
+    tp = np.array(g["taps"], np.int32)
+    w = np.array(g["weights"], np.float32)
+    scale = oracle.c_abs_scale(I, dl, tp, w=w)
+    np.testing.assert_array_equal(scale, np.array(g["abs_scale"]))
+    signed = oracle.c_dedisperse(I, dl, tp, w=w)
+    assert signed[0, 0] == g["signed_trial0_t0"] and signed[1, 0] == g["signed_trial1_t0"]
+    # planted mistakes: absolute value of I only, of w only
+    assert not np.array_equal(oracle.c_dedisperse(np.abs(I), dl, tp, w=w), scale)
+    assert not np.array_equal(oracle.c_dedisperse(I, dl, tp, w=np.abs(w)), scale)
+
+
+def test_abs_scale_brute_force_and_rows():
+    """The scale against a pure-Python loop over every (c, k) term on a small random case
+    of mixed signs, for all rows, a row subset and an offset window."""
+    rng = np.random.default_rng(31)
+    C, T, D, K = 5, 40, 4, 4
+    I = rng.standard_normal((C, T)).astype(np.float32)
+    dl = rng.integers(0, 6, size=(D, C)).astype(np.int32)
+    tp = rng.integers(1, K + 1, size=(D, C)).astype(np.int32)
+    w = rng.uniform(-1.5, 1.5, size=(D, C, K)).astype(np.float32)
+    t_off, nsamp = 3, 30
+    t_out = nsamp - int((dl.astype(np.int64) + tp - 1).max())
+    brute = np.zeros((D, t_out))
+    for d in range(D):
+        for t in range(t_out):
+            s = 0.0
+            for c in range(C):
+                for k in range(int(tp[d, c])):
+                    s += abs(float(w[d, c, k])) * abs(float(I[c, t_off + t + dl[d, c] + k]))
+            brute[d, t] = s
+    got = oracle.c_abs_scale(I, dl, tp, w=w, t_offset=t_off, nsamp=nsamp)
+    np.testing.assert_allclose(got, brute, rtol=1e-13, atol=0)
+    rows = np.array([1, 3], np.int32)
+    np.testing.assert_allclose(oracle.c_abs_scale(I, dl, tp, w=w, t_offset=t_off, nsamp=nsamp, rows=rows),
+                               brute[rows], rtol=1e-13, atol=0)
+    # unit weights: Σ |I| over the sample set
+    unit = oracle.c_abs_scale(I, dl, tp, t_offset=t_off, nsamp=nsamp)
+    np.testing.assert_allclose(unit, ref.dedisperse(np.abs(I).astype(np.float64), dl, tp,
+                                                    w=np.ones((D, C, K)), t_offset=t_off, nsamp=nsamp),
+                               rtol=1e-13, atol=0)
+
+
 def test_hand_adjoint():
     g = _gold("hand_sums.json")
     I = np.array(g["I"], np.float32)
@@ -224,8 +273,8 @@ def test_trial_rule_dropouts_and_limits():
     b = synth.CRAFT_BAND
     dms, eps = ref.trial_dms(0.0, 4000.0, 4096, b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, 1.0)
     assert dms[-1] == pytest.approx(4000.0, rel=1e-9)
-    dd = ref.dm_diag(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms)
-    dt_ = ref.dm_tau(b.nchan, b.f_lo_mhz, b.df_mhz, 1.0)
+    dd = _smear_root_dm(b, b.dt_ms)
+    dt_ = _smear_root_dm(b, 1.0)
     # low-DM step: (2ε/C)·√(DM_diag² + DM_τ²) from DM_0 = 0
     assert dms[1] - dms[0] == pytest.approx(2 * eps / b.nchan * math.sqrt(dd ** 2 + dt_ ** 2), rel=1e-12)
     # high-DM ratio tends to 1 + 2ε/C
@@ -234,8 +283,54 @@ def test_trial_rule_dropouts_and_limits():
     assert abs(r - lim) < 0.05 * (lim - 1)
     # DM_diag is where the mean first-order channel smear equals Δt
     nu = ref.channel_top_ghz(b.nchan, b.f_lo_mhz, b.df_mhz)
-    mean_smear = np.mean(2 * dd * (b.df_mhz / 1000) * 4.15 / nu ** 3)
+    mean_smear = np.mean(2 * ref.dm_diag(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms)
+                         * (b.df_mhz / 1000) * 4.15 / nu ** 3)
     assert mean_smear == pytest.approx(b.dt_ms, rel=1e-12)
+
+
+def _smear_root_dm(band, target_ms, k_dm=4.15):
+    """The DM at which the mean first-order smear across a channel, 2·DM·Δν·k_dm/ν_c³
+    (Sec. 3, averaged over the channels as in Sec. 6.2), equals target_ms: found by
+    bisection on the smear itself, not from the closed form of eq. DM_tau."""
+    nu = (band.f_lo_mhz + (np.arange(band.nchan) + 1) * band.df_mhz) / 1000.0
+    dnu = band.df_mhz / 1000.0
+
+    def mean_smear(dm):
+        return float(np.mean([2.0 * dm * dnu * k_dm / v ** 3 for v in nu]))
+
+    lo, hi = 0.0, 1.0
+    while mean_smear(hi) < target_ms:
+        hi *= 2.0
+    for _ in range(200):
+        mid = 0.5 * (lo + hi)
+        if mean_smear(mid) < target_ms:
+            lo = mid
+        else:
+            hi = mid
+    return 0.5 * (lo + hi)
+
+
+@pytest.mark.parametrize("band,tau_ms", [
+    (synth.CRAFT_BAND, 3.0),                        # pulse three samples wide
+    (synth.Band(304, 700.0, 1.0, 1.0), 0.25),       # narrower than a sample
+    (synth.Band(256, 21000.0, 7.8125, 0.1), 2.0),   # Galactic-Centre band, 100 us sampling
+])
+def test_dm_tau_is_where_mean_smear_equals_pulse_width(band, tau_ms):
+    """DM_τ (eq. DM_tau, Sec. 6.2) is the DM whose mean smear across a channel equals the
+    scattered pulse width τ'_av; DM_diag the one whose smear equals Δt.  Checked at
+    τ'_av ≠ Δt against a bisection on the smear, so that swapping τ' for Δt or dropping
+    it fails; the ratio DM_τ/DM_diag is τ'_av/Δt."""
+    dt_ = ref.dm_tau(band.nchan, band.f_lo_mhz, band.df_mhz, tau_ms)
+    dd = ref.dm_diag(band.nchan, band.f_lo_mhz, band.df_mhz, band.dt_ms)
+    assert dt_ == pytest.approx(_smear_root_dm(band, tau_ms), rel=1e-12)
+    assert dd == pytest.approx(_smear_root_dm(band, band.dt_ms), rel=1e-12)
+    assert dt_ / dd == pytest.approx(tau_ms / band.dt_ms, rel=1e-12)
+    # the trial rule's low-DM step with both smear terms (eq. trial DMs at DM_0 = 0)
+    dms, eps = ref.trial_dms(0.0, 2000.0, 512, band.nchan, band.f_lo_mhz, band.df_mhz,
+                             band.dt_ms, tau_ms)
+    step = 2 * eps / band.nchan * math.sqrt(_smear_root_dm(band, band.dt_ms) ** 2
+                                            + _smear_root_dm(band, tau_ms) ** 2)
+    assert dms[1] - dms[0] == pytest.approx(step, rel=1e-9)
 
 
 def test_dm_error_attenuation_closed_form():

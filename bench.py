@@ -35,8 +35,8 @@ if ROOT not in sys.path:
 METRIC = "dedispersed DM-trial·samples/s on 1 GB300 and % roofline; fwd+bwd vs plain fwd"
 UNIT = "DM-trial·samples/s"
 FALLBACK_PEAKS = {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "sm_max_mhz": 2070.0}
-N_SM = 152
 FP32_LANES_PER_SM = 128
+SMEM_BYTES_PER_CLK_PER_SM = 128
 LAUNCHES_PER_STEP = 4    # channel stats, dedispersion, normaliser, boxcar scan
 
 
@@ -219,13 +219,17 @@ def run_gpu(args):
     value = ws * units / (ms / 1e3)
 
     e2e = None if args.no_e2e else e2e_run(args, W, ws, plan, x, out, widths, stream)
-    # the device's measured FP32 FMA and INT32 add rates (after the timed region)
-    live = {"fma_tflops": dd.alu_peak("fma") / 1e12, "iadd_tops": dd.alu_peak("iadd") / 1e12}
+    # the device's measured FP32 FMA (scalar and packed pairs) and INT32 add rates (after
+    # the timed region), and its SM count
+    live = {"fma_tflops": dd.alu_peak("fma") / 1e12, "fma2_tflops": dd.alu_peak("fma2") / 1e12,
+            "iadd_tops": dd.alu_peak("iadd") / 1e12,
+            "sms": torch.cuda.get_device_properties(dev).multi_processor_count}
     extras = None
     if rank == 0 and not args.no_extras:
         extras = {"fwd_bwd": diff_extra(dd, dev, flush, stream),
                   "batched": batched_extra(dd, dev, flush, stream),
-                  "large_lowband": large_extra(dd, dev, flush, stream, iadd_tops=live["iadd_tops"])}
+                  "large_lowband": large_extra(dd, dev, flush, stream, iadd_tops=live["iadd_tops"],
+                                               sms=live["sms"])}
     return _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras, live)
 
 
@@ -409,7 +413,7 @@ def batched_extra(dd, dev, flush, stream, reps=3):
 
 
 def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, iadd_tops=None,
-                sm_mhz=None):
+                sm_mhz=None, sms=None):
     """Large low-band configuration: 1024 ch over 700-1000 MHz, dt 64 us, 2^20 uint8
     samples, 8192 trial DMs 0-2000 (unit weights, run-length sums), streamed in
     overlapping chunks of `chunk` outputs (each chunk reads its outputs plus d_max
@@ -418,6 +422,8 @@ def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, 
     import synth
     if sm_mhz is None:
         sm_mhz = float(_peaks()[0].get("sm_max_mhz", 2070.0))
+    if sms is None:
+        sms = torch.cuda.get_device_properties(dev).multi_processor_count
     cfg = synth.make_large(nsamp=nsamp)
     b, T = cfg["band"], cfg["nsamp"]
     dms = cfg["dms"] if ndm == len(cfg["dms"]) else np.linspace(0.0, cfg["dms"][-1], ndm)
@@ -470,16 +476,16 @@ def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, 
         "fused_series_bytes_not_stored": plan.ndm * chunk * 4,
         # the run-length kernel's bound: shared-memory reads, one 4-byte word per (trial,
         # channel, output) from the CTA's difference rows (two without them), against
-        # 152 SMs x 128 B/clk at the measured clock
+        # the SMs x 128 B/clk at the measured clock
         "smem_read_bytes_per_block": 4.0 * dct,
         "smem_read_tbps": 4.0 * dct / (dd_ms / 1e3) / 1e12,
-        "smem_peak_tbps": N_SM * 128 * sm_mhz * 1e6 / 1e12,
+        "smem_peak_tbps": sms * SMEM_BYTES_PER_CLK_PER_SM * sm_mhz * 1e6 / 1e12,
         "graded_adds_per_block": graded,
         "graded_tops": graded / (dd_ms / 1e3) / 1e12,
         "bound": "shared-memory reads (1 word per trial, channel and output with the CTA's difference rows; see profiles)",
     }
     res["smem_read_frac"] = res["smem_read_tbps"] / res["smem_peak_tbps"]
-    res["smem_peak_kind"] = f"derived: {N_SM} SMs x 128 B/clk x {sm_mhz:.0f} MHz"
+    res["smem_peak_kind"] = f"derived: {sms} SMs x {SMEM_BYTES_PER_CLK_PER_SM} B/clk x {sm_mhz:.0f} MHz"
     if iadd_tops:
         res["graded_frac_of_measured_iadd"] = res["graded_tops"] / iadd_tops
     plan.close()
@@ -487,26 +493,22 @@ def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, 
 
 
 def _profile_traffic():
-    """DRAM bytes per dedispersion launch from the committed ncu summary, if it was
-    taken on the current kernel source (else None)."""
+    """DRAM bytes per dedispersion launch from the ncu capture recorded in
+    profiles/traffic.json, if it was taken on the current kernel source (else None)."""
     import hashlib
-    path = os.path.join(ROOT, "profiles", "k_dedisp_f32_craft.md")
+    path = os.path.join(ROOT, "profiles", "traffic.json")
     src = os.path.join(ROOT, "paper_1301_3968_gb300", "csrc", "dd_dedisp.cu")
     try:
-        text = open(path).read()
+        with open(path) as f:
+            rec = json.load(f)["k_dedisp_f32_craft"]
         sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
-    except OSError:
+    except (OSError, KeyError, ValueError):
         return None
-    got = {}
-    for line in text.splitlines():
-        if ":" in line:
-            k, v = line.split(":", 1)
-            got[k.strip().strip("-* `")] = v.strip().strip("` ")
-    if got.get("source_sha256") != sha:
+    if rec.get("source_sha256") != sha:
         return None
     try:
-        return float(got["dram_bytes_per_full_launch"])
-    except (KeyError, ValueError):
+        return float(rec["dram_bytes_per_launch"])
+    except (KeyError, TypeError, ValueError):
         return None
 
 
@@ -515,7 +517,16 @@ def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras=None, live=N
         return None
     peaks, kind = _peaks()
     sm_max = float(peaks.get("sm_max_mhz", 2070.0))
-    peak_tflops = N_SM * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    sms = live["sms"] if live else 152
+    derived = sms * FP32_LANES_PER_SM * 2 * sm_max * 1e6 / 1e12
+    # the denominator is the largest of the derived FP32 rate and the measured scalar and
+    # packed FMA rates
+    cands = {"derived": derived}
+    if live:
+        cands["measured_fma"] = live["fma_tflops"]
+        cands["measured_fma2"] = live["fma2_tflops"]
+    peak_name = max(cands, key=cands.get)
+    peak_tflops = cands[peak_name]
     k_avg = sum(k_ms) / len(k_ms)
     achieved = W["flops"] / (k_avg / 1e3) / 1e12
     res = {
@@ -532,14 +543,18 @@ def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras=None, live=N
                      "achieved": achieved, "peak": peak_tflops, "unit": "TFLOP/s",
                      "frac": achieved / peak_tflops,
                      "traffic": args.traffic if args.traffic is not None else _profile_traffic(),
-                     "peak_kind": f"derived: {N_SM} SMs x {FP32_LANES_PER_SM} FP32 lanes x 2 flop x "
-                                  f"{sm_max:.0f} MHz ({kind} sm_max_mhz)",
+                     "peak_kind": (f"{peak_name}: the largest of the derived rate ({sms} SMs x "
+                                   f"{FP32_LANES_PER_SM} FP32 lanes x 2 flop x {sm_max:.0f} MHz, {kind} "
+                                   "sm_max_mhz = %.1f) and the measured scalar and packed FMA rates" % derived),
+                     "peak_candidates": cands,
                      "kernel_ms": k_avg, "flops_per_launch": W["flops"]},
         "alu_peaks_measured": live,
         "clocks": clocks,
     }
     if live:
         res["roofline"]["frac_of_measured_fma"] = achieved / live["fma_tflops"]
+        res["roofline"]["frac_of_measured_fma2"] = achieved / live["fma2_tflops"]
+        res["config"]["sms"] = sms
     if extras is not None:
         res["extras"] = extras
     if not args.no_cpu_baseline:

@@ -26,7 +26,8 @@
  *     16 bytes and the input base pointer 16-byte aligned (rows are staged in 16-byte
  *     chunks).  Violations return DD_ERR_ARG.
  *   - No call here allocates device memory except dd_plan_create / dd_set_profiles /
- *     the first device call on a plan (tables), dd_boxcar_snr when the width count
+ *     the first device call on a plan (tables; on a device's first plan also the 8 MiB
+ *     array of dd_boxcar_snr_noalloc), dd_boxcar_snr when the width count
  *     grows (normaliser workspace), dd_dedisperse on a run-length plan when nsamp
  *     grows (prefix scratch), dd_dedisperse_boxcar when its scratch grows, and the
  *     first dd_backward (adjoint workspace).
@@ -167,19 +168,22 @@ dd_status dd_boxcar_snr(dd_plan_t plan, const void* d_series, int64_t ld, int64_
  * that gives the library a fixed device budget.  The paper has no counterpart; this is
  * a deployment variant.  Same arguments, results and errors as dd_boxcar_snr, but the
  * normaliser tables live in an 8 MiB array in device global memory that is part of the
- * library image (every GPU that loads the library holds it until the process exits),
- * so the call allocates nothing.  Limits and rules:
+ * library image, so the call allocates nothing.  Limits and rules:
  *   - ndm * 8 + 2 * ndm * nw * 4 + nw * 4 bytes (each part rounded up to 256) must fit
  *     in 8 MiB (about ndm * nw <= 1,000,000); larger requests return DD_ERR_CAPACITY.
  *   - The plan's tables must already be on the current device (any earlier device call
  *     on the plan, e.g. dd_dedisperse, puts them there); otherwise DD_ERR_STATE, since
- *     uploading them would allocate.
- *   - The first call on each device looks up the array's device address and caches it;
- *     make that first call before any stream capture.
+ *     uploading them would allocate.  Putting a plan's tables on a device for the first
+ *     time also loads the 8 MiB array and the boxcar kernels there (CUDA would otherwise
+ *     load them lazily, at this call) and looks up the array's device address; that
+ *     device then holds the array until the process exits.
  *   - Every call shares the one array, and it keeps the last call's contents: calls on
  *     one stream are ordered, but calls that overlap on the GPU (different streams or
  *     host threads) race.  Nothing in it needs clearing: each call writes every value
- *     it reads. */
+ *     it reads.
+ *   - The widths are sent with a stream-ordered copy from the caller's host array.  From
+ *     pageable memory the copy has read them when the call returns; from pinned memory
+ *     the array must stay unchanged until the stream reaches the call. */
 dd_status dd_boxcar_snr_noalloc(dd_plan_t plan, const void* d_series, int64_t ld, int64_t t_len,
                                 const int32_t* widths, int32_t nw, const double* d_chan_mean,
                                 const double* d_chan_std, float* d_peak_snr, int32_t* d_peak_t,
@@ -373,7 +377,8 @@ dd_status dd_detector_profile(const double* pbar, int32_t nchan, int32_t nt, con
 /* Measured ALU throughput of the current device (no counterpart in the paper; the
  * denominator of the roofline fraction of the ALU-bound kernels).  kind 0: FP32 fused
  * multiply-adds, reported as flops/s (2 per FMA); kind 1: INT32 three-input adds,
- * reported as additions/s (2 per instruction).  Dependency-free loops over every SM;
+ * reported as additions/s (2 per instruction); kind 2: packed FP32 pairs (fma.rn.f32x2,
+ * the instruction of the fp32 dedispersion kernels), flops/s (4 per instruction).  Dependency-free loops over every SM;
  * one warm-up launch, one timed launch (about 0.1 s); synchronises the stream.
  * Errors: DD_ERR_ARG, DD_ERR_OOM, DD_ERR_CUDA. */
 dd_status dd_alu_peak(int32_t kind, double* ops_per_s, void* stream);

@@ -48,9 +48,10 @@ def _stream(stream=None) -> ctypes.c_void_p:
 
 
 def alu_peak(kind: str = "fma", stream=None) -> float:
-    """Measured device throughput: "fma" in flops/s (FP32 FMA), "iadd" in additions/s."""
+    """Measured device throughput: "fma" in flops/s (FP32 FMA), "fma2" in flops/s (packed
+    FP32 pairs), "iadd" in additions/s."""
     v = ctypes.c_double()
-    check(_lib.load().dd_alu_peak({"fma": 0, "iadd": 1}[kind], ctypes.cast(ctypes.byref(v), ctypes.c_void_p),
+    check(_lib.load().dd_alu_peak({"fma": 0, "iadd": 1, "fma2": 2}[kind], ctypes.cast(ctypes.byref(v), ctypes.c_void_p),
                                   _stream(stream)), "dd_alu_peak")
     return v.value
 

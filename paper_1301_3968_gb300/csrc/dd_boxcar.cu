@@ -681,6 +681,24 @@ dd_status launch_boxcar_scratch(dd_plan_s* p, const void* x, int64_t ld, int64_t
     return dispatch_boxcar(p, a, widths, nw, s, false);
 }
 
+// Loads every kernel that launch_boxcar_scratch can launch onto the current device.
+// Under lazy module loading a kernel's code is placed in device memory at its first
+// launch; the allocation-free boxcar entry point must not be the call that does that.
+dd_status preload_boxcar_kernels() {
+    cudaFuncAttributes fa;
+    const void* kerns[] = {
+        (const void*)k_norm,
+        (const void*)k_boxcar_run<float, float>, (const void*)k_boxcar<float, float>,
+        (const void*)k_boxcar_run<int, int>, (const void*)k_boxcar<int, int>,
+        (const void*)k_boxcar_run<int, long long>, (const void*)k_boxcar<int, long long>,
+    };
+    for (const void* k : kerns) {
+        const cudaError_t e = cudaFuncGetAttributes(&fa, k);
+        if (e != cudaSuccess) return cuda_status(e);
+    }
+    return DD_OK;
+}
+
 // The normaliser of the plan's trials for a width list: dev.off, dev.mu, dev.isd.
 dd_status launch_norm(dd_plan_s* p, const int32_t* widths, int32_t nw, const double* mean,
                       const double* sd, cudaStream_t s) {

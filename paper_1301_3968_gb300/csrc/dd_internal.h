@@ -255,6 +255,10 @@ size_t fused_smem_for(const dd_plan_s* p, int rowlen, int C);
 int fused_blocks_per_sm(const dd_plan_s* p, size_t smem);
 dd_status launch_dedisperse_fused(const dd_plan_s* p, DedispArgs a, const FusedArgs& f, size_t smem,
                                   cudaStream_t s);
+// allocation-free boxcar path: loads its kernels and its static scratch array onto the
+// current device (once per device; called when a plan's tables are uploaded)
+dd_status preload_boxcar_kernels();
+dd_status noalloc_preload();
 dd_status launch_backward(dd_plan_s* p, const float* in, int64_t ld, int64_t t_offset,
                           int64_t t_out, const float* g, int64_t gld, float* gw, float* gin,
                           int64_t gin_ld, cudaStream_t s);

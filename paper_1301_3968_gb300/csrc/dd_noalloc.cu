@@ -7,6 +7,11 @@
 // a host that gives the library a fixed device-memory budget.  dd_boxcar_snr_noalloc
 // computes the same result with its scratch in a fixed-size array in device global
 // memory that is part of the library image, so it allocates nothing.
+//
+// CUDA loads a module's code and its __device__ arrays onto a device lazily, at first
+// use.  So that this entry point's first call is not that use, the array and the boxcar
+// kernels are loaded when a plan's tables are first put on a device (noalloc_preload,
+// from upload_tables), which the entry point requires anyway.
 #include <mutex>
 
 #include "dd_internal.h"
@@ -15,7 +20,8 @@ namespace {
 
 // Scratch for the normaliser tables of one call: per-trial offsets (fp64), the
 // normaliser means and inverse deviations ([ndm][nw] fp32 each) and the width list.
-// Every GPU that loads the library holds these 8 MiB until the process exits.
+// Every GPU on which a plan's tables have been uploaded holds these 8 MiB until the
+// process exits.
 constexpr size_t kScratchBytes = (size_t)8 << 20;
 static __device__ __align__(256) unsigned char g_noalloc_scratch[kScratchBytes];
 
@@ -27,7 +33,8 @@ size_t align256(size_t n) { return (n + 255) & ~(size_t)255; }
 
 // The array's device address on the current device.  In host code the array's name
 // is only a stand-in, so the address is looked up once per device (with that device
-// current) and cached.
+// current) and cached.  The first lookup on a device also loads the array and the
+// boxcar kernels there.
 dd_status scratch_address(void** out) {
     int dev = -1;
     cudaError_t e = cudaGetDevice(&dev);
@@ -38,6 +45,8 @@ dd_status scratch_address(void** out) {
         void* p = nullptr;
         e = cudaGetSymbolAddress(&p, g_noalloc_scratch);
         if (e != cudaSuccess) return dd::cuda_status(e);
+        const dd_status st = dd::preload_boxcar_kernels();
+        if (st != DD_OK) return st;
         g_scratch_addr[dev] = p;
     }
     *out = g_scratch_addr[dev];
@@ -45,6 +54,13 @@ dd_status scratch_address(void** out) {
 }
 
 }  // namespace
+
+namespace dd {
+dd_status noalloc_preload() {
+    void* p = nullptr;
+    return scratch_address(&p);
+}
+}  // namespace dd
 
 extern "C" dd_status dd_boxcar_snr_noalloc(dd_plan_t p, const void* x, int64_t ld, int64_t t_len,
                                            const int32_t* widths, int32_t nw, const double* mean,
@@ -76,7 +92,9 @@ extern "C" dd_status dd_boxcar_snr_noalloc(dd_plan_t p, const void* x, int64_t l
     float* isd = (float*)(s + b_off + b_tab);
     int32_t* wdev = (int32_t*)(s + b_off + 2 * b_tab);
     // every scratch value this call reads is written earlier in the same call, so
-    // nothing needs clearing; the widths travel by a stream-ordered copy
+    // nothing needs clearing; the widths travel by a stream-ordered copy (from pageable
+    // memory the copy has read them when it returns; from pinned memory only once the
+    // stream reaches it)
     e = cudaMemcpyAsync(wdev, widths, (size_t)nw * sizeof(int32_t), cudaMemcpyHostToDevice,
                         (cudaStream_t)stream);
     if (e != cudaSuccess) return dd::cuda_status(e);

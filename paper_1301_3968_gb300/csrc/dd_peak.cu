@@ -1,10 +1,12 @@
 // Measured ALU throughput of the device: the denominators for kernels bound by plain
 // FP32 FMA or INT32 add issue.  Each thread runs 16 independent dependency chains (no
 // memory traffic in the loop) and the grid fills every SM several times over; one
-// warm-up launch, then one launch timed with CUDA events.
+// warm-up launch, then one launch timed with CUDA events.  The packed form runs the
+// paired fma.rn.f32x2 that the fp32 dedispersion kernels issue.
 #include <cstdint>
 
 #include "dd_internal.h"
+#include "dd_packed.cuh"
 
 namespace dd {
 namespace {
@@ -22,6 +24,28 @@ __global__ void __launch_bounds__(256) k_fma_peak(float* sink, int iters, float 
     float s = 0.f;
 #pragma unroll
     for (int i = 0; i < kChains; ++i) s += a[i];
+    if (s == 1234.5f) sink[0] = s;  // keeps the loop alive
+}
+
+// Packed pairs: each chain is one 64-bit register of two fp32 lanes, one fma.rn.f32x2
+// (two FMAs) per chain per step.
+__global__ void __launch_bounds__(256) k_fma2_peak(float* sink, int iters, float m, float b) {
+    uint64_t a[kChains];
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) a[i] = pk2(threadIdx.x * 1e-3f + i, threadIdx.x * 2e-3f - i);
+    const uint64_t mm = pk_dup(m), bb = pk_dup(b);
+    for (int it = 0; it < iters; ++it) {
+#pragma unroll
+        for (int i = 0; i < kChains; ++i)  // a = a * m + b, both lanes
+            asm("fma.rn.f32x2 %0, %1, %2, %3;" : "=l"(a[i]) : "l"(a[i]), "l"(mm), "l"(bb));
+    }
+    float s = 0.f;
+#pragma unroll
+    for (int i = 0; i < kChains; ++i) {
+        float lo, hi;
+        unpk(a[i], lo, hi);
+        s += lo + hi;
+    }
     if (s == 1234.5f) sink[0] = s;  // keeps the loop alive
 }
 
@@ -47,7 +71,7 @@ __global__ void __launch_bounds__(256) k_iadd_peak(int* sink, int iters, int u, 
 }  // namespace dd
 
 extern "C" dd_status dd_alu_peak(int32_t kind, double* ops_per_s, void* stream) {
-    if (!ops_per_s || (kind != 0 && kind != 1)) return DD_ERR_ARG;
+    if (!ops_per_s || kind < 0 || kind > 2) return DD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     int dev = 0, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -66,6 +90,8 @@ extern "C" dd_status dd_alu_peak(int32_t kind, double* ops_per_s, void* stream) 
             cudaEventRecord(e0, s);
             if (kind == 0)
                 dd::k_fma_peak<<<blocks, threads, 0, s>>>((float*)sink, rep ? iters : 200, 1.0000001f, 1e-7f);
+            else if (kind == 2)
+                dd::k_fma2_peak<<<blocks, threads, 0, s>>>((float*)sink, rep ? iters : 200, 1.0000001f, 1e-7f);
             else
                 dd::k_iadd_peak<<<blocks, threads, 0, s>>>((int*)sink, rep ? iters : 200, 3, 5);
             cudaEventRecord(e1, s);
@@ -78,8 +104,9 @@ extern "C" dd_status dd_alu_peak(int32_t kind, double* ops_per_s, void* stream) 
     if (e1) cudaEventDestroy(e1);
     cudaFree(sink);
     if (e != cudaSuccess) return dd::cuda_status(e);
-    // FP32: 2 flops per FMA; INT32: 2 additions per three-input add
-    const double ops = 2.0 * dd::kChains * (double)iters * blocks * threads;
+    // FP32: 2 flops per FMA (two FMAs per packed instruction); INT32: 2 additions per
+    // three-input add
+    const double ops = (kind == 2 ? 4.0 : 2.0) * dd::kChains * (double)iters * blocks * threads;
     *ops_per_s = ops / (ms * 1e-3);
     return DD_OK;
 }

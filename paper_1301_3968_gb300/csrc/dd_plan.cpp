@@ -430,6 +430,9 @@ dd_status upload_tables(dd_plan_s* p) {
     if ((st = put(&p->dev.status, &zero, 1)) != DD_OK) return st;
     e = cudaMalloc((void**)&p->dev.off, (size_t)p->ndm * sizeof(double));
     if (e != cudaSuccess) return cuda_status(e);
+    // place dd_boxcar_snr_noalloc's scratch array and kernels on this device now, so
+    // that its calls allocate nothing (lazy module loading would do it at its first call)
+    if ((st = noalloc_preload()) != DD_OK) return st;
     p->dev_dirty = false;
     return DD_OK;
 }

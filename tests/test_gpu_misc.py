@@ -54,8 +54,13 @@ def test_dm_range_split_concatenates(dd, in_type):
 
 
 def test_measured_alu_peaks_are_plausible(dd):
+    import torch
     fma = dd.alu_peak("fma")
+    fma2 = dd.alu_peak("fma2")
     iadd = dd.alu_peak("iadd")
-    derived = 152 * 128 * 2 * 2.07e9           # FP32 lanes x 2 flops x max SM clock
+    sms = torch.cuda.get_device_properties(0).multi_processor_count
+    derived = sms * 128 * 2 * 2.07e9           # FP32 lanes x 2 flops x max SM clock
     assert 0.3 * derived < fma < 1.1 * derived
+    # packed pairs: two FMAs per instruction, at most twice the scalar rate
+    assert 0.3 * derived < fma2 < 2.2 * derived
     assert 0.1 * derived < iadd < 2.2 * derived    # additions: two per three-input add

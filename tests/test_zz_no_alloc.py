@@ -3,8 +3,9 @@
 Some callers may not allocate device memory while running, e.g. a real-time pipeline
 that fixes its device footprint at start-up.  This entry point keeps its scratch in a
 fixed device array inside the library; here its results are checked against
-dd_boxcar_snr on two calls in a row, through the C ABI.  The file is named so that
-pytest collects it last."""
+dd_boxcar_snr on two calls in a row, through the C ABI, and the device's free memory
+is checked to stay the same across calls (the first one included).  The file is named
+so that pytest collects it last."""
 import ctypes
 
 import numpy as np
@@ -84,3 +85,44 @@ def test_noalloc_rejects_oversize_and_missing_tables():
     assert call(256) == 7                    # DD_ERR_CAPACITY: 4096 x 256 does not fit 8 MiB
     assert call(8) == 0
     torch.cuda.synchronize()
+
+
+def test_noalloc_calls_leave_device_memory_unchanged():
+    """Back-to-back calls on one stream, with different plans and width lists sharing the
+    scratch array, change the device's free memory by nothing (the first call after the
+    plans' tables went to the device included) and each matches dd_boxcar_snr."""
+    import torch
+    from paper_1301_3968_gb300 import build
+    build.build()
+    import paper_1301_3968_gb300 as dd
+    torch.cuda.set_device(0)
+    cases = []
+    for seed, weighted, widths in ((5, False, np.arange(1, 17, dtype=np.int32)),
+                                   (6, True, np.array([1, 2, 3, 5, 8, 13, 21], dtype=np.int32))):
+        cfg = synth.make_plain(seed=synth.sub_seed("tests", 50 + seed), snr_total=16.0)
+        b = cfg["band"]
+        data = cfg["data"].astype(np.float32) if weighted else cfg["data"]
+        plan = dd.Plan(dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, cfg["nsamp"],
+                               "f32" if weighted else "u8"), cfg["dms"])
+        if weighted:
+            _, t = plan.tables()
+            w = np.random.default_rng(seed).uniform(0.5, 1.5, size=(len(cfg["dms"]), b.nchan, int(t.max())))
+            plan.set_profiles(weights=w.astype(np.float32))
+        x = torch.from_numpy(data).cuda()
+        out = plan.dedisperse(x, nsamp=cfg["nsamp"])           # puts the tables on the device
+        mean, sd = plan.channel_stats(x, nsamp=cfg["nsamp"])
+        peak = torch.full((plan.ndm, len(widths)), -1.0, dtype=torch.float32, device="cuda")
+        arg = torch.full((plan.ndm, len(widths)), -1, dtype=torch.int32, device="cuda")
+        cases.append((plan, out, mean, sd, widths, peak, arg))
+    torch.cuda.synchronize()
+    free0 = torch.cuda.mem_get_info()[0]
+    for rep in range(2):
+        for plan, out, mean, sd, widths, peak, arg in cases:   # no synchronisation between calls
+            plan.boxcar_snr_noalloc(out, widths, mean, sd, peak, arg)
+        torch.cuda.synchronize()
+        assert torch.cuda.mem_get_info()[0] == free0, f"free device memory changed (pass {rep})"
+    for plan, out, mean, sd, widths, peak, arg in cases:
+        want_p, want_a, _ = plan.boxcar_snr(out, widths, mean, sd)
+        np.testing.assert_allclose(peak.cpu().numpy(), want_p.cpu().numpy(), rtol=1e-5, atol=1e-5)
+        np.testing.assert_array_equal(arg.cpu().numpy(), want_a.cpu().numpy())
+        plan.close()

@@ -357,6 +357,20 @@ dd_status dd_select_samples(const double* pbar, int32_t nchan, int32_t nt, int32
                             int32_t* delay, int32_t* ntaps, float* w, int32_t* nsel, double* gain);
 dd_status dd_exact_profiles(dd_plan_t plan, double tau_prime_ms, int32_t* delay, int32_t* ntaps);
 
+/* dd_select_profiles: the Sec. 2.2 sample selection for every trial of the plan, on the
+ * eq. Pavg cell powers of the rectangular scattered pulse of eq. profile_sb (dd_predict_rect
+ * with p0 = 1, spectral index alpha about nu0_ghz, scattering tau_ms, width tau_prime_ms) at
+ * the trial's own DM, arriving `phase` samples (>= 0) into output sample 0 at the top of the
+ * band.  Each trial's cells run from there to the end of its sweep across the whole band,
+ * plus tau' and two samples.  Writes delay and ntaps [ndm][nchan], the weights w
+ * [ndm][nchan][kmax] (0/1, as dd_select_samples; may be NULL), each trial's S/N gain over
+ * taking every sample with pulse power (gains [ndm], may be NULL) and the longest run in
+ * *kused (may be NULL).  Call with w = NULL to learn kused, then with kmax >= kused.  Host
+ * only.  Errors: DD_ERR_ARG, DD_ERR_CAPACITY (a run longer than kmax), DD_ERR_OVERFLOW. */
+dd_status dd_select_profiles(dd_plan_t plan, double tau_ms, double tau_prime_ms, double alpha,
+                             double nu0_ghz, double phase, int32_t kmax, int32_t* delay,
+                             int32_t* ntaps, float* w, double* gains, int32_t* kused);
+
 /* The comparison detectors of Sec. 5 as profiles for the same dedispersion kernel, from one
  * trial's predicted powers pbar [nchan][nt] (host):
  *   kind 0, dynamic-spectrum matched filter: every cell with power, weighted by its power

@@ -70,6 +70,8 @@ SIGNATURES = {
                                 ctypes.c_double, ctypes.c_double, ctypes.c_double, c_i32, c_vp]),
     "dd_select_samples": (c_i32, [c_vp, c_i32, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "dd_exact_profiles": (c_i32, [c_vp, ctypes.c_double, c_vp, c_vp]),
+    "dd_select_profiles": (c_i32, [c_vp, ctypes.c_double, ctypes.c_double, ctypes.c_double,
+                                   ctypes.c_double, ctypes.c_double, c_i32, c_vp, c_vp, c_vp, c_vp, c_vp]),
     "dd_detector_profile": (c_i32, [c_vp, c_i32, c_i32, c_vp, c_i32, c_i32, c_vp, c_vp, c_vp, c_vp]),
     "dd_plan_get_method": (c_i32, [c_vp, c_vp]),
     "dd_plan_autotune": (c_i32, [c_vp, c_vp, c_i64, c_vp, c_i64, ctypes.c_char_p, c_vp, c_vp]),

@@ -111,22 +111,26 @@ def select_profiles(band: Band, dms, tau_ms: float = 1.0, tau_prime_ms: float = 
                     alpha: float = 0.0, nu0_ghz: float = 1.0, phase: float = 0.0):
     """Selected-sample profiles for every trial (pulse arriving `phase` samples into the
     output sample at the top of the band): delay [D][C], ntaps [D][C], weights [D][C][K]
-    and each trial's S/N gain over taking every sample with pulse power."""
-    dms = np.asarray(dms, dtype=np.float64)
-    lo = band.f_lo_mhz / 1000.0
-    top = (band.f_lo_mhz + band.nchan * band.df_mhz) / 1000.0
-    k = band.k_dm if band.k_dm > 0 else 4.15
-    rows = []
-    for dm in dms:
-        span = k * dm * (1.0 / lo ** 2 - 1.0 / top ** 2) + tau_prime_ms + 2 * band.dt_ms
-        nt = int(np.ceil(span / band.dt_ms)) + 2
-        p = predict_rect(band, dm, nt, phase * band.dt_ms, tau_ms, tau_prime_ms, alpha, nu0_ghz)
-        rows.append(select_samples(p, nt))
-    K = max(int(r[1].max()) for r in rows)
-    delay = np.stack([r[0] for r in rows])
-    taps = np.stack([r[1] for r in rows])
-    w = np.stack([r[2][:, :K] for r in rows])
-    gains = np.array([r[4] for r in rows])
+    and each trial's S/N gain over taking every sample with pulse power
+    (dd_select_profiles)."""
+    lib = _lib.load()
+    plan = Plan(band, dms)
+    try:
+        D, C = plan.ndm, band.nchan
+        delay = np.zeros((D, C), np.int32)
+        taps = np.zeros((D, C), np.int32)
+        gains = np.zeros(D, np.float64)
+        kused = ctypes.c_int32(0)
+        args = (float(tau_ms), float(tau_prime_ms), float(alpha), float(nu0_ghz), float(phase))
+        check(lib.dd_select_profiles(plan._h, *args, 0, _np_ptr(delay), _np_ptr(taps), None,
+                                     None, ctypes.cast(ctypes.byref(kused), ctypes.c_void_p)),
+              "dd_select_profiles")
+        K = int(kused.value)
+        w = np.zeros((D, C, K), np.float32)
+        check(lib.dd_select_profiles(plan._h, *args, K, _np_ptr(delay), _np_ptr(taps), _np_ptr(w),
+                                     _np_ptr(gains), None), "dd_select_profiles")
+    finally:
+        plan.close()
     return delay, taps, w, gains
 
 

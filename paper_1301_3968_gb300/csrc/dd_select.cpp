@@ -182,6 +182,51 @@ dd_status dd_detector_profile(const double* pbar, int32_t nchan, int32_t nt, con
     return DD_OK;
 }
 
+dd_status dd_select_profiles(dd_plan_t plan, double tau_ms, double tau_prime_ms, double alpha,
+                             double nu0_ghz, double phase, int32_t kmax, int32_t* delay,
+                             int32_t* ntaps, float* w, double* gains, int32_t* kused) {
+    if (!plan || !delay || !ntaps || (w && kmax < 1) || !(phase >= 0) || !(tau_prime_ms > 0))
+        return DD_ERR_ARG;
+    const dd_band& b = plan->band;
+    const double k = b.k_dm > 0 ? b.k_dm : kDefaultKdm;
+    const double lo = b.f_lo_mhz / 1000.0;
+    const double top = (b.f_lo_mhz + b.nchan * b.df_mhz) / 1000.0;
+    const int C = b.nchan;
+    int32_t kmx = 1;
+    std::vector<double> pbar;
+    std::vector<float> wrow;
+    for (int d = 0; d < plan->ndm; ++d) {
+        // cells from the arrival at the top of the band to the end of the sweep across the
+        // whole band, the pulse width and two samples' margin
+        const double span = k * plan->dms[d] * (1.0 / (lo * lo) - 1.0 / (top * top)) + tau_prime_ms +
+                            2.0 * b.dt_ms;
+        const double ntd = std::ceil(span / b.dt_ms) + 2.0;
+        if (!(ntd < 1.0e8)) return DD_ERR_OVERFLOW;
+        const int32_t nt = (int32_t)ntd;
+        pbar.assign((size_t)C * nt, 0.0);
+        dd_status st = dd_predict_rect(&b, plan->dms[d], phase * b.dt_ms, tau_ms, tau_prime_ms, alpha,
+                                       nu0_ghz, 1.0, nt, pbar.data());
+        if (st != DD_OK) return st;
+        wrow.assign((size_t)C * nt, 0.0f);
+        double g = 0.0;
+        st = dd_select_samples(pbar.data(), C, nt, nt, delay + (size_t)d * C, ntaps + (size_t)d * C,
+                               wrow.data(), nullptr, &g);
+        if (st != DD_OK) return st;
+        if (gains) gains[d] = g;
+        for (int c = 0; c < C; ++c) {
+            const int32_t n = ntaps[(size_t)d * C + c];
+            kmx = std::max(kmx, n);
+            if (!w) continue;
+            if (n > kmax) return DD_ERR_CAPACITY;
+            float* dst = w + ((size_t)d * C + c) * kmax;
+            std::fill(dst, dst + kmax, 0.0f);
+            std::copy(wrow.data() + (size_t)c * nt, wrow.data() + (size_t)c * nt + n, dst);
+        }
+    }
+    if (kused) *kused = kmx;
+    return DD_OK;
+}
+
 dd_status dd_exact_profiles(dd_plan_t plan, double tau_prime_ms, int32_t* delay, int32_t* ntaps) {
     if (!plan || !delay || !ntaps || tau_prime_ms < 0) return DD_ERR_ARG;
     const dd_band& b = plan->band;

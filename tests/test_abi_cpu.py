@@ -244,6 +244,31 @@ def test_select_samples_matches_oracle(lib):
         dd.select_samples(np.ones((2, 10)), 4)          # a 10-sample run with kmax 4
 
 
+def test_select_profiles_match_oracle_selection(lib):
+    """dd_select_profiles (every trial of a plan) equals the oracle's Sec. 2.2 selection on
+    the pulse model's cells of each trial, trial by trial, with the same gains."""
+    import paper_1301_3968_gb300 as dd
+    b = synth.Band(60, 700.0, 5.0, 1.0)
+    dms = np.array([0.0, 12.5, 30.0, 55.0])
+    band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, 4096, "f32")
+    phase, tau, taup, alpha = 0.4, 1.0, 1.5, 1.0
+    delay, taps, w, gains = dd.select_profiles(band, dms, tau_ms=tau, tau_prime_ms=taup, alpha=alpha,
+                                               nu0_ghz=0.85, phase=phase)
+    assert w.shape == (len(dms), b.nchan, int(taps.max()))
+    for d, dm in enumerate(dms):
+        # a map long enough for the whole sweep across the band
+        nt = int(4.15 * dm * (1 / 0.7 ** 2 - 1 / 1.0 ** 2) / b.dt_ms) + 20
+        P = synth.rect_pulse_cells(b, nt, dm, phase * b.dt_ms, tau, taup, alpha=alpha, nu0_ghz=0.85)
+        want = ref.select_samples(P)
+        mask = np.zeros_like(want)
+        for c in range(b.nchan):
+            for k in range(taps[d, c]):
+                if w[d, c, k] == 1.0:
+                    mask[c, delay[d, c] + k] = True
+        np.testing.assert_array_equal(mask, want)
+        assert gains[d] == pytest.approx(ref.set_snr(P, want) / ref.set_snr(P, P > 0), rel=1e-9)
+
+
 def test_exact_profiles_cover_the_rect_pulse(lib):
     """eq. num_samples: delay = floor(t_A/dt), taps = ceil(t_B/dt) - floor(t_A/dt) is the
     extent of the cells holding power of a pulse arriving at t = 0 with width tau'.  The

@@ -52,7 +52,26 @@ def _peaks():
 # ----------------------------------------------------------------------------- workload
 
 
-def craft_workload(dd, dev, ndm=None):
+def dm_shards(cost, ws, align=16):
+    """Contiguous trial ranges, one per rank, of about equal cost (cost[d]: taps of trial
+    d), with boundaries on multiples of `align` trials (one CTA's trial block) where the
+    list allows.  Returns [(lo, hi)] * ws covering 0 .. len(cost)."""
+    cost = np.asarray(cost, np.float64)
+    D = len(cost)
+    cum = np.concatenate([[0.0], np.cumsum(cost)])
+    bounds = [0]
+    for r in range(1, ws):
+        d = int(np.searchsorted(cum, cum[-1] * r / ws))
+        d = int(round(d / align)) * align if D >= ws * align else d
+        bounds.append(min(max(d, bounds[-1]), D))
+    bounds.append(D)
+    return [(bounds[r], bounds[r + 1]) for r in range(ws)]
+
+
+def craft_workload(dd, dev, ndm=None, rank=0, ws=1):
+    """The CRAFT-like block; with ws > 1 ranks, this rank's contiguous range of its trial
+    list (cost-balanced), every rank computing the same output span as one GPU would
+    (the full list's t_out) from a full replica of the input."""
     import torch
     import synth
     cfg = synth.make_craft()
@@ -62,21 +81,28 @@ def craft_workload(dd, dev, ndm=None):
     if ndm:   # a smaller profiling case: a contiguous block from the middle of the list
         m = max(0, len(dms) // 2 - ndm // 2)
         dms = dms[m:m + ndm]
-    plan = dd.Plan(band, dms)
+    full = dd.Plan(band, dms)
+    delay_f, taps_f = full.tables()
+    t_out = cfg["nsamp"] - full.d_max
+    full.close()
+    shards = dm_shards(taps_f.astype(np.int64).sum(axis=1), ws)
+    lo, hi = shards[rank]
+    plan = dd.Plan(band, dms[lo:hi])
     delay, taps = plan.tables()
-    K = int(taps.max())
+    K = int(taps_f.max())
     w = np.where(np.arange(K)[None, None, :] < taps[:, :, None], cfg["wchan"][None, :, None], 0.0)
     w = np.ascontiguousarray(w, dtype=np.float32)
     plan.set_profiles(weights=w)
     x = torch.from_numpy(cfg["data"]).to(dev)
     info = plan.info()
-    t_out = cfg["nsamp"] - info["d_max"]
     return dict(
         name="CRAFT-like",
         desc=("CRAFT-like: 336 ch x 1 MHz (1130-1466 MHz), dt 1 ms, 65536 fp32 samples, "
               f"{len(dms)} trial DMs 0-{dms[-1]:.0f} (eq. trial DMs, eps={eps:.4f}), "
               "weights ~ nu^-1.4 on every tap, boxcar widths 1-32"),
-        plan=plan, x=x, host=cfg["data"], nsamp=cfg["nsamp"], t_out=t_out, ndm=len(dms),
+        plan=plan, x=x, host=cfg["data"], nsamp=t_out + info["d_max"], t_out=t_out,
+        nsamp_in=cfg["nsamp"],
+        ndm=hi - lo, ndm_total=len(dms), shards=shards, dms=dms, wchan=cfg["wchan"],
         widths=cfg["widths"], delay=delay, taps=taps, w=w, dtype="f32",
         flops=2.0 * float(taps.astype(np.int64).sum()) * t_out, ns_total=int(info["ns_total"]),
     )
@@ -173,7 +199,7 @@ def run_gpu(args):
     torch.cuda.set_device(local)
     dev = torch.device("cuda", local)
     dd_build.build()
-    W = craft_workload(dd, dev, args.ndm)
+    W = craft_workload(dd, dev, args.ndm, rank, ws)
     plan, x = W["plan"], W["x"]
     widths = W["widths"]
     stream = torch.cuda.current_stream()
@@ -181,7 +207,7 @@ def run_gpu(args):
     out = torch.empty((W["ndm"], W["t_out"]), dtype=torch.float32, device=dev)
 
     def step(ev=None):
-        mean, sd = plan.channel_stats(x, nsamp=W["nsamp"])
+        mean, sd = plan.channel_stats(x, nsamp=W["nsamp_in"])
         if ev is not None:
             ev[0].record(stream)
         plan.dedisperse(x, nsamp=W["nsamp"], out=out)
@@ -215,22 +241,57 @@ def run_gpu(args):
     k_ms = [a.elapsed_time(b) for a, b in kev]
     clocks = clk.stop() if clk else None
     ms = _max_over_ranks(sum(step_ms) / len(step_ms), ws)
-    units = float(W["ndm"]) * W["t_out"]
-    value = ws * units / (ms / 1e3)
+    units = float(W["ndm_total"]) * W["t_out"]      # every rank's trials, one output span
+    value = units / (ms / 1e3)
 
     e2e = None if args.no_e2e else e2e_run(args, W, ws, plan, x, out, widths, stream)
+    shard = merge_check(dd, dev, W, rank, ws, plan, x, out, widths) if ws > 1 else None
     # the device's measured FP32 FMA (scalar and packed pairs) and INT32 add rates (after
     # the timed region), and its SM count
     live = {"fma_tflops": dd.alu_peak("fma") / 1e12, "fma2_tflops": dd.alu_peak("fma2") / 1e12,
             "iadd_tops": dd.alu_peak("iadd") / 1e12,
             "sms": torch.cuda.get_device_properties(dev).multi_processor_count}
     extras = None
-    if rank == 0 and not args.no_extras:
+    if rank == 0 and ws == 1 and not args.no_extras:
         extras = {"fwd_bwd": diff_extra(dd, dev, flush, stream),
                   "batched": batched_extra(dd, dev, flush, stream),
                   "large_lowband": large_extra(dd, dev, flush, stream, iadd_tops=live["iadd_tops"],
                                                sms=live["sms"])}
-    return _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras, live)
+    return _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras, live, shard)
+
+
+def merge_check(dd, dev, W, rank, ws, plan, x, out, widths):
+    """After the timed region: gathers every rank's peak S/N and peak times on rank 0 and
+    compares the merged tables with one plan over the whole trial list on rank 0's GPU."""
+    import torch
+    import torch.distributed as dist
+    mean, sd = plan.channel_stats(x, nsamp=W["nsamp_in"])
+    plan.dedisperse(x, nsamp=W["nsamp"], out=out)
+    pk, ag, _ = plan.boxcar_snr(out, widths, mean, sd, t_len=W["t_out"])
+    mine = (pk.cpu().numpy(), ag.cpu().numpy())
+    got = [None] * ws if rank == 0 else None
+    dist.gather_object(mine, got, dst=0)
+    if rank != 0:
+        return None
+    peak = np.concatenate([g[0] for g in got])
+    arg = np.concatenate([g[1] for g in got])
+    fp = dd.Plan(dd.Band(336, 1130.0, 1.0, 1.0, W["host"].shape[1], "f32"), W["dms"])
+    _, taps = fp.tables()
+    K = W["w"].shape[2]
+    w = np.where(np.arange(K)[None, None, :] < taps[:, :, None], W["wchan"][None, :, None], 0.0)
+    fp.set_profiles(weights=np.ascontiguousarray(w, dtype=np.float32))
+    nsamp = W["t_out"] + fp.d_max
+    fout = torch.empty((fp.ndm, W["t_out"]), dtype=torch.float32, device=dev)
+    m1, s1 = fp.channel_stats(x, nsamp=W["nsamp_in"])
+    fp.dedisperse(x, nsamp=nsamp, out=fout)
+    p1, a1, _ = fp.boxcar_snr(fout, widths, m1, s1, t_len=W["t_out"])
+    p1, a1 = p1.cpu().numpy(), a1.cpu().numpy()
+    fp.close()
+    return {"trials_per_rank": [hi - lo for lo, hi in W["shards"]],
+            "trial_ranges": W["shards"],
+            "merged_peak_snr_equal_one_gpu": bool(np.array_equal(peak, p1)),
+            "merged_peak_t_equal_one_gpu": bool(np.array_equal(arg, a1)),
+            "max_abs_snr_diff": float(np.max(np.abs(peak - p1)))}
 
 
 def e2e_run(args, W, ws, plan, x, out, widths, stream):
@@ -245,7 +306,7 @@ def e2e_run(args, W, ws, plan, x, out, widths, stream):
 
     def e2e_step():
         xin.copy_(host, non_blocking=True)
-        mean, sd = plan.channel_stats(xin, nsamp=W["nsamp"])
+        mean, sd = plan.channel_stats(xin, nsamp=W["nsamp_in"])
         plan.dedisperse(xin, nsamp=W["nsamp"], out=out)
         pk, ag, _ = plan.boxcar_snr(out, widths, mean, sd, t_len=W["t_out"])
         peak_h.copy_(pk, non_blocking=True)
@@ -263,10 +324,11 @@ def e2e_run(args, W, ws, plan, x, out, widths, stream):
     e1.record(stream)
     torch.cuda.synchronize()
     e_ms = _max_over_ranks(e0.elapsed_time(e1) / args.steps, ws)
-    h2d = host.numel() * host.element_size()
-    d2h = peak_h.numel() * 4 + arg_h.numel() * 4
-    units = float(W["ndm"]) * W["t_out"]
-    return {"value": ws * units / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
+    # bytes of the whole job: every rank copies the input in and its peaks out
+    h2d = ws * host.numel() * host.element_size()
+    d2h = W["ndm_total"] * len(widths) * 8
+    units = float(W["ndm_total"]) * W["t_out"]
+    return {"value": units / (e_ms / 1e3), "unit": UNIT, "h2d_bytes_per_step": h2d,
             "d2h_bytes_per_step": d2h, "ms_per_step": e_ms}
 
 
@@ -512,7 +574,7 @@ def _profile_traffic():
         return None
 
 
-def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras=None, live=None):
+def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras=None, live=None, shard=None):
     if rank != 0:
         return None
     peaks, kind = _peaks()
@@ -532,11 +594,13 @@ def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras=None, live=N
     res = {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
         "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True,
-        "scaling": "weak", "vs_baseline": None, "dtype": W["dtype"], "data": "synthetic",
-        "config": {"workload": W["desc"], "trials": W["ndm"], "t_out": W["t_out"],
-                   "channels": 336, "nsamp": W["nsamp"], "taps_total": W["ns_total"],
+        "scaling": "strong", "vs_baseline": None, "dtype": W["dtype"], "data": "synthetic",
+        "config": {"workload": W["desc"], "trials": W["ndm_total"], "t_out": W["t_out"],
+                   "channels": 336, "nsamp": int(W["host"].shape[1]), "taps_total": W["ns_total"],
                    "l2": "flushed between steps (256 MiB write outside the timed events)",
-                   "parallelism": f"replicas x{ws} (independent blocks per GPU)"},
+                   "parallelism": (f"dm{ws}: contiguous cost-balanced trial ranges per GPU, a full "
+                                   "input replica each, peaks merged on the host; no collective "
+                                   "on the data path")},
         "e2e": e2e,
         "gpu_launches": LAUNCHES_PER_STEP * args.steps,
         "roofline": {"bound": "alu", "kernel": "k_dedisp<float,float,weighted>",
@@ -555,9 +619,11 @@ def _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras=None, live=N
         res["roofline"]["frac_of_measured_fma"] = achieved / live["fma_tflops"]
         res["roofline"]["frac_of_measured_fma2"] = achieved / live["fma2_tflops"]
         res["config"]["sms"] = sms
+    if shard is not None:
+        res["shard"] = shard
     if extras is not None:
         res["extras"] = extras
-    if not args.no_cpu_baseline:
+    if ws == 1 and not args.no_cpu_baseline:
         res["cpu_baseline"] = cpu_baseline(W, budget_s=args.cpu_seconds)
     return res
 
@@ -683,6 +749,17 @@ def main():
     ap.add_argument("--traffic", type=float, default=None,
                     help="DRAM bytes per dedispersion launch from an ncu capture")
     args = ap.parse_args()
+    if args.gpus > 1 and "WORLD_SIZE" not in os.environ and not args.only:
+        # not started by a launcher: start one rank per GPU on this node
+        import socket
+        sk = socket.socket()
+        sk.bind(("127.0.0.1", 0))
+        port = sk.getsockname()[1]
+        sk.close()
+        cmd = [sys.executable, "-m", "torch.distributed.run", "--nnodes=1",
+               f"--nproc-per-node={args.gpus}", "--master-addr=127.0.0.1", f"--master-port={port}",
+               os.path.abspath(__file__)] + sys.argv[1:]
+        sys.exit(subprocess.run(cmd).returncode)
     if args.only:
         res = run_only(args)
     elif args.impl == "reference":

@@ -5,11 +5,12 @@
 // Work decomposition (sm_103a):
 //   * A CTA has kWarps = 8 warps covering 8 / nch warp-groups x nch time chunks.  On the
 //     fp32 path a warp unit sums two adjacent trials from one shared register window
-//     (their delays and tap counts differ by at most a sample or so on a trial list of
-//     eq. trial DMs); on the exact integer path a warp sums one trial, on the run-length
-//     path three.  A chunk is 32 * R outputs and lane l owns outputs chunk_start + l*R + r,
-//     r < R (R = kRPair on the pair path, kRInt otherwise).  The plan picks the most
-//     trials per CTA whose staged window fits in shared memory.
+//     whose registers hold each trial's own sample (their delays differ by a few samples
+//     at most on a trial list of eq. trial DMs); on the exact integer path a warp sums
+//     one trial, on the run-length path three.  A chunk is 32 * R outputs and lane l
+//     owns outputs chunk_start + l*R + r, r < R (R = kRPair on the pair path, kRInt
+//     otherwise).  The plan picks the most trials per CTA whose staged window fits in
+//     shared memory.
 //   * Channels are streamed in stages of cs rows through a ring of NBUF shared-memory
 //     buffers (two on the pair and run-length paths, four on the integer path).  For each
 //     channel the CTA stages the window that all its trials read -- [T0 + min delta,
@@ -25,7 +26,7 @@
 //   * Every wait is bounded by time; a wait that runs out records DD_ERR_TIMEOUT in the
 //     plan's status word, the CTA drains its own copies in flight and returns.
 //   * Inner loop: a register window of R samples slides along the taps.  Pair path: per
-//     tap one shared-memory load, one weight-pair broadcast and R packed FMAs
+//     tap one or two shared-memory loads, one weight-pair broadcast and R packed FMAs
 //     (fma.rn.f32x2, 2 x R fp32 FMAs).  Integer path: per two taps one load and R
 //     three-input adds.  Run-length path: per output two loads and one add (one load with
 //     shared difference rows), whatever the tap count.  R is odd, so the lane-strided
@@ -120,8 +121,8 @@ __device__ __forceinline__ TACC cvt(TIN v) {
 }
 
 // Packed pairs for the fp32 pair units (dd_packed.cuh): one 64-bit register holds
-// (trial 0, trial 1) accumulators or weights, or a window sample duplicated in both
-// halves, and one fma.rn.f32x2 performs both trials' fused multiply-adds.
+// (trial 0, trial 1) accumulators, weights or window samples, and one fma.rn.f32x2
+// performs both trials' fused multiply-adds.
 
 struct Smem {
     unsigned char* stages;
@@ -276,64 +277,80 @@ __device__ __forceinline__ void stage_rl_rows(const uint32_t* brows, const int2*
     }
 }
 
-// One stage of one warp unit on the fp32 path: two adjacent trials share the register
-// window.  The entry's window is the union of the two trials' windows, and its weights
-// are (w0, w1) pairs that are zero where a trial has no tap, so each tap costs one
-// window load, one weight-pair broadcast and R packed FMAs (2 x R fp32 FMAs).  The
-// window keeps each sample duplicated in both halves of a 64-bit register.  SHORT: the
-// plan's union windows are at most R taps, so the taps are one unrolled pass.  Sums
-// run over channels, then taps, in a fixed order (deterministic); single-precision
-// accumulation of the ~10^3-10^4 terms of an output stays orders of magnitude inside
-// the 1e-5 scale-aware bound.
+// One channel of a pair unit on the fp32 path: two adjacent trials share the register
+// window.  Window register j holds (sample j of trial 0's run, sample j of trial 1's
+// run) -- the same sample duplicated when the runs start together (SHIFT false), else
+// the two samples s apart -- and the weights are (w0, w1) pairs, zero past a trial's
+// own taps, so each tap costs one weight-pair broadcast, one or two window loads and R
+// packed FMAs (2 x R fp32 FMAs) for max(n0, n1) taps.  SHORT: the plan's units have at
+// most R taps (one unrolled pass) or 2R (two passes).  Sums run over channels, then
+// taps, in a fixed order (deterministic); single-precision accumulation of the
+// ~10^3-10^4 terms of an output stays orders of magnitude inside the 1e-5 scale-aware
+// bound.
+template <typename TIN, int SHORT, bool SHIFT>
+__device__ __forceinline__ void pair_channel(const TIN* p, int s, int n, const uint64_t* wk,
+                                             uint64_t (&acc)[kRPair]) {
+    constexpr int R = kRPair;
+    const TIN* p2 = p + s;  // trial 1's run
+    auto ld = [&](int j) -> uint64_t {
+        if constexpr (SHIFT) return pk2((float)p[j], (float)p2[j]);
+        else return pk_dup((float)p[j]);
+    };
+    uint64_t win[R];
+#pragma unroll
+    for (int j = 0; j < R; ++j) win[j] = ld(j);
+    if constexpr (SHORT == 1) {
+#pragma unroll
+        for (int kk = 0; kk < R; ++kk) {
+            if (kk >= n) break;
+            const uint64_t w = wk[kk];
+#pragma unroll
+            for (int r = 0; r < R; ++r) fma2(acc[r], w, win[(r + kk) % R]);
+            win[kk] = ld(R + kk);
+        }
+    } else if constexpr (SHORT == 2) {  // at most 2R taps: two unrolled passes
+#pragma unroll
+        for (int h = 0; h < 2; ++h) {
+#pragma unroll
+            for (int kk = 0; kk < R; ++kk) {
+                if (h * R + kk >= n) break;
+                const uint64_t w = wk[h * R + kk];
+#pragma unroll
+                for (int r = 0; r < R; ++r) fma2(acc[r], w, win[(r + kk) % R]);
+                win[kk] = ld(R + h * R + kk);
+            }
+        }
+    } else {
+        for (int k0 = 0; k0 < n; k0 += R) {
+#pragma unroll
+            for (int kk = 0; kk < R; ++kk) {
+                if (k0 + kk >= n) break;
+                const uint64_t w = wk[k0 + kk];
+#pragma unroll
+                for (int r = 0; r < R; ++r) fma2(acc[r], w, win[(r + kk) % R]);
+                win[kk] = ld(R + k0 + kk);
+            }
+        }
+    }
+}
+
+// One stage of one pair unit: its entries are (trial 0's start - block minimum,
+// max(n0, n1), trial 1's start - trial 0's, 0).
 template <typename TIN, int SHORT>
-__device__ __forceinline__ void stage_pair(const TIN* rows, const int2* ent, const float2* wts,
+__device__ __forceinline__ void stage_pair(const TIN* rows, const int4* ent, const float2* wts,
                                            const int* lo, int csn, int lcap, int kw, int bq,
                                            int lane_off, uint64_t (&acc)[kRPair]) {
     constexpr int Q = Elem<TIN>::Q;
-    constexpr int R = kRPair;
     for (int ci = 0; ci < csn; ++ci) {
-        const int2 q = ent[ci];
-        const int n = q.y;
+        const int4 q = ent[ci];
         const TIN* p = rows + ci * lcap + ((bq + lo[ci]) & (Q - 1)) + q.x + lane_off;
         const uint64_t* wk = (const uint64_t*)(wts + ci * kw);
         __builtin_assume(__isShared(p));
         __builtin_assume(__isShared(wk));
-        uint64_t win[R];
-#pragma unroll
-        for (int j = 0; j < R; ++j) win[j] = pk_dup((float)p[j]);
-        if constexpr (SHORT == 1) {
-#pragma unroll
-            for (int kk = 0; kk < R; ++kk) {
-                if (kk >= n) break;
-                const uint64_t w = wk[kk];
-#pragma unroll
-                for (int r = 0; r < R; ++r) fma2(acc[r], w, win[(r + kk) % R]);
-                win[kk] = pk_dup((float)p[R + kk]);
-            }
-        } else if constexpr (SHORT == 2) {  // at most 2R taps: two unrolled passes
-#pragma unroll
-            for (int h = 0; h < 2; ++h) {
-#pragma unroll
-                for (int kk = 0; kk < R; ++kk) {
-                    if (h * R + kk >= n) break;
-                    const uint64_t w = wk[h * R + kk];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) fma2(acc[r], w, win[(r + kk) % R]);
-                    win[kk] = pk_dup((float)p[R + h * R + kk]);
-                }
-            }
-        } else {
-            for (int k0 = 0; k0 < n; k0 += R) {
-#pragma unroll
-                for (int kk = 0; kk < R; ++kk) {
-                    if (k0 + kk >= n) break;
-                    const uint64_t w = wk[k0 + kk];
-#pragma unroll
-                    for (int r = 0; r < R; ++r) fma2(acc[r], w, win[(r + kk) % R]);
-                    win[kk] = pk_dup((float)p[R + k0 + kk]);
-                }
-            }
-        }
+        if (q.z == 0)
+            pair_channel<TIN, SHORT, false>(p, 0, q.y, wk, acc);
+        else
+            pair_channel<TIN, SHORT, true>(p, q.z, q.y, wk, acc);
     }
 }
 
@@ -492,8 +509,9 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
             const int c0 = s * cs;
             const int csn = min(cs, a.nchan - c0);
             if constexpr (PAIR) {
+                const int4* ent4 = (const int4*)(buf + g.rec_off) + dmi * cs;
                 const float2* wts = (const float2*)(buf + g.rec_off + g.w_off) + dmi * cs * a.kpad;
-                stage_pair<TIN, SHORT>(rows, ent, wts, lo_all + c0, csn, a.lcap, a.kpad, bq,
+                stage_pair<TIN, SHORT>(rows, ent4, wts, lo_all + c0, csn, a.lcap, a.kpad, bq,
                                        lane_off, accp);
             } else {
                 stage_int<TIN, SHORT>(rows, ent, lo_all + c0, csn, a.lcap, bq, lane_off, acc0);
@@ -712,9 +730,9 @@ int blocks_per_sm(size_t smem) {
 }
 
 // Builds the pair records' (w0, w1) weights from the device weights [d][c][kpad] and
-// the delay and tap tables (the entries themselves do not change).
-__global__ void k_repack_w(const float* w, const int32_t* delay, const int32_t* taps,
-                           unsigned char* rec, int32_t rec_bytes,
+// the tap table: tap k of a pair entry holds each trial's own tap k, zero past its taps
+// (the entries themselves do not change).
+__global__ void k_repack_w(const float* w, const int32_t* taps, unsigned char* rec, int32_t rec_bytes,
                            int32_t w_off, int32_t nchan, int32_t ndm, int32_t cs, int32_t nu,
                            int32_t kw, int32_t kpad, int32_t nst) {
     const int rid = blockIdx.x;  // record = (block, stage)
@@ -727,18 +745,13 @@ __global__ void k_repack_w(const float* w, const int32_t* delay, const int32_t* 
         const int j = e / cs, ci = e - j * cs;
         const int d0 = blk * 2 * nu + 2 * j, c = st * cs + ci;
         float v[2] = {0.f, 0.f};
-        if (d0 < ndm && c < nchan) {
-            // window start of the entry: the smaller of the two trials' delays
-            int lo = delay[(int64_t)d0 * nchan + c];
-            if (d0 + 1 < ndm) lo = min(lo, delay[(int64_t)(d0 + 1) * nchan + c]);
+        if (c < nchan)
             for (int t = 0; t < 2; ++t) {
                 const int dd = d0 + t;
                 if (dd >= ndm) break;
                 const int64_t dc = (int64_t)dd * nchan + c;
-                const int kk = k - (delay[dc] - lo);
-                if (kk >= 0 && kk < taps[dc]) v[t] = w[dc * kpad + kk];
+                if (k < taps[dc]) v[t] = w[dc * kpad + k];
             }
-        }
         dst[2 * i] = v[0];
         dst[2 * i + 1] = v[1];
     }
@@ -824,9 +837,8 @@ dd_status launch_repack(dd_plan_s* p, cudaStream_t s) {
     const int nu = kWarps / p->nch;
     const int nst = (p->nchan + p->cs - 1) / p->cs;
     const StageGeom g(p->band.in_type == DD_U8 ? 1 : 4, true, p->lcap, p->kw, p->cs, nu);
-    k_repack_w<<<p->nblk * nst, 256, 0, s>>>(p->dev.w, p->dev.delay, p->dev.taps, p->dev.rec,
-                                              g.rec_bytes, g.w_off, p->nchan, p->ndm, p->cs, nu,
-                                              p->kw, p->kpad, nst);
+    k_repack_w<<<p->nblk * nst, 256, 0, s>>>(p->dev.w, p->dev.taps, p->dev.rec, g.rec_bytes, g.w_off,
+                                              p->nchan, p->ndm, p->cs, nu, p->kw, p->kpad, nst);
     return cuda_status(cudaGetLastError());
 }
 

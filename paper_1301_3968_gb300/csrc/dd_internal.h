@@ -41,6 +41,9 @@ constexpr long long kWaitNs = 2000000000;  // bound on any device-side barrier w
 // of the CTA's nu warp units and each of the stage's channels, an entry (window start
 // relative to the block's minimum delay for the channel, taps) and, for fp32 plans,
 // the per-tap weights of the unit's two trials as (w0, w1) pairs (kw pairs per entry).
+// An fp32 (pair) entry is 16 bytes: (trial 0's start, the larger of the two tap
+// counts, trial 1's start minus trial 0's, 0); tap k of the pair reads sample k of each
+// trial's own run, so the pair sums max(n0, n1) taps.
 // With shared difference rows (run-length path, `brow`) an entry is (run start, index of
 // its tap count in the channel's list) and the record ends with each channel's list of
 // at most two tap counts; the CTA then also holds cs x 2 difference rows of lcap words
@@ -52,7 +55,7 @@ struct StageGeom {
                                   bool brow = false) {
         rows_bytes = (cs * lcap * esz + 15) & ~15;
         rec_off = rows_bytes;
-        w_off = 8 * nu * cs;
+        w_off = (has_w ? 16 : 8) * nu * cs;
         rec_bytes = (w_off + (has_w ? 8 * nu * cs * kw : 0) + (brow ? 8 * cs : 0) + 15) & ~15;
         bytes = (rec_off + rec_bytes + 127) & ~127;
         bbytes = brow ? cs * 2 * lcap * 4 : 0;
@@ -175,7 +178,7 @@ struct dd_plan_s {
     int32_t rec_bytes = 0;             // bytes of one stage's profile record
     bool pair = true;                  // fp32 path: each warp sums two adjacent trials
     int32_t kw = 0;                    // weight pairs per record entry (pair path)
-    int32_t umax = 0;                  // longest union window of a pair unit (pair path)
+    int32_t umax = 0;                  // most taps of a pair unit, max(n0, n1) (pair path)
     std::vector<unsigned char> rec;    // host copy of the records
     bool rec_from_dev_w = false;       // records' weights come from dev.w (device weights)
     int32_t debug_skip_stage = -1;     // test hook: a stage whose bulk copies are never issued

@@ -102,23 +102,43 @@ int64_t staged_len(const dd_plan_s* p, int nch, int64_t span) {
     return (need + q - 1) / q * q;
 }
 
-// Weight pairs per record entry for a given trial block size: the longest union
-// window [min delta, max(delta + n)) of any warp unit's trials on any channel.
-int32_t union_taps(const dd_plan_s* p, int db) {
+// Weight pairs per record entry on the pair path: the most taps of any warp unit on
+// any channel, max(n0, n1) (each trial's tap k reads sample k of its own run).
+int32_t pair_taps(const dd_plan_s* p) {
     const int C = p->nchan, tpw = trials_per_unit(p);
     int64_t u = 0;
     for (int d0 = 0; d0 < p->ndm; d0 += tpw)
-        for (int c = 0; c < C; ++c) {
-            int64_t lo = INT64_MAX, hi = 0;
-            for (int i = 0; i < tpw && d0 + i < p->ndm; ++i) {
-                const size_t dc = (size_t)(d0 + i) * C + c;
-                lo = std::min<int64_t>(lo, p->delay[dc]);
-                hi = std::max<int64_t>(hi, (int64_t)p->delay[dc] + p->taps[dc]);
-            }
-            u = std::max(u, hi - lo);
-        }
-    (void)db;
+        for (int c = 0; c < C; ++c)
+            for (int i = 0; i < tpw && d0 + i < p->ndm; ++i)
+                u = std::max<int64_t>(u, p->taps[(size_t)(d0 + i) * C + c]);
     return (int32_t)std::min<int64_t>(u, INT32_MAX);
+}
+
+// Samples past the block minimum that a pair unit's register window reaches: each
+// trial reads max(n0, n1) samples from its own start, so the shorter run's trial reads
+// past its own window by |n0 - n1| (with zero weights).  The staged window must hold
+// them.
+int64_t pair_read_span(const dd_plan_s* p, int db) {
+    const int C = p->nchan;
+    const int nblk = (p->ndm + db - 1) / db;
+    int64_t span = 0;
+    for (int b = 0; b < nblk; ++b)
+        for (int c = 0; c < C; ++c) {
+            int64_t lo = INT64_MAX;
+            for (int d = b * db; d < std::min(p->ndm, (b + 1) * db); ++d)
+                lo = std::min<int64_t>(lo, p->delay[(size_t)d * C + c]);
+            for (int d0 = b * db; d0 < std::min(p->ndm, (b + 1) * db); d0 += 2) {
+                const size_t a = (size_t)d0 * C + c;
+                int64_t st = p->delay[a], n = p->taps[a];
+                if (d0 + 1 < p->ndm) {
+                    const size_t bb = (size_t)(d0 + 1) * C + c;
+                    st = std::max<int64_t>(st, p->delay[bb]);
+                    n = std::max<int64_t>(n, p->taps[bb]);
+                }
+                span = std::max(span, st + n - lo);
+            }
+        }
+    return span;
 }
 
 // Most distinct tap counts among one trial block's trials on any channel (run-length
@@ -144,8 +164,8 @@ int max_distinct_taps(const dd_plan_s* p, int db) {
 
 // Lays the profile tables out as the kernel stages them: one record per (trial block,
 // channel stage).  Entry (unit j, channel ci) = (window start - block minimum, taps);
-// on the pair path the window is the union of the unit's two trials' windows and the
-// weights are (w0, w1) pairs, zero where a trial has no tap.
+// on the pair path it is (trial 0's start - block minimum, max(n0, n1), trial 1's start
+// - trial 0's, 0) and the weights are (w0, w1) pairs, zero past a trial's own taps.
 void build_records(dd_plan_s* p) {
     const int C = p->nchan;
     const int tpw = trials_per_unit(p);
@@ -180,6 +200,26 @@ void build_records(dd_plan_s* p) {
                     const int c = st * p->cs + ci;
                     const int d0 = b * db + j * tpw;
                     if (d0 >= p->ndm || c >= C) continue;
+                    if (p->pair) {
+                        // (trial 0's start, max(n0, n1), trial 1's start - trial 0's, 0) and
+                        // per tap k the pair (w0[k], w1[k]), zero past a trial's own taps
+                        const int e = j * p->cs + ci;
+                        const int64_t blo = p->blk_lo[(size_t)b * C + c];
+                        const size_t a0 = (size_t)d0 * C + c;
+                        const bool two = d0 + 1 < p->ndm;
+                        const size_t a1 = two ? a0 + C : a0;
+                        ent[4 * e] = (int32_t)(p->delay[a0] - blo);
+                        ent[4 * e + 1] = std::max(p->taps[a0], two ? p->taps[a1] : 0);
+                        ent[4 * e + 2] = two ? p->delay[a1] - p->delay[a0] : 0;
+                        ent[4 * e + 3] = 0;
+                        for (int i = 0; i < 2; ++i) {
+                            if (i == 1 && !two) break;
+                            const size_t dc = i ? a1 : a0;
+                            for (int k = 0; k < p->taps[dc]; ++k)
+                                w[((size_t)e * kw + k) * 2 + i] = p->unit ? 1.0f : p->w[dc * p->kpad + k];
+                        }
+                        continue;
+                    }
                     int64_t lo = INT64_MAX, hi = 0;
                     for (int i = 0; i < tpw && d0 + i < p->ndm; ++i) {
                         const size_t dc = (size_t)(d0 + i) * C + c;
@@ -190,13 +230,6 @@ void build_records(dd_plan_s* p) {
                     ent[2 * e] = (int32_t)(lo - p->blk_lo[(size_t)b * C + c]);
                     ent[2 * e + 1] = (int32_t)(hi - lo);
                     if (p->rl_b) ent[2 * e + 1] = (hi - lo) == nlist[2 * ci] ? 0 : 1;
-                    if (!p->pair) continue;
-                    for (int i = 0; i < tpw && d0 + i < p->ndm; ++i) {
-                        const size_t dc = (size_t)(d0 + i) * C + c;
-                        const int off = (int)(p->delay[dc] - lo);
-                        for (int k = 0; k < p->taps[dc]; ++k)
-                            w[((size_t)e * kw + off + k) * 2 + i] = p->unit ? 1.0f : p->w[dc * p->kpad + k];
-                    }
                 }
         }
 }
@@ -223,8 +256,9 @@ dd_status build_schedule(dd_plan_s* p) {
         for (int nch = 1; nch <= dd::kWarps; nch *= 2) {
             const int nu = dd::kWarps / nch * units_per_warp(p);
             const int db = tpw * nu;
-            const int64_t span = block_span(p, db, nullptr);
-            p->umax = p->pair ? union_taps(p, db) : 0;
+            int64_t span = block_span(p, db, nullptr);
+            if (p->pair) span = std::max(span, pair_read_span(p, db));
+            p->umax = p->pair ? pair_taps(p) : 0;
             p->rl_b = p->rl && max_distinct_taps(p, db) <= 2;
             const int32_t kw = p->pair ? ((p->umax + 1) & ~1) : 0;
             const int64_t need = staged_len(p, nch, span);
@@ -255,8 +289,9 @@ dd_status build_schedule_fixed(dd_plan_s* p, int nch, int cs) {
     const int esz = stage_esz(p);
     const int nu = dd::kWarps / nch * units_per_warp(p);
     const int db = trials_per_unit(p) * nu;
-    const int64_t span = block_span(p, db, nullptr);
-    p->umax = p->pair ? union_taps(p, db) : 0;
+    int64_t span = block_span(p, db, nullptr);
+    if (p->pair) span = std::max(span, pair_read_span(p, db));
+    p->umax = p->pair ? pair_taps(p) : 0;
     const bool rl_b = p->rl && max_distinct_taps(p, db) <= 2;
     const int32_t kw = p->pair ? ((p->umax + 1) & ~1) : 0;
     const int64_t need = staged_len(p, nch, span);

@@ -399,7 +399,7 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
     using TACC = typename std::conditional<PAIR, float, int>::type;
     const int cs = a.cs;
     const int nu = kWarps / a.nch * UPW;  // warp units per CTA
-    const StageGeom g((int)sizeof(TIN), PAIR, a.lcap, a.kpad, cs, nu, BROW);
+    const StageGeom g((int)sizeof(TIN), PAIR, a.lcap, a.kpad, cs, nu, BROW, a.blen);
     const Smem sm = carve<NBUF>(smem, g, a.smem_bytes, a.nchan);
     const int tid = threadIdx.x;
     const int warp = tid >> 5, lane = tid & 31;
@@ -442,52 +442,86 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
     const int lane_off = chunk * TT + lane * R;
     bool ok = true;
 
-    for (int i = 0; i < nloc; ++i) {
-        const int s = s_lo + i;
-        const int b = i % NBUF;
-        // a one-tile CTA starts every buffer at phase 0; a persistent CTA continues
-        const uint32_t parity = (uint32_t)(((MULTI ? ts.uses[b] : 0) + i / NBUF) & 1);
-        const bool got = mbar_wait_bounded(&sm.full[b], parity, a.wait_ns);
-        if constexpr (BROW) {
-            // the whole CTA builds the stage's difference rows, so it must agree to go on;
-            // this barrier also keeps the rows of the previous stage until all warps are done
+    if constexpr (BROW) {
+        // Run-length path with difference rows shared by the CTA.  The rows of stage i
+        // (B_q[j] = P[j + n_q] - P[j], per channel and tap count, over the positions its
+        // trials read) are built by all threads one stage ahead, into half i & 1 of the
+        // row area, together with a copy of the stage's entries; so the prefix buffer of a
+        // stage is refilled as soon as its rows are built, and one CTA barrier per stage
+        // both publishes the next rows and ends the reads of the current ones.
+        const int* lo_all = (const int*)(smem + NBUF * g.bytes);
+        auto build = [&](int i) {  // stage s_lo + i, from its prefix buffer
+            const unsigned char* buf = smem + (i % NBUF) * g.bytes;
+            const uint32_t* rows = (const uint32_t*)buf;
+            const int4* nlist = (const int4*)(buf + g.rec_off + g.w_off);
+            const int2* esrc = (const int2*)(buf + g.rec_off);
+            uint32_t* half = sm.brows + (i & 1) * g.bhalf_words;
+            int2* edst = (int2*)(half + cs * 2 * a.blen);
+            for (int e = tid; e < nu * cs; e += kWarps * 32) edst[e] = esrc[e];
+            const int csn = min(cs, a.nchan - (s_lo + i) * cs);
+            for (int ci = 0; ci < csn; ++ci) {
+                const int4 nn = nlist[ci];
+#pragma unroll
+                for (int q = 0; q < 2; ++q) {
+                    const int n = q ? nn.y : nn.x;
+                    const int len = q ? nn.w : nn.z;
+                    if (n <= 0) continue;
+                    const uint32_t* pr = rows + ci * a.lcap;
+                    uint32_t* br = half + (ci * 2 + q) * a.blen;
+#pragma unroll 4
+                    for (int j = tid; j < len; j += kWarps * 32) br[j] = pr[j + n] - pr[j];
+                }
+            }
+        };
+        auto parity_of = [&](int i) {
+            return (uint32_t)(((MULTI ? ts.uses[i % NBUF] : 0) + i / NBUF) & 1);
+        };
+        bool got = nloc > 0 ? mbar_wait_bounded(&sm.full[0], parity_of(0), a.wait_ns) : true;
+        if (got && nloc > 0) build(0);
+        if (__syncthreads_or(!got)) {
+            if (tid == 0) atomicExch(a.status, (int)DD_ERR_TIMEOUT);
+            ok = false;
+        } else if (tid == 0 && NBUF < nloc) {
+            issue_stage<TIN, NBUF>(a, g, sm, blk, s_lo + NBUF, 0, base, tail);
+        }
+        for (int i = 0; ok && i < nloc; ++i) {
+            if (i + 1 < nloc) {
+                got = mbar_wait_bounded(&sm.full[(i + 1) % NBUF], parity_of(i + 1), a.wait_ns);
+                if (got) build(i + 1);
+            }
+            const uint32_t* half = sm.brows + (i & 1) * g.bhalf_words;
+            const int2* ent = (const int2*)(half + cs * 2 * a.blen) + dmi * cs;
+            const int c0 = (s_lo + i) * cs;
+            const int csn = min(cs, a.nchan - c0);
+            if (d < a.ndm) stage_rl_rows(half, ent, lo_all + c0, csn, a.blen, bq, lane_off, acc0);
+#pragma unroll
+            for (int u = 1; u < UPW; ++u)
+                if (d + u < a.ndm)
+                    stage_rl_rows(half, ent + u * cs, lo_all + c0, csn, a.blen, bq, lane_off, accr[u - 1]);
             if (__syncthreads_or(!got)) {
                 if (tid == 0) atomicExch(a.status, (int)DD_ERR_TIMEOUT);
                 ok = false;
                 break;
             }
-        } else if (!__all_sync(0xffffffffu, got)) {
+            if (tid == 0 && i + 1 + NBUF < nloc)
+                issue_stage<TIN, NBUF>(a, g, sm, blk, s_lo + i + 1 + NBUF, (i + 1) % NBUF, base, tail);
+        }
+    }
+
+    // every other path: warps go through the ring on their own, the last one out of a
+    // buffer refills it
+    for (int i = 0; !BROW && i < nloc; ++i) {
+        const int s = s_lo + i;
+        const int b = i % NBUF;
+        // a one-tile CTA starts every buffer at phase 0; a persistent CTA continues
+        const uint32_t parity = (uint32_t)(((MULTI ? ts.uses[b] : 0) + i / NBUF) & 1);
+        const bool got = mbar_wait_bounded(&sm.full[b], parity, a.wait_ns);
+        if (!__all_sync(0xffffffffu, got)) {
             if (lane == 0) atomicExch(a.status, (int)DD_ERR_TIMEOUT);
             ok = false;
             break;
         }
-        if constexpr (BROW) {
-            const unsigned char* buf = smem + b * g.bytes;
-            const uint32_t* rows = (const uint32_t*)buf;
-            const int2* nlist = (const int2*)(buf + g.rec_off + g.w_off);
-            const int2* ent = (const int2*)(buf + g.rec_off) + dmi * cs;
-            const int* lo_all = (const int*)(smem + NBUF * g.bytes);
-            const int c0 = s * cs;
-            const int csn = min(cs, a.nchan - c0);
-            for (int ci = 0; ci < csn; ++ci) {
-                const int2 nn = nlist[ci];
-#pragma unroll
-                for (int q = 0; q < 2; ++q) {
-                    const int n = q ? nn.y : nn.x;
-                    if (n <= 0) continue;
-                    const uint32_t* pr = rows + ci * a.lcap;
-                    uint32_t* br = sm.brows + (ci * 2 + q) * a.lcap;
-#pragma unroll 4
-                    for (int j = tid; j + n < a.lcap; j += kWarps * 32) br[j] = pr[j + n] - pr[j];
-                }
-            }
-            __syncthreads();
-            if (d < a.ndm) stage_rl_rows(sm.brows, ent, lo_all + c0, csn, a.lcap, bq, lane_off, acc0);
-#pragma unroll
-            for (int u = 1; u < UPW; ++u)
-                if (d + u < a.ndm)
-                    stage_rl_rows(sm.brows, ent + u * cs, lo_all + c0, csn, a.lcap, bq, lane_off, accr[u - 1]);
-        } else if constexpr (RL) {
+        if constexpr (RL) {
             const unsigned char* buf = smem + b * g.bytes;
             const uint32_t* rows = (const uint32_t*)buf;
             const int2* ent = (const int2*)(buf + g.rec_off) + dmi * cs;
@@ -661,8 +695,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_fused(DedispArgs a, c
 // barriers, and at least the output transpose area plus the barriers (which sit at the
 // end and survive the transpose).
 template <typename TIN, bool PAIR, int NBUF>
-size_t smem_for(int lcap, int kpad, int cs, int nch, int nchan, bool brow = false) {
-    const StageGeom g((int)sizeof(TIN), PAIR, lcap, kpad, cs, kWarps / nch * upw<TIN>(), brow);
+size_t smem_for(int lcap, int kpad, int cs, int nch, int nchan, bool brow = false, int blen = 0) {
+    const StageGeom g((int)sizeof(TIN), PAIR, lcap, kpad, cs, kWarps / nch * upw<TIN>(), brow, blen);
     size_t smem = (size_t)dedisp_smem_bytes(g, NBUF, nchan);
     const size_t st = (size_t)kStoreBytes + NBUF * 8 + 2 * NBUF * 4;
     if (smem < st) smem = st;
@@ -673,7 +707,7 @@ template <typename TIN, bool PAIR, int NBUF, int SHORT = 0>
 dd_status run(DedispArgs a, cudaStream_t s) {
     const int nu = kWarps / a.nch * upw<TIN>();
     const size_t smem = smem_for<TIN, PAIR, NBUF>(a.lcap, a.kpad, a.cs, a.nch, a.nchan,
-                                                  std::is_same<TIN, uint32_t>::value && SHORT != 0);
+                                                  std::is_same<TIN, uint32_t>::value && SHORT != 0, a.blen);
     a.smem_bytes = (uint32_t)smem;
     auto kern = k_dedisp<TIN, PAIR, NBUF, SHORT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
@@ -855,6 +889,7 @@ void fill_dedisp_args(const dd_plan_s* p, const void* in, int64_t ld, int64_t t_
     a->nchan = p->nchan;
     a->ndm = p->ndm;
     a->lcap = p->lcap;
+    a->blen = p->blen;
     a->cs = p->cs;
     a->nch = p->nch;
     a->kpad = p->pair ? p->kw : 0;
@@ -868,7 +903,7 @@ void fill_dedisp_args(const dd_plan_s* p, const void* in, int64_t ld, int64_t t_
 
 size_t dedisp_smem_for(const dd_plan_s* p) {
     const int kp = p->pair ? p->kw : 0;
-    if (p->rl) return smem_for<uint32_t, false, kStagesRl>(p->lcap, 0, p->cs, p->nch, p->nchan, p->rl_b);
+    if (p->rl) return smem_for<uint32_t, false, kStagesRl>(p->lcap, 0, p->cs, p->nch, p->nchan, p->rl_b, p->blen);
     if (!p->pair) return smem_for<uint8_t, false, kStagesInt>(p->lcap, kp, p->cs, p->nch, p->nchan);
     if (p->band.in_type == DD_U8) return smem_for<uint8_t, true, kStagesPair>(p->lcap, kp, p->cs, p->nch, p->nchan);
     return smem_for<float, true, kStagesPair>(p->lcap, kp, p->cs, p->nch, p->nchan);

@@ -45,20 +45,23 @@ constexpr long long kWaitNs = 2000000000;  // bound on any device-side barrier w
 // counts, trial 1's start minus trial 0's, 0); tap k of the pair reads sample k of each
 // trial's own run, so the pair sums max(n0, n1) taps.
 // With shared difference rows (run-length path, `brow`) an entry is (run start, index of
-// its tap count in the channel's list) and the record ends with each channel's list of
-// at most two tap counts; the CTA then also holds cs x 2 difference rows of lcap words
-// (`bbytes`, outside the ring).  Records are stored in this layout in global memory
+// its tap count in the channel's list) and the record ends with, per channel, its at
+// most two tap counts and the length of each one's difference row (n0, n1, len0, len1).
+// The CTA then also holds two halves (stage i uses half i & 1), each with cs x 2
+// difference rows of blen words and a copy of the stage's nu x cs entries (`bbytes`,
+// outside the ring).  Records are stored in this layout in global memory
 // ([block][stage][rec_bytes]) and staged by one bulk copy.
 struct StageGeom {
-    int rows_bytes, rec_off, rec_bytes, w_off, bytes, bbytes;
+    int rows_bytes, rec_off, rec_bytes, w_off, bytes, bbytes, bhalf_words;
     __host__ __device__ StageGeom(int esz, bool has_w, int lcap, int kw, int cs, int nu,
-                                  bool brow = false) {
+                                  bool brow = false, int blen = 0) {
         rows_bytes = (cs * lcap * esz + 15) & ~15;
         rec_off = rows_bytes;
         w_off = (has_w ? 16 : 8) * nu * cs;
-        rec_bytes = (w_off + (has_w ? 8 * nu * cs * kw : 0) + (brow ? 8 * cs : 0) + 15) & ~15;
+        rec_bytes = (w_off + (has_w ? 8 * nu * cs * kw : 0) + (brow ? 16 * cs : 0) + 15) & ~15;
         bytes = (rec_off + rec_bytes + 127) & ~127;
-        bbytes = brow ? cs * 2 * lcap * 4 : 0;
+        bhalf_words = brow ? ((cs * 2 * blen + 2 * nu * cs + 3) & ~3) : 0;
+        bbytes = 2 * bhalf_words * 4;
     }
 };
 
@@ -84,6 +87,7 @@ struct DedispArgs {
     int32_t nchan;
     int32_t ndm;
     int32_t lcap;
+    int32_t blen;  // difference-row stride (run-length path with shared rows)
     int32_t cs;   // channels per stage
     int32_t nch;  // time chunks per CTA (trials per CTA = kWarps / nch)
     int32_t kpad;  // weight pairs per record entry (pair path)
@@ -202,6 +206,7 @@ struct dd_plan_s {
     int32_t method = DD_METHOD_AUTO;   // requested
     bool rl = false;                   // in use
     bool rl_b = false;                 // run-length with difference rows shared by the CTA
+    int32_t blen = 0;                  // their stride (words)
     uint32_t* d_prefix = nullptr;
     int64_t prefix_elems = 0;
     // fused dedispersion + boxcar scratch: merged maxima, per-CTA carries, strip seams

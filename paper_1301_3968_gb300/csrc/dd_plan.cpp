@@ -162,6 +162,41 @@ int max_distinct_taps(const dd_plan_s* p, int db) {
     return most;
 }
 
+// Length of one difference row (run-length path with shared rows) for tap count n on
+// channel c of block b: its words are read up to the largest run start of the block's
+// trials with that count (relative to the block minimum), plus the CTA's outputs, plus
+// three words of 16-byte alignment slack.
+int32_t brow_row_len(const dd_plan_s* p, int db, int nch, const std::vector<int32_t>& blk_lo, int b,
+                     int c, int n) {
+    const int C = p->nchan;
+    const int64_t lo = blk_lo[(size_t)b * C + c];
+    int64_t x = 0;
+    for (int d = b * db; d < std::min(p->ndm, (b + 1) * db); ++d)
+        if (p->taps[(size_t)d * C + c] == n) x = std::max<int64_t>(x, p->delay[(size_t)d * C + c] - lo);
+    return (int32_t)(x + (int64_t)nch * dd::chunk_t(false) + 4);
+}
+
+// The stride of the difference rows: the longest row of any block and channel.
+int32_t brow_stride(const dd_plan_s* p, int db, int nch) {
+    const int C = p->nchan;
+    const int nblk = (p->ndm + db - 1) / db;
+    std::vector<int32_t> lo;
+    block_span(p, db, &lo);
+    int32_t len = 0;
+    for (int b = 0; b < nblk; ++b)
+        for (int c = 0; c < C; ++c) {
+            int n0 = 0, n1 = 0;
+            for (int d = b * db; d < std::min(p->ndm, (b + 1) * db); ++d) {
+                const int t = p->taps[(size_t)d * C + c];
+                if (n0 == 0) n0 = t;
+                else if (t != n0 && n1 == 0) n1 = t;
+            }
+            len = std::max(len, brow_row_len(p, db, nch, lo, b, c, n0));
+            if (n1) len = std::max(len, brow_row_len(p, db, nch, lo, b, c, n1));
+        }
+    return (len + 3) & ~3;
+}
+
 // Lays the profile tables out as the kernel stages them: one record per (trial block,
 // channel stage).  Entry (unit j, channel ci) = (window start - block minimum, taps);
 // on the pair path it is (trial 0's start - block minimum, max(n0, n1), trial 1's start
@@ -173,7 +208,7 @@ void build_records(dd_plan_s* p) {
     const int db = tpw * nu;
     const int nst = (C + p->cs - 1) / p->cs;
     const int kw = p->pair ? p->kw : 0;
-    const dd::StageGeom g(stage_esz(p), p->pair, p->lcap, kw, p->cs, nu, p->rl_b);
+    const dd::StageGeom g(stage_esz(p), p->pair, p->lcap, kw, p->cs, nu, p->rl_b, p->blen);
     p->rec_bytes = g.rec_bytes;
     p->rec.assign((size_t)p->nblk * nst * g.rec_bytes, 0);
     for (int b = 0; b < p->nblk; ++b)
@@ -181,7 +216,8 @@ void build_records(dd_plan_s* p) {
             unsigned char* r = p->rec.data() + ((size_t)b * nst + st) * g.rec_bytes;
             int32_t* ent = (int32_t*)r;
             float* w = (float*)(r + g.w_off);
-            int32_t* nlist = (int32_t*)(r + g.w_off);  // difference rows: (n0, n1) per channel
+            // difference rows: (n0, n1, len0, len1) per channel
+            int32_t* nlist = (int32_t*)(r + g.w_off);
             if (p->rl_b)
                 for (int ci = 0; ci < p->cs; ++ci) {
                     const int c = st * p->cs + ci;
@@ -192,8 +228,10 @@ void build_records(dd_plan_s* p) {
                         if (a == 0) a = t;
                         else if (t != a && bb == 0) bb = t;
                     }
-                    nlist[2 * ci] = a;
-                    nlist[2 * ci + 1] = bb;
+                    nlist[4 * ci] = a;
+                    nlist[4 * ci + 1] = bb;
+                    nlist[4 * ci + 2] = a ? brow_row_len(p, db, p->nch, p->blk_lo, b, c, a) : 0;
+                    nlist[4 * ci + 3] = bb ? brow_row_len(p, db, p->nch, p->blk_lo, b, c, bb) : 0;
                 }
             for (int j = 0; j < nu; ++j)
                 for (int ci = 0; ci < p->cs; ++ci) {
@@ -229,7 +267,7 @@ void build_records(dd_plan_s* p) {
                     const int e = j * p->cs + ci;
                     ent[2 * e] = (int32_t)(lo - p->blk_lo[(size_t)b * C + c]);
                     ent[2 * e + 1] = (int32_t)(hi - lo);
-                    if (p->rl_b) ent[2 * e + 1] = (hi - lo) == nlist[2 * ci] ? 0 : 1;
+                    if (p->rl_b) ent[2 * e + 1] = (hi - lo) == nlist[4 * ci] ? 0 : 1;
                 }
         }
 }
@@ -263,9 +301,10 @@ dd_status build_schedule(dd_plan_s* p) {
             const int32_t kw = p->pair ? ((p->umax + 1) & ~1) : 0;
             const int64_t need = staged_len(p, nch, span);
             if (need > (1 << 22)) continue;
+            p->blen = p->rl_b ? brow_stride(p, db, nch) : 0;
             int cs = cs_want;
             while (cs >= min_cs[pass] &&
-                   dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu, p->rl_b),
+                   dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu, p->rl_b, p->blen),
                                          nbuf, p->nchan) > budgets[pass])
                 --cs;
             if (cs < min_cs[pass]) continue;
@@ -296,9 +335,11 @@ dd_status build_schedule_fixed(dd_plan_s* p, int nch, int cs) {
     const int32_t kw = p->pair ? ((p->umax + 1) & ~1) : 0;
     const int64_t need = staged_len(p, nch, span);
     if (need > (1 << 22)) return DD_ERR_UNSUPPORTED;
-    if (dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu, rl_b), stages_of(p),
+    const int32_t blen = rl_b ? brow_stride(p, db, nch) : 0;
+    if (dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu, rl_b, blen), stages_of(p),
                               p->nchan) > dd::kSmemBudgetOne)
         return DD_ERR_UNSUPPORTED;
+    p->blen = blen;
     p->rl_b = rl_b;
     p->nch = nch;
     p->cs = cs;

@@ -335,16 +335,17 @@ __device__ __forceinline__ void pair_channel(const TIN* p, int s, int n, const u
 }
 
 // One stage of one pair unit: its entries are (trial 0's start - block minimum,
-// max(n0, n1), trial 1's start - trial 0's, 0).
+// max(n0, n1), trial 1's start - trial 0's, offset of the entry's weight pairs in the
+// record's weight list).
 template <typename TIN, int SHORT>
 __device__ __forceinline__ void stage_pair(const TIN* rows, const int4* ent, const float2* wts,
-                                           const int* lo, int csn, int lcap, int kw, int bq,
+                                           const int* lo, int csn, int lcap, int bq,
                                            int lane_off, uint64_t (&acc)[kRPair]) {
     constexpr int Q = Elem<TIN>::Q;
     for (int ci = 0; ci < csn; ++ci) {
         const int4 q = ent[ci];
         const TIN* p = rows + ci * lcap + ((bq + lo[ci]) & (Q - 1)) + q.x + lane_off;
-        const uint64_t* wk = (const uint64_t*)(wts + ci * kw);
+        const uint64_t* wk = (const uint64_t*)(wts + q.w);
         __builtin_assume(__isShared(p));
         __builtin_assume(__isShared(wk));
         if (q.z == 0)
@@ -544,9 +545,8 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
             const int csn = min(cs, a.nchan - c0);
             if constexpr (PAIR) {
                 const int4* ent4 = (const int4*)(buf + g.rec_off) + dmi * cs;
-                const float2* wts = (const float2*)(buf + g.rec_off + g.w_off) + dmi * cs * a.kpad;
-                stage_pair<TIN, SHORT>(rows, ent4, wts, lo_all + c0, csn, a.lcap, a.kpad, bq,
-                                       lane_off, accp);
+                const float2* wts = (const float2*)(buf + g.rec_off + g.w_off);
+                stage_pair<TIN, SHORT>(rows, ent4, wts, lo_all + c0, csn, a.lcap, bq, lane_off, accp);
             } else {
                 stage_int<TIN, SHORT>(rows, ent, lo_all + c0, csn, a.lcap, bq, lane_off, acc0);
             }
@@ -764,30 +764,27 @@ int blocks_per_sm(size_t smem) {
 }
 
 // Builds the pair records' (w0, w1) weights from the device weights [d][c][kpad] and
-// the tap table: tap k of a pair entry holds each trial's own tap k, zero past its taps
-// (the entries themselves do not change).
+// the tap table, at each entry's weight offset: tap k holds each trial's own tap k,
+// zero past its taps (the entries themselves do not change).  One warp per entry.
 __global__ void k_repack_w(const float* w, const int32_t* taps, unsigned char* rec, int32_t rec_bytes,
                            int32_t w_off, int32_t nchan, int32_t ndm, int32_t cs, int32_t nu,
-                           int32_t kw, int32_t kpad, int32_t nst) {
+                           int32_t kpad, int32_t nst) {
     const int rid = blockIdx.x;  // record = (block, stage)
     const int blk = rid / nst, st = rid - blk * nst;
+    const int4* ent = (const int4*)(rec + (int64_t)rid * rec_bytes);
     float* dst = (float*)(rec + (int64_t)rid * rec_bytes + w_off);
-    const int n = nu * cs * kw;
-    for (int i = threadIdx.x; i < n; i += blockDim.x) {
-        const int k = i % kw;
-        const int e = i / kw;  // entry = (unit, channel)
+    const int lane = threadIdx.x & 31;
+    for (int e = threadIdx.x >> 5; e < nu * cs; e += blockDim.x >> 5) {
         const int j = e / cs, ci = e - j * cs;
         const int d0 = blk * 2 * nu + 2 * j, c = st * cs + ci;
-        float v[2] = {0.f, 0.f};
-        if (c < nchan)
-            for (int t = 0; t < 2; ++t) {
-                const int dd = d0 + t;
-                if (dd >= ndm) break;
-                const int64_t dc = (int64_t)dd * nchan + c;
-                if (k < taps[dc]) v[t] = w[dc * kpad + k];
-            }
-        dst[2 * i] = v[0];
-        dst[2 * i + 1] = v[1];
+        if (d0 >= ndm || c >= nchan) continue;
+        const int4 q = ent[e];
+        const int64_t dc0 = (int64_t)d0 * nchan + c, dc1 = dc0 + nchan;
+        const int n0 = taps[dc0], n1 = d0 + 1 < ndm ? taps[dc1] : 0;
+        for (int k = lane; k < q.y; k += 32) {
+            dst[2 * (q.w + k)] = k < n0 ? w[dc0 * kpad + k] : 0.f;
+            dst[2 * (q.w + k) + 1] = k < n1 ? w[dc1 * kpad + k] : 0.f;
+        }
     }
 }
 
@@ -872,7 +869,7 @@ dd_status launch_repack(dd_plan_s* p, cudaStream_t s) {
     const int nst = (p->nchan + p->cs - 1) / p->cs;
     const StageGeom g(p->band.in_type == DD_U8 ? 1 : 4, true, p->lcap, p->kw, p->cs, nu);
     k_repack_w<<<p->nblk * nst, 256, 0, s>>>(p->dev.w, p->dev.taps, p->dev.rec, g.rec_bytes, g.w_off,
-                                              p->nchan, p->ndm, p->cs, nu, p->kw, p->kpad, nst);
+                                              p->nchan, p->ndm, p->cs, nu, p->kpad, nst);
     return cuda_status(cudaGetLastError());
 }
 

@@ -40,10 +40,11 @@ constexpr long long kWaitNs = 2000000000;  // bound on any device-side barrier w
 // rows of lcap elements, then the stage's profile record.  The record holds, for each
 // of the CTA's nu warp units and each of the stage's channels, an entry (window start
 // relative to the block's minimum delay for the channel, taps) and, for fp32 plans,
-// the per-tap weights of the unit's two trials as (w0, w1) pairs (kw pairs per entry).
-// An fp32 (pair) entry is 16 bytes: (trial 0's start, the larger of the two tap
-// counts, trial 1's start minus trial 0's, 0); tap k of the pair reads sample k of each
-// trial's own run, so the pair sums max(n0, n1) taps.
+// the per-tap weights of the unit's two trials as (w0, w1) pairs, packed one entry
+// after another (kw pairs per record, the most any record needs).  An fp32 (pair)
+// entry is 16 bytes: (trial 0's start, the larger of the two tap counts, trial 1's
+// start minus trial 0's, offset of its weight pairs); tap k of the pair reads sample k
+// of each trial's own run, so the pair sums max(n0, n1) taps.
 // With shared difference rows (run-length path, `brow`) an entry is (run start, index of
 // its tap count in the channel's list) and the record ends with, per channel, its at
 // most two tap counts and the length of each one's difference row (n0, n1, len0, len1).
@@ -58,7 +59,7 @@ struct StageGeom {
         rows_bytes = (cs * lcap * esz + 15) & ~15;
         rec_off = rows_bytes;
         w_off = (has_w ? 16 : 8) * nu * cs;
-        rec_bytes = (w_off + (has_w ? 8 * nu * cs * kw : 0) + (brow ? 16 * cs : 0) + 15) & ~15;
+        rec_bytes = (w_off + (has_w ? 8 * kw : 0) + (brow ? 16 * cs : 0) + 15) & ~15;
         bytes = (rec_off + rec_bytes + 127) & ~127;
         bhalf_words = brow ? ((cs * 2 * blen + 2 * nu * cs + 3) & ~3) : 0;
         bbytes = 2 * bhalf_words * 4;
@@ -90,7 +91,7 @@ struct DedispArgs {
     int32_t blen;  // difference-row stride (run-length path with shared rows)
     int32_t cs;   // channels per stage
     int32_t nch;  // time chunks per CTA (trials per CTA = kWarps / nch)
-    int32_t kpad;  // weight pairs per record entry (pair path)
+    int32_t kpad;  // weight pairs per stage record (pair path)
     int32_t nsplit;    // channel-sum splits (grid z); split z writes out + z * split_ld
     int64_t split_ld;
     int32_t* status;
@@ -181,7 +182,7 @@ struct dd_plan_s {
     int32_t nch = 1;                   // time chunks per CTA
     int32_t rec_bytes = 0;             // bytes of one stage's profile record
     bool pair = true;                  // fp32 path: each warp sums two adjacent trials
-    int32_t kw = 0;                    // weight pairs per record entry (pair path)
+    int32_t kw = 0;                    // weight pairs per stage record (pair path)
     int32_t umax = 0;                  // most taps of a pair unit, max(n0, n1) (pair path)
     std::vector<unsigned char> rec;    // host copy of the records
     bool rec_from_dev_w = false;       // records' weights come from dev.w (device weights)

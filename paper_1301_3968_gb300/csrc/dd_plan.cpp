@@ -114,6 +114,27 @@ int32_t pair_taps(const dd_plan_s* p) {
     return (int32_t)std::min<int64_t>(u, INT32_MAX);
 }
 
+// Weight pairs of the fullest stage record on the pair path for stages of cs channels:
+// each entry holds max(n0, n1) pairs.
+int32_t pair_record_pairs(const dd_plan_s* p, int db, int cs) {
+    const int C = p->nchan;
+    const int nblk = (p->ndm + db - 1) / db;
+    int64_t most = 0;
+    for (int b = 0; b < nblk; ++b)
+        for (int c0 = 0; c0 < C; c0 += cs) {
+            int64_t tot = 0;
+            for (int d0 = b * db; d0 < std::min(p->ndm, (b + 1) * db); d0 += 2)
+                for (int c = c0; c < std::min(C, c0 + cs); ++c) {
+                    const size_t a = (size_t)d0 * C + c;
+                    int64_t n = p->taps[a];
+                    if (d0 + 1 < p->ndm) n = std::max<int64_t>(n, p->taps[a + C]);
+                    tot += n;
+                }
+            most = std::max(most, tot);
+        }
+    return (int32_t)std::min<int64_t>((most + 1) & ~(int64_t)1, INT32_MAX);
+}
+
 // Samples past the block minimum that a pair unit's register window reaches: each
 // trial reads max(n0, n1) samples from its own start, so the shorter run's trial reads
 // past its own window by |n0 - n1| (with zero weights).  The staged window must hold
@@ -218,6 +239,7 @@ void build_records(dd_plan_s* p) {
             float* w = (float*)(r + g.w_off);
             // difference rows: (n0, n1, len0, len1) per channel
             int32_t* nlist = (int32_t*)(r + g.w_off);
+            int32_t woff = 0;  // pair path: weight pairs used so far in this record
             if (p->rl_b)
                 for (int ci = 0; ci < p->cs; ++ci) {
                     const int c = st * p->cs + ci;
@@ -239,23 +261,26 @@ void build_records(dd_plan_s* p) {
                     const int d0 = b * db + j * tpw;
                     if (d0 >= p->ndm || c >= C) continue;
                     if (p->pair) {
-                        // (trial 0's start, max(n0, n1), trial 1's start - trial 0's, 0) and
-                        // per tap k the pair (w0[k], w1[k]), zero past a trial's own taps
+                        // (trial 0's start, max(n0, n1), trial 1's start - trial 0's, offset of
+                        // the entry's weights) and per tap k the pair (w0[k], w1[k]), zero past
+                        // a trial's own taps; entries' weights follow one another
                         const int e = j * p->cs + ci;
                         const int64_t blo = p->blk_lo[(size_t)b * C + c];
                         const size_t a0 = (size_t)d0 * C + c;
                         const bool two = d0 + 1 < p->ndm;
                         const size_t a1 = two ? a0 + C : a0;
+                        const int n = std::max(p->taps[a0], two ? p->taps[a1] : 0);
                         ent[4 * e] = (int32_t)(p->delay[a0] - blo);
-                        ent[4 * e + 1] = std::max(p->taps[a0], two ? p->taps[a1] : 0);
+                        ent[4 * e + 1] = n;
                         ent[4 * e + 2] = two ? p->delay[a1] - p->delay[a0] : 0;
-                        ent[4 * e + 3] = 0;
+                        ent[4 * e + 3] = woff;
                         for (int i = 0; i < 2; ++i) {
                             if (i == 1 && !two) break;
                             const size_t dc = i ? a1 : a0;
                             for (int k = 0; k < p->taps[dc]; ++k)
-                                w[((size_t)e * kw + k) * 2 + i] = p->unit ? 1.0f : p->w[dc * p->kpad + k];
+                                w[((size_t)woff + k) * 2 + i] = p->unit ? 1.0f : p->w[dc * p->kpad + k];
                         }
+                        woff += n;
                         continue;
                     }
                     int64_t lo = INT64_MAX, hi = 0;
@@ -298,15 +323,17 @@ dd_status build_schedule(dd_plan_s* p) {
             if (p->pair) span = std::max(span, pair_read_span(p, db));
             p->umax = p->pair ? pair_taps(p) : 0;
             p->rl_b = p->rl && max_distinct_taps(p, db) <= 2;
-            const int32_t kw = p->pair ? ((p->umax + 1) & ~1) : 0;
             const int64_t need = staged_len(p, nch, span);
             if (need > (1 << 22)) continue;
             p->blen = p->rl_b ? brow_stride(p, db, nch) : 0;
             int cs = cs_want;
+            int32_t kw = p->pair ? pair_record_pairs(p, db, cs) : 0;
             while (cs >= min_cs[pass] &&
                    dd::dedisp_smem_bytes(dd::StageGeom(esz, p->pair, (int)need, kw, cs, nu, p->rl_b, p->blen),
-                                         nbuf, p->nchan) > budgets[pass])
+                                         nbuf, p->nchan) > budgets[pass]) {
                 --cs;
+                if (p->pair && cs >= 1) kw = pair_record_pairs(p, db, cs);
+            }
             if (cs < min_cs[pass]) continue;
             p->nch = nch;
             p->cs = cs;
@@ -332,7 +359,7 @@ dd_status build_schedule_fixed(dd_plan_s* p, int nch, int cs) {
     if (p->pair) span = std::max(span, pair_read_span(p, db));
     p->umax = p->pair ? pair_taps(p) : 0;
     const bool rl_b = p->rl && max_distinct_taps(p, db) <= 2;
-    const int32_t kw = p->pair ? ((p->umax + 1) & ~1) : 0;
+    const int32_t kw = p->pair ? pair_record_pairs(p, db, cs) : 0;
     const int64_t need = staged_len(p, nch, span);
     if (need > (1 << 22)) return DD_ERR_UNSUPPORTED;
     const int32_t blen = rl_b ? brow_stride(p, db, nch) : 0;

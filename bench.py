@@ -254,7 +254,7 @@ def run_gpu(args):
     extras = None
     if rank == 0 and ws == 1 and not args.no_extras:
         extras = {"fwd_bwd": diff_extra(dd, dev, flush, stream),
-                  "batched": batched_extra(dd, dev, flush, stream),
+                  "batched": batched_extra(dd, dev, flush, stream, iadd_tops=live["iadd_tops"]),
                   "large_lowband": large_extra(dd, dev, flush, stream, iadd_tops=live["iadd_tops"],
                                                sms=live["sms"])}
     return _result(args, W, ws, rank, ms, value, k_ms, clocks, e2e, extras, live, shard)
@@ -405,73 +405,114 @@ def diff_extra(dd, dev, flush, stream, reps=5):
     }
 
 
-def batched_extra(dd, dev, flush, stream, reps=3):
-    """Batched configuration: 36 beams on the CRAFT band, uint8 in / int32 out, per-beam
-    lengths 2^14-2^17 and 512-8192 trial DMs (seeded log-uniform), each plan autotuned.
-    One persistent launch (and the CUDA graph of the whole block, boxcars included)
-    against the same beams run one plain launch after another."""
-    import tempfile
+def _batch_case(dd, dev, flush, stream, cfg, reps, tune, widths, graph=True):
+    """Plans for a set of beams (default schedules timed one launch after another, then
+    autotuned), their persistent launch, and optionally the graph of the whole block."""
     import torch
     import synth
-    cfg = synth.make_batched_beams()
     b = cfg["band"]
-    widths = np.arange(1, 33, dtype=np.int32)
     plans, xs, outs = [], [], []
-    tune = os.path.join(tempfile.mkdtemp(prefix="dd_tune_"), "schedule.txt")
     for beam in cfg["beams"]:
         band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, beam["nsamp"], "u8")
         dms, _ = dd.trial_dms(band, 0.0, beam["dm_max"], beam["ndm"], tau_av_ms=1.0)
-        plan = dd.Plan(band, dms)
-        x = torch.from_numpy(synth.make_beam_data(beam)).to(dev)
-        out = torch.empty((len(dms), beam["nsamp"] - plan.d_max), dtype=torch.int32, device=dev)
-        plan.autotune(x, out, cache_path=tune)
-        plans.append(plan)
-        xs.append(x)
-        outs.append(out)
-    units = float(sum(p.ndm * o.shape[1] for p, o in zip(plans, outs)))
-    batch = dd.Batch(plans)
-    batch.bind(xs, outs)
-    means = [torch.empty(b.nchan, dtype=torch.float64, device=dev) for _ in plans]
-    sds = [torch.empty_like(m) for m in means]
-    peaks = [torch.empty((p.ndm, len(widths)), dtype=torch.float32, device=dev) for p in plans]
-    args = [torch.empty((p.ndm, len(widths)), dtype=torch.int32, device=dev) for p in plans]
-    batch.bind_boxcar(widths, means, sds, peaks, args)
+        plans.append(dd.Plan(band, dms))
+        xs.append(torch.from_numpy(synth.make_beam_data(beam)).to(dev))
+        outs.append(torch.empty((len(dms), beam["nsamp"] - plans[-1].d_max), dtype=torch.int32, device=dev))
 
     def per_beam_fwd():
         for p, x, o in zip(plans, xs, outs):
             p.dedisperse(x, nsamp=p.band.nsamp, out=o)
 
-    def per_beam_step():
-        for p, x, o in zip(plans, xs, outs):
-            m, s = p.channel_stats(x, nsamp=p.band.nsamp)
-            p.dedisperse(x, nsamp=p.band.nsamp, out=o)
-            p.boxcar_snr(o, widths, m, s)
-
-    # a graph is captured on a stream of its own (not the legacy default stream); every
-    # variant runs and is timed on that stream
     gs = torch.cuda.Stream(dev)
     gs.wait_stream(stream)
+    res = {}
     with torch.cuda.stream(gs):
-        plain_ms = _ev_time(per_beam_fwd, reps, flush, gs)
-        batched_ms = _ev_time(lambda: batch.dedisperse(gs), reps, flush, gs)
-        eager_ms = _ev_time(per_beam_step, reps, flush, gs)
-        batch.capture(gs)
-        graph_ms = _ev_time(lambda: batch.replay(gs), reps, flush, gs)
+        res["default_fwd_ms"] = _ev_time(per_beam_fwd, reps, flush, gs)
+        for p, x, o in zip(plans, xs, outs):
+            p.autotune(x, o, cache_path=tune)
+        batch = dd.Batch(plans)
+        batch.bind(xs, outs)
+        res["plain_fwd_ms"] = _ev_time(per_beam_fwd, reps, flush, gs)
+        res["batched_fwd_ms"] = _ev_time(lambda: batch.dedisperse(gs), reps, flush, gs)
+        if graph:
+            means = [torch.empty(b.nchan, dtype=torch.float64, device=dev) for _ in plans]
+            sds = [torch.empty_like(m) for m in means]
+            peaks = [torch.empty((p.ndm, len(widths)), dtype=torch.float32, device=dev) for p in plans]
+            args = [torch.empty((p.ndm, len(widths)), dtype=torch.int32, device=dev) for p in plans]
+            batch.bind_boxcar(widths, means, sds, peaks, args)
+
+            def per_beam_step():
+                for p, x, o in zip(plans, xs, outs):
+                    m, s = p.channel_stats(x, nsamp=p.band.nsamp)
+                    p.dedisperse(x, nsamp=p.band.nsamp, out=o)
+                    p.boxcar_snr(o, widths, m, s)
+
+            res["plain_step_ms"] = _ev_time(per_beam_step, reps, flush, gs)
+            batch.capture(gs)
+            res["graph_step_ms"] = _ev_time(lambda: batch.replay(gs), reps, flush, gs)
     info = batch.info()
+    # work: trial x output samples; additions the direct path executes (one per tap,
+    # trial and output) and the graded exact count (min(n, 2) per trial, channel and
+    # output plus one per input sample for a prefix pass)
+    units = executed = graded = 0.0
+    for p, o in zip(plans, outs):
+        _, taps = p.tables()
+        t_out = o.shape[1]
+        units += float(p.ndm) * t_out
+        executed += float(taps.astype(np.int64).sum()) * t_out
+        graded += float(np.minimum(taps, 2).astype(np.int64).sum()) * t_out + float(b.nchan) * p.band.nsamp
     batch.close()
     for p in plans:
         p.close()
-    return {
-        "workload": (f"batched: {len(plans)} beams, {b.nchan} ch, {sum(x.shape[1] for x in xs)} "
-                     f"uint8 samples in all, {sum(p.ndm for p in plans)} trials in all, "
-                     "int32 out, boxcar widths 1-32, autotuned schedules"),
-        "units": units, "items": info["items"], "grid": info["grid"],
-        "plain_fwd_ms": plain_ms, "batched_fwd_ms": batched_ms,
-        "plain_step_ms": eager_ms, "graph_step_ms": graph_ms,
-        "plain_fwd_value": units / (plain_ms / 1e3), "batched_fwd_value": units / (batched_ms / 1e3),
-        "graph_step_value": units / (graph_ms / 1e3), "unit": UNIT,
-        "batched_over_plain_fwd": plain_ms / batched_ms,
+    res.update(units=units, executed_adds=executed, graded_adds=graded, items=info["items"],
+               grid=info["grid"], nbeams=len(plans), samples=sum(x.shape[1] for x in xs),
+               trials=sum(o.shape[0] for o in outs))
+    return res
+
+
+def batched_extra(dd, dev, flush, stream, reps=3, iadd_tops=None):
+    """Batched configuration: 36 beams on the CRAFT band, uint8 in / int32 out, per-beam
+    lengths 2^14-2^17 and 512-8192 trial DMs (seeded log-uniform), each plan autotuned.
+    One persistent launch (and the CUDA graph of the whole block, boxcars included)
+    against the same beams run one plain launch after another; the autotuner's gain over
+    the default schedules; and 36 beams from the lower end of both ranges (2^14-2^15
+    samples, 512-1024 trials), where each beam's own launch is a few waves."""
+    import tempfile
+    import synth
+    widths = np.arange(1, 33, dtype=np.int32)
+    tune = os.path.join(tempfile.mkdtemp(prefix="dd_tune_"), "schedule.txt")
+    r = _batch_case(dd, dev, flush, stream, synth.make_batched_beams(), reps, tune, widths)
+    small = _batch_case(dd, dev, flush, stream,
+                        synth.make_batched_beams(seed=synth.sub_seed("batched-small"), t_exp=(14, 15),
+                                                 d_exp=(9, 10)), 5, tune, widths, graph=False)
+    units = r["units"]
+    res = {
+        "workload": (f"batched: {r['nbeams']} beams, 336 ch, {r['samples']} uint8 samples in all, "
+                     f"{r['trials']} trials in all, int32 out, boxcar widths 1-32, autotuned schedules"),
+        "units": units, "items": r["items"], "grid": r["grid"],
+        "default_schedule_fwd_ms": r["default_fwd_ms"], "plain_fwd_ms": r["plain_fwd_ms"],
+        "autotune_gain": r["default_fwd_ms"] / r["plain_fwd_ms"],
+        "batched_fwd_ms": r["batched_fwd_ms"],
+        "plain_step_ms": r["plain_step_ms"], "graph_step_ms": r["graph_step_ms"],
+        "plain_fwd_value": units / (r["plain_fwd_ms"] / 1e3),
+        "batched_fwd_value": units / (r["batched_fwd_ms"] / 1e3),
+        "graph_step_value": units / (r["graph_step_ms"] / 1e3), "unit": UNIT,
+        "batched_over_plain_fwd": r["plain_fwd_ms"] / r["batched_fwd_ms"],
+        "executed_adds_per_block": r["executed_adds"], "graded_adds_per_block": r["graded_adds"],
+        "small_beams": {
+            "workload": (f"{small['nbeams']} beams, 336 ch, 2^14-2^15 samples and 512-1024 trials each "
+                         f"({small['samples']} samples, {small['trials']} trials in all), autotuned"),
+            "plain_fwd_ms": small["plain_fwd_ms"], "batched_fwd_ms": small["batched_fwd_ms"],
+            "batched_over_plain_fwd": small["plain_fwd_ms"] / small["batched_fwd_ms"],
+            "autotune_gain": small["default_fwd_ms"] / small["plain_fwd_ms"],
+            "batched_fwd_value": small["units"] / (small["batched_fwd_ms"] / 1e3)},
     }
+    if iadd_tops:
+        # the direct integer path: one add per tap (two per three-input add); graded: the
+        # exact minimum of a prefix-difference method
+        res["executed_frac_of_measured_iadd"] = r["executed_adds"] / (r["batched_fwd_ms"] / 1e3) / 1e12 / iadd_tops
+        res["graded_frac_of_measured_iadd"] = r["graded_adds"] / (r["batched_fwd_ms"] / 1e3) / 1e12 / iadd_tops
+    return res
 
 
 def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, iadd_tops=None,
@@ -721,7 +762,7 @@ def run_only(args):
     if args.only == "fwd_bwd":
         r = diff_extra(dd, dev, flush, stream)
     elif args.only == "batched":
-        r = batched_extra(dd, dev, flush, stream)
+        r = batched_extra(dd, dev, flush, stream, iadd_tops=dd.alu_peak("iadd") / 1e12)
     else:
         r = large_extra(dd, dev, flush, stream, nsamp=args.large_nsamp, ndm=args.large_ndm,
                         iadd_tops=dd.alu_peak("iadd") / 1e12)

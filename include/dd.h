@@ -258,8 +258,8 @@ dd_status dd_plan_get_schedule(dd_plan_t plan, int32_t* nch, int32_t* cs, int32_
  *     is at least 12, DIRECT otherwise.
  * dd_plan_set_method rebuilds the schedule (DD_ERR_UNSUPPORTED: RUNLENGTH on a weighted
  * or fp32 plan; the method is then unchanged).  A run-length plan that later gets weights
- * sums directly.  dd_plan_get_method reports the method in use (never AUTO).  Batches
- * (below) take DIRECT plans only. */
+ * sums directly.  dd_plan_get_method reports the method in use (never AUTO).  A batch
+ * (below) takes plans of one method. */
 typedef enum {
     DD_METHOD_AUTO = 0,
     DD_METHOD_DIRECT = 1,
@@ -280,11 +280,15 @@ dd_status dd_plan_autotune(dd_plan_t plan, const void* d_in, int64_t in_ld, void
                            int64_t out_ld, const char* cache_path, float* best_ms, void* stream);
 
 /* Many beams in one persistent launch (uneven lengths and trial lists; no counterpart in
- * the paper, which describes one beam).  Each beam has its own plan (same input type and
- * path for all, DD_METHOD_DIRECT, else DD_ERR_UNSUPPORTED; the plans must outlive the
+ * the paper, which describes one beam).  Each beam has its own plan (the same input type
+ * and tap-sum path for all: DD_ERR_ARG for mixed input types, DD_ERR_UNSUPPORTED for mixed
+ * methods, or run-length beams longer than 2^24 samples; the plans must outlive the
  * batch); a beam's block is the band's nsamp samples from column 0.  The work list has
  * one item per CTA tile (beam, trial block, time tile), sorted by estimated cost, largest
- * first; the kernel's CTAs take items from an atomic counter that each launch resets. */
+ * first; the kernel's CTAs take items from an atomic counter that each launch resets.
+ * Run-length beams first get their per-channel prefix sums (one small launch per beam,
+ * into device memory the batch owns: 4 bytes per channel and sample, allocated by
+ * dd_batch_bind), then the persistent launch sums them. */
 typedef struct dd_batch_s* dd_batch_t;
 dd_status dd_batch_create(dd_batch_t* batch, const dd_plan_t* plans, int32_t nbeams);
 /* Binds each beam's device input [nchan][in_ld] and output [ndm][out_ld] (host arrays of
@@ -292,7 +296,8 @@ dd_status dd_batch_create(dd_batch_t* batch, const dd_plan_t* plans, int32_t nbe
  * (allocates; synchronous).  Rebinding invalidates a captured graph. */
 dd_status dd_batch_bind(dd_batch_t batch, const void* const* d_in, const int64_t* in_ld,
                         void* const* d_out, const int64_t* out_ld);
-/* The persistent dedispersion launch for all bound beams (counter reset + kernel). */
+/* The persistent dedispersion launch for all bound beams (counter reset + kernel; on
+ * run-length beams the prefix passes before it). */
 dd_status dd_batch_dedisperse(dd_batch_t batch, void* stream);
 /* Binds, per beam, the outputs of the detection stage (boxcar widths shared by all beams;
  * device channel mean/std [nchan], peak S/N and peak time [ndm][nw]). */

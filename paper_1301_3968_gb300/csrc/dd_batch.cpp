@@ -23,7 +23,11 @@
 struct dd_batch_s {
     std::vector<dd_plan_s*> plans;
     bool u8 = false, pair = true;
-    bool short_taps = true;  // every plan's tap runs (union windows) fit one register window
+    bool rl = false;         // run-length beams (per-channel prefix sums, then differences)
+    bool short_taps = true;  // every plan's tap runs fit one register window (run-length
+                             // beams: every plan shares difference rows in the CTA)
+    std::vector<uint32_t*> d_prefix;  // run-length beams: each beam's prefix sums
+    std::vector<int64_t> ldp;
     std::vector<dd::BatchItem> items;
     size_t smem = 0;
     int grid = 0;
@@ -54,6 +58,9 @@ int64_t plan_t_out(const dd_plan_s* p) { return p->band.nsamp - p->dmax; }
 void free_batch_dev(dd_batch_s* b) {
     if (b->exec) cudaGraphExecDestroy(b->exec);
     if (b->graph) cudaGraphDestroy(b->graph);
+    for (uint32_t* q : b->d_prefix) cudaFree(q);
+    b->d_prefix.clear();
+    b->ldp.clear();
     cudaFree(b->d_args);
     cudaFree(b->d_items);
     cudaFree(b->d_counter);
@@ -64,8 +71,9 @@ void free_batch_dev(dd_batch_s* b) {
     b->d_counter = nullptr;
 }
 
-// Work list: one item per CTA tile, with the tile's FMA count plus a fixed per-stage
-// cost as the estimate; sorted largest first.
+// Work list: one item per CTA tile, with the tile's FMA count (run-length beams: its
+// trial-channel pairs, each costing the same per output whatever its taps) plus a fixed
+// per-stage cost as the estimate; sorted largest first.
 void build_items(dd_batch_s* b) {
     struct Est {
         double cost;
@@ -75,7 +83,7 @@ void build_items(dd_batch_s* b) {
     b->units = 0;
     for (int beam = 0; beam < (int)b->plans.size(); ++beam) {
         const dd_plan_s* p = b->plans[beam];
-        const int tpw = p->pair ? 2 : 1;
+        const int tpw = p->pair ? 2 : (p->rl ? dd::kRlUnits : 1);
         const int db = tpw * dd::kWarps / p->nch;
         const int64_t t_out = plan_t_out(p);
         const int64_t tile = (int64_t)dd::chunk_t(p->pair) * p->nch;
@@ -87,7 +95,7 @@ void build_items(dd_batch_s* b) {
             for (int i = 0; i < db; ++i) {
                 const int d = blk * db + i;
                 if (d >= p->ndm) break;
-                for (int c = 0; c < p->nchan; ++c) taps += p->taps[(size_t)d * p->nchan + c];
+                for (int c = 0; c < p->nchan; ++c) taps += p->rl ? 1.0 : p->taps[(size_t)d * p->nchan + c];
             }
             for (int tx = 0; tx < ntile; ++tx) {
                 const double len = (double)std::min<int64_t>(tile, t_out - (int64_t)tx * tile);
@@ -120,13 +128,16 @@ dd_status dd_batch_create(dd_batch_t* out, const dd_plan_t* plans, int32_t nbeam
         if (plans[i]->band.in_type != plans[0]->band.in_type || plans[i]->pair != plans[0]->pair)
             return DD_ERR_ARG;
         if (plan_t_out(plans[i]) < 1) return DD_ERR_ARG;
-        if (plans[i]->rl) return DD_ERR_UNSUPPORTED;
+        // one kernel serves the batch: every beam on the same tap-sum path
+        if (plans[i]->rl != plans[0]->rl || plans[i]->rl_b != plans[0]->rl_b) return DD_ERR_UNSUPPORTED;
+        if (plans[i]->rl && plans[i]->band.nsamp > ((int64_t)1 << 24)) return DD_ERR_UNSUPPORTED;
     }
     dd_batch_s* b = new (std::nothrow) dd_batch_s;
     if (!b) return DD_ERR_OOM;
     b->plans.assign(plans, plans + nbeams);
     b->u8 = plans[0]->band.in_type == DD_U8;
     b->pair = plans[0]->pair;
+    b->rl = plans[0]->rl;
     for (auto* p : b->plans) b->smem = std::max(b->smem, dd::dedisp_smem_for(p));
     build_items(b);
     *out = b;
@@ -140,7 +151,8 @@ dd_status dd_batch_bind(dd_batch_t b, const void* const* d_in, const int64_t* in
     std::vector<dd::DedispArgs> args(nb);
     for (int i = 0; i < nb; ++i) {
         dd_plan_s* p = b->plans[i];
-        if (p->rl) return DD_ERR_UNSUPPORTED;
+        if (p->rl != b->rl || p->pair != b->pair || (b->rl && p->rl_b != b->plans[0]->rl_b))
+            return DD_ERR_UNSUPPORTED;  // a plan changed path since dd_batch_create
         const int64_t esz = p->band.in_type == DD_U8 ? 1 : 4;
         const int64_t t_out = plan_t_out(p);
         if (!d_in[i] || !d_out[i] || !aligned16(d_in[i]) || (in_ld[i] * esz) % 16 != 0 ||
@@ -148,21 +160,39 @@ dd_status dd_batch_bind(dd_batch_t b, const void* const* d_in, const int64_t* in
             return DD_ERR_ARG;
         dd_status st = dd::upload_tables(p);
         if (st != DD_OK) return st;
-        dd::fill_dedisp_args(p, d_in[i], in_ld[i], 0, t_out, d_out[i], out_ld[i], &args[i]);
     }
     // plans may have been retuned since dd_batch_create: rebuild the work list
     b->smem = 0;
     for (auto* p : b->plans) b->smem = std::max(b->smem, dd::dedisp_smem_for(p));
     build_items(b);
     free_batch_dev(b);
+    for (int i = 0; i < nb; ++i) {
+        dd_plan_s* p = b->plans[i];
+        const int64_t t_out = plan_t_out(p);
+        if (!b->rl) {
+            dd::fill_dedisp_args(p, d_in[i], in_ld[i], 0, t_out, d_out[i], out_ld[i], &args[i]);
+            continue;
+        }
+        // run-length beams read their own prefix sums, which the batch owns
+        const int64_t ldp = (p->band.nsamp + 1 + 3) & ~(int64_t)3;
+        uint32_t* q = nullptr;
+        const cudaError_t e = cudaMalloc((void**)&q, (size_t)ldp * p->nchan * sizeof(uint32_t));
+        if (e != cudaSuccess) {
+            free_batch_dev(b);
+            return dd::cuda_status(e);
+        }
+        b->d_prefix.push_back(q);
+        b->ldp.push_back(ldp);
+        dd::fill_dedisp_args(p, q, ldp, 0, t_out, d_out[i], out_ld[i], &args[i]);
+    }
     int dev = -1, sms = 0;
     cudaError_t e = cudaGetDevice(&dev);
     if (e == cudaSuccess) e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev);
     if (e != cudaSuccess) return dd::cuda_status(e);
     b->short_taps = true;
     for (auto* p : b->plans)
-        b->short_taps = b->short_taps && (p->pair ? p->umax <= dd::kRPair : p->kmax <= dd::kRInt);
-    const int per_sm = dd::dedisp_batched_blocks_per_sm(b->u8, b->pair, b->short_taps, b->smem);
+        b->short_taps = b->short_taps && (p->rl ? p->rl_b : p->pair ? p->umax <= dd::kRPair : p->kmax <= dd::kRInt);
+    const int per_sm = dd::dedisp_batched_blocks_per_sm(b->u8, b->pair, b->short_taps, b->smem, b->rl);
     if (per_sm < 1) return DD_ERR_UNSUPPORTED;
     b->grid = std::min<int>(per_sm * sms, (int)b->items.size());
     b->device = dev;
@@ -190,8 +220,15 @@ dd_status dd_batch_bind(dd_batch_t b, const void* const* d_in, const int64_t* in
 dd_status dd_batch_dedisperse(dd_batch_t b, void* stream) {
     if (!b) return DD_ERR_ARG;
     if (!b->bound) return DD_ERR_STATE;
+    if (b->rl)  // every beam's prefix sums first
+        for (size_t i = 0; i < b->plans.size(); ++i) {
+            const dd_status st = dd::launch_prefix_into(b->plans[i], b->in[i], b->in_ld[i], 0,
+                                                        b->plans[i]->band.nsamp, b->d_prefix[i], b->ldp[i],
+                                                        (cudaStream_t)stream);
+            if (st != DD_OK) return st;
+        }
     return dd::launch_dedisperse_batched(b->u8, b->pair, b->short_taps, b->d_args, b->d_items, (int32_t)b->items.size(),
-                                         b->d_counter, b->smem, b->grid, (cudaStream_t)stream);
+                                         b->d_counter, b->smem, b->grid, (cudaStream_t)stream, b->rl);
 }
 
 dd_status dd_batch_bind_boxcar(dd_batch_t b, const int32_t* widths, int32_t nw, double* const* d_mean,

@@ -620,13 +620,19 @@ __device__ __forceinline__ unsigned char* pipeline_area(unsigned char* smem, siz
     return smem + smem_bytes - (size_t)(nbuf * 8 + 2 * nbuf * 4);
 }
 
+// Grid: time tiles along x and trial blocks along y, except on the run-length path,
+// where trial blocks run along x so that the CTAs resident together share time tiles
+// and each tile's prefix rows come from L2 for all trial blocks (instead of every trial
+// block reading the whole prefix array from DRAM).
 template <typename TIN, bool PAIR, int NBUF, int SHORT>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ TileState ts;
     if (threadIdx.x == 0) init_pipeline<NBUF>(pipeline_area(smem, a.smem_bytes, NBUF), ts);
     __syncthreads();
-    dedisp_tile<TIN, PAIR, NBUF, false, SHORT>(a, smem, blockIdx.y, blockIdx.x, ts);
+    constexpr bool BLK_X = std::is_same<TIN, uint32_t>::value;
+    dedisp_tile<TIN, PAIR, NBUF, false, SHORT>(a, smem, BLK_X ? blockIdx.x : blockIdx.y,
+                                               BLK_X ? blockIdx.y : blockIdx.x, ts);
 }
 
 // Persistent form: each CTA takes work items (beam, trial block, time tile) from an
@@ -714,8 +720,9 @@ dd_status run(DedispArgs a, cudaStream_t s) {
     if (e != cudaSuccess) return cuda_status(e);
     const int64_t tile = (int64_t)chunk_t(PAIR) * a.nch;
     const int db = (PAIR ? 2 : 1) * nu;
-    dim3 grid((unsigned)((a.t_out + tile - 1) / tile), (unsigned)((a.ndm + db - 1) / db),
-              (unsigned)a.nsplit);
+    const unsigned ntile = (unsigned)((a.t_out + tile - 1) / tile), nblk = (unsigned)((a.ndm + db - 1) / db);
+    const bool blk_x = std::is_same<TIN, uint32_t>::value;
+    dim3 grid(blk_x ? nblk : ntile, blk_x ? ntile : nblk, (unsigned)a.nsplit);
     if (grid.y > 65535 || a.nsplit < 1 || a.nsplit > 64) return DD_ERR_UNSUPPORTED;
     kern<<<grid, kWarps * 32, smem, s>>>(a);
     return cuda_status(cudaGetLastError());
@@ -928,6 +935,14 @@ dd_status launch_dedisperse(dd_plan_s* p, const void* in, int64_t ld, int64_t t_
     return run<float, true, kStagesPair>(a, s);
 }
 
+// Prefix sums of columns t_offset .. t_offset + nsamp - 1 into caller-owned P
+// [nchan][ldp] (ldp >= nsamp + 1).
+dd_status launch_prefix_into(const dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
+                             int64_t nsamp, uint32_t* P, int64_t ldp, cudaStream_t s) {
+    k_prefix<<<p->nchan, 256, 0, s>>>((const uint8_t*)in, ld, t_offset, nsamp, P, ldp);
+    return cuda_status(cudaGetLastError());
+}
+
 // Run-length path: prefix sums of columns t_offset .. t_offset + nsamp - 1 into the
 // plan's scratch, then the run-length sums over them.
 dd_status launch_prefix(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset, int64_t nsamp,
@@ -959,7 +974,10 @@ dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t
 
 dd_status launch_dedisperse_batched(bool u8, bool pair, bool short_taps, const DedispArgs* d_args,
                                     const BatchItem* d_items, int32_t nitems, int32_t* d_counter,
-                                    size_t smem, int grid, cudaStream_t s) {
+                                    size_t smem, int grid, cudaStream_t s, bool rl) {
+    if (rl)  // run-length beams: short_taps = difference rows shared by the CTA
+        return short_taps ? run_batched<uint32_t, false, kStagesRl, 1>(d_args, d_items, nitems, d_counter, smem, grid, s)
+                          : run_batched<uint32_t, false, kStagesRl>(d_args, d_items, nitems, d_counter, smem, grid, s);
     if (!pair)
         return short_taps ? run_batched<uint8_t, false, kStagesInt, 1>(d_args, d_items, nitems, d_counter, smem, grid, s)
                           : run_batched<uint8_t, false, kStagesInt>(d_args, d_items, nitems, d_counter, smem, grid, s);
@@ -990,7 +1008,8 @@ dd_status launch_dedisperse_fused(const dd_plan_s* p, DedispArgs a, const FusedA
                             : run_fused<uint8_t, kStagesInt, 0>(a, f, smem, s);
 }
 
-int dedisp_batched_blocks_per_sm(bool u8, bool pair, bool short_taps, size_t smem) {
+int dedisp_batched_blocks_per_sm(bool u8, bool pair, bool short_taps, size_t smem, bool rl) {
+    if (rl) return short_taps ? blocks_per_sm<uint32_t, false, kStagesRl, 1>(smem) : blocks_per_sm<uint32_t, false, kStagesRl>(smem);
     if (!pair) return short_taps ? blocks_per_sm<uint8_t, false, kStagesInt, 1>(smem) : blocks_per_sm<uint8_t, false, kStagesInt>(smem);
     if (u8) return short_taps ? blocks_per_sm<uint8_t, true, kStagesPair, 1>(smem) : blocks_per_sm<uint8_t, true, kStagesPair>(smem);
     return short_taps ? blocks_per_sm<float, true, kStagesPair, 1>(smem) : blocks_per_sm<float, true, kStagesPair>(smem);

@@ -316,15 +316,16 @@ def make_large(seed: int | None = None, nsamp: int = 1 << 20, npulse: int = 8, w
                 dms=np.linspace(0.0, 2000.0, 8192), widths=np.arange(1, 257, dtype=np.int32))
 
 
-def make_batched_beams(seed: int | None = None, nbeams: int = 36):
+def make_batched_beams(seed: int | None = None, nbeams: int = 36, t_exp=(14, 17), d_exp=(9, 13)):
     """Seeded beam shapes: T_b = round(2^U[14,17]), D_b = round(2^U[9,13]),
-    DM_max,b = logU[500, 4000]; every beam uses the CRAFT band and uint8 samples."""
+    DM_max,b = logU[500, 4000]; every beam uses the CRAFT band and uint8 samples.
+    t_exp and d_exp narrow the exponent ranges (e.g. the lower end of both)."""
     seed = sub_seed("batched") if seed is None else seed
     rng = np.random.default_rng(seed)
     beams = []
     for b in range(nbeams):
-        T = int(round(2.0 ** rng.uniform(14, 17)))
-        D = int(round(2.0 ** rng.uniform(9, 13)))
+        T = int(round(2.0 ** rng.uniform(*t_exp)))
+        D = int(round(2.0 ** rng.uniform(*d_exp)))
         dmax = float(math.exp(rng.uniform(math.log(500.0), math.log(4000.0))))
         beams.append(dict(nsamp=T, ndm=D, dm_max=dmax, seed=seed * 100 + b))
     return dict(band=CRAFT_BAND, beams=beams)

@@ -147,3 +147,69 @@ def test_batched_long_taps_equals_per_beam(dd):
         np.testing.assert_array_equal(ob.cpu().numpy(), p.dedisperse(xb, nsamp=p.band.nsamp).cpu().numpy())
     want = oracle.c_dedisperse(data, delay, taps, nsamp=plan.band.nsamp, rows=[0, D - 1])
     np.testing.assert_array_equal(o2.cpu().numpy()[[0, D - 1]].astype(np.int64), want)
+
+
+def _rl_beams(dd, n=5, seed=47, share_rows=True):
+    """Uneven run-length beams on 256 channels of the low band (700-775 MHz, 64 us
+    sampling): long tap runs, prefix-sum differences; with share_rows the trial lists
+    are dense enough that each block of trials has at most two tap counts per channel."""
+    import torch
+    rng = np.random.default_rng(seed)
+    out = []
+    for i in range(n):
+        T = int(round(2 ** rng.uniform(14, 15.5)))
+        dm_max = float(rng.uniform(60.0, 150.0))
+        # dense lists: a 24-trial block spans < 7 pc cm^-3, so at most two tap counts
+        D = int(3.5 * dm_max) + int(rng.integers(0, 30)) if share_rows else int(rng.integers(40, 60))
+        dms = np.linspace(0.0, dm_max, D)
+        band = dd.Band(256, 700.0, 300.0 / 1024, 0.064, T, "u8")
+        plan = dd.Plan(band, dms)
+        plan.set_method("runlength")
+        ld = (T + 15) // 16 * 16                # rows staged in 16-byte chunks
+        data = np.zeros((256, ld), np.uint8)
+        data[:, :T] = rng.integers(0, 256, size=(256, T))
+        x = torch.from_numpy(data).cuda()
+        outb = torch.zeros((D, T - plan.d_max), dtype=torch.int32, device="cuda")
+        out.append((plan, x, outb, data))
+    return out
+
+
+@pytest.mark.parametrize("share_rows", [True, False])
+def test_batched_runlength_equals_per_beam_and_oracle(dd, share_rows):
+    """Run-length beams in one persistent launch (prefix passes first) give the per-beam
+    run-length sums bit for bit, sampled rows equal the oracle, and the graph replay
+    repeats them."""
+    import torch
+    beams = _rl_beams(dd, share_rows=share_rows)
+    assert all(p.method == "runlength" for p, _, _, _ in beams)
+    batch = dd.Batch([p for p, _, _, _ in beams])
+    batch.bind([x for _, x, _, _ in beams], [o for _, _, o, _ in beams])
+    batch.dedisperse()
+    torch.cuda.synchronize()
+    for plan, x, o, data in beams:
+        ref = plan.dedisperse(x, nsamp=plan.band.nsamp)
+        np.testing.assert_array_equal(o.cpu().numpy(), ref.cpu().numpy())
+        delay, taps = plan.tables()
+        rows = [0, plan.ndm // 3, plan.ndm - 1]
+        want = oracle.c_dedisperse(data, delay, taps, nsamp=plan.band.nsamp, rows=rows)
+        np.testing.assert_array_equal(o.cpu().numpy()[rows].astype(np.int64), want)
+    before = [o.clone() for _, _, o, _ in beams]
+    for _, _, o, _ in beams:
+        o.zero_()
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        batch.capture(s)
+        for _, _, o, _ in beams:
+            o.zero_()
+        batch.replay(s)
+    s.synchronize()
+    for b_, (_, _, o, _) in zip(before, beams):
+        assert torch.equal(b_, o)
+    batch.close()
+
+
+def test_batch_refuses_mixed_methods(dd):
+    beams = _rl_beams(dd, n=2)
+    beams[1][0].set_method("direct")
+    with pytest.raises(dd.DDError):
+        dd.Batch([p for p, _, _, _ in beams])

@@ -6,6 +6,10 @@ import os
 
 HERE = os.path.dirname(os.path.abspath(__file__))
 LIB_PATH = os.path.join(HERE, "_build", "libdd.so")
+# DD_DEBUG_LIB=1 in the environment (read at the first load) selects the debug build:
+# the same library with bounds checks in the kernels that record DD_ERR_ARG in the
+# plan's device status word
+LIB_DEBUG_PATH = os.path.join(HERE, "_build", "libdd_debug.so")
 
 c_i32 = ctypes.c_int32
 c_i64 = ctypes.c_int64
@@ -99,9 +103,10 @@ def load():
     global _lib
     if _lib is not None:
         return _lib
-    if not os.path.exists(LIB_PATH):
-        raise ImportError(f"libdd.so is not built ({LIB_PATH}); run __graft_entry__.build()")
-    lib = ctypes.CDLL(LIB_PATH)
+    path = LIB_DEBUG_PATH if os.environ.get("DD_DEBUG_LIB", "") == "1" else LIB_PATH
+    if not os.path.exists(path):
+        raise ImportError(f"{os.path.basename(path)} is not built ({path}); run __graft_entry__.build()")
+    lib = ctypes.CDLL(path)
     for name, (res, args) in SIGNATURES.items():
         fn = getattr(lib, name)
         fn.restype = res

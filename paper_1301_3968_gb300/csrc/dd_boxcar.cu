@@ -12,6 +12,7 @@
 #include <cstdint>
 
 #include "dd_async.cuh"
+#include "dd_debug.cuh"
 #include "dd_internal.h"
 
 namespace dd {
@@ -203,6 +204,7 @@ struct BoxArgs {
     // equals narrow_sel (the int32 launch takes the flagged rows, the int64 one the rest)
     const uint8_t* narrow;
     int32_t narrow_sel;
+    int32_t* status;  // the plan's device status word (debug-build bounds checks)
 };
 
 template <typename T>
@@ -314,6 +316,7 @@ __global__ void __launch_bounds__(256) k_boxcar(BoxArgs a) {
             }
         }
         const int64_t o2 = (int64_t)d * a.nw + j0 + j;
+        if (!dbg_ok(d < a.ndm && j0 + j < a.nw, a.status)) return;
         const float snr = (float)(((double)b - (double)a.mu[o2]) * (double)a.isd[o2]);
         a.peak[o2] = snr;
         a.arg[o2] = i;
@@ -425,6 +428,8 @@ __global__ void __launch_bounds__(256) k_boxcar_run(BoxArgs a) {
     const int chunk = 256 * S;
     const int stage = chunk + w0 + G;
     const int ls = tid * S;
+    // the staged chunk fits its buffer and every width of the group fits the series
+    if (!dbg_ok(stage <= bufl && w0 >= 1 && wlast <= a.t_len, a.status)) return;
     // past the end of the row the buffer holds zeros; only windows that run past the
     // series end read them, and those are excluded
     auto load = [&](int tc, TX* dst) {
@@ -519,6 +524,7 @@ __global__ void __launch_bounds__(256) k_boxcar_run(BoxArgs a) {
             }
         }
         const int64_t o2 = (int64_t)d * a.nw + j0 + j;
+        if (!dbg_ok(d < a.ndm && j0 + j < a.nw, a.status)) return;
         const float snr = (float)(((double)b - (double)a.mu[o2]) * (double)a.isd[o2]);
         a.peak[o2] = snr;
         a.arg[o2] = arg;
@@ -678,6 +684,7 @@ dd_status launch_boxcar_scratch(dd_plan_s* p, const void* x, int64_t ld, int64_t
     a.ncands = ncands;
     a.narrow = nullptr;
     a.narrow_sel = 0;
+    a.status = p->dev.status;
     return dispatch_boxcar(p, a, widths, nw, s, false);
 }
 
@@ -749,6 +756,7 @@ dd_status launch_boxcar(dd_plan_s* p, const void* x, int64_t ld, int64_t t_len,
     a.ncands = ncands;
     a.narrow = nullptr;
     a.narrow_sel = 0;
+    a.status = p->dev.status;
     return dispatch_boxcar(p, a, widths, nw, s, true);
 }
 

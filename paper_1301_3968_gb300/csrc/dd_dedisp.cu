@@ -38,6 +38,7 @@
 #include <cstdint>
 #include <type_traits>
 
+#include "dd_debug.cuh"
 #include "dd_internal.h"
 #include "dd_packed.cuh"
 #include "dd_fused_scan.cuh"
@@ -164,6 +165,18 @@ __device__ void issue_stage(const DedispArgs& a, const StageGeom& g, const Smem&
     const int nst = (a.nchan + a.cs - 1) / a.cs;
     const unsigned char* rec = a.rec + ((int64_t)blk * nst + stage) * g.rec_bytes;
     const uint32_t row_bytes = (uint32_t)a.lcap * sizeof(TIN);
+    if (kDebug) {  // every copied window inside its row and its stage buffer
+        bool ok = (int64_t)csn * row_bytes <= g.rows_bytes && c0 >= 0 && csn > 0;
+        for (int ci = 0; ci < csn; ++ci) {
+            const int64_t a0 = (base + sm.lo_all[c0 + ci]) & ~(int64_t)(Q - 1);
+            ok = ok && a0 >= 0 && (tail || a0 + a.lcap <= a.ld);
+        }
+        if (!dbg_ok(ok, a.status)) {  // complete the phase without copies
+            asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];\n" ::"r"(su32(&sm.full[b])) : "memory");
+            sm.issued[b] += 1;
+            return;
+        }
+    }
     if (!tail) {
         mbar_expect_tx(&sm.full[b], (uint32_t)csn * row_bytes + g.rec_bytes);
         for (int ci = 0; ci < csn; ++ci) {
@@ -211,13 +224,15 @@ __device__ void issue_stage(const DedispArgs& a, const StageGeom& g, const Smem&
 template <typename TIN, int SHORT>
 __device__ __forceinline__ void stage_int(const TIN* rows, const int2* ent, const int* lo,
                                           int csn, int lcap, int bq, int lane_off,
-                                          int (&acc)[kRInt]) {
+                                          int (&acc)[kRInt], int32_t* status) {
     constexpr int Q = Elem<TIN>::Q;
     constexpr int R = kRInt;
     for (int ci = 0; ci < csn; ++ci) {
         const int2 q = ent[ci];  // (window start - block minimum, taps)
         const int n = q.y;
-        const TIN* p = rows + ci * lcap + ((bq + lo[ci]) & (Q - 1)) + q.x + lane_off;
+        const int i0 = ((bq + lo[ci]) & (Q - 1)) + q.x + lane_off;
+        if (!dbg_ok(q.x >= 0 && n >= 1 && i0 + R + n <= lcap, status)) continue;
+        const TIN* p = rows + ci * lcap + i0;
         __builtin_assume(__isShared(p));
         int win[R];
 #pragma unroll
@@ -249,11 +264,14 @@ __device__ __forceinline__ void stage_int(const TIN* rows, const int2* ent, cons
 // add per output whatever n is; the uint32 difference is exact (taken modulo 2^32 and
 // at most 255 n).
 __device__ __forceinline__ void stage_rl(const uint32_t* rows, const int2* ent, const int* lo,
-                                         int csn, int lcap, int bq, int lane_off, int (&acc)[kRInt]) {
+                                         int csn, int lcap, int bq, int lane_off, int (&acc)[kRInt],
+                                         int32_t* status) {
     constexpr int R = kRInt;
     for (int ci = 0; ci < csn; ++ci) {
         const int2 q = ent[ci];  // (run start - block minimum, taps)
-        const uint32_t* p = rows + ci * lcap + ((bq + lo[ci]) & 3) + q.x + lane_off;
+        const int i0 = ((bq + lo[ci]) & 3) + q.x + lane_off;
+        if (!dbg_ok(q.x >= 0 && q.y >= 1 && i0 + q.y + R <= lcap, status)) continue;
+        const uint32_t* p = rows + ci * lcap + i0;
         const uint32_t* pe = p + q.y;
         __builtin_assume(__isShared(p));
         __builtin_assume(__isShared(pe));
@@ -266,11 +284,14 @@ __device__ __forceinline__ void stage_rl(const uint32_t* rows, const int2* ent, 
 // channel, B_q[i] = P[i + n_q] - P[i] for the block's (at most two) tap counts n_q, and
 // the unit's entry is (run start, q).  One load and one add per output.
 __device__ __forceinline__ void stage_rl_rows(const uint32_t* brows, const int2* ent, const int* lo,
-                                              int csn, int lcap, int bq, int lane_off, int (&acc)[kRInt]) {
+                                              int csn, int lcap, int bq, int lane_off, int (&acc)[kRInt],
+                                              int32_t* status) {
     constexpr int R = kRInt;
     for (int ci = 0; ci < csn; ++ci) {
         const int2 q = ent[ci];  // (run start - block minimum, index of the tap count)
-        const uint32_t* p = brows + (ci * 2 + q.y) * lcap + ((bq + lo[ci]) & 3) + q.x + lane_off;
+        const int i0 = ((bq + lo[ci]) & 3) + q.x + lane_off;
+        if (!dbg_ok(q.x >= 0 && (q.y == 0 || q.y == 1) && i0 + R <= lcap, status)) continue;
+        const uint32_t* p = brows + (ci * 2 + q.y) * lcap + i0;
         __builtin_assume(__isShared(p));
 #pragma unroll
         for (int r = 0; r < R; ++r) acc[r] += (int)p[r];
@@ -340,11 +361,17 @@ __device__ __forceinline__ void pair_channel(const TIN* p, int s, int n, const u
 template <typename TIN, int SHORT>
 __device__ __forceinline__ void stage_pair(const TIN* rows, const int4* ent, const float2* wts,
                                            const int* lo, int csn, int lcap, int bq,
-                                           int lane_off, uint64_t (&acc)[kRPair]) {
+                                           int lane_off, uint64_t (&acc)[kRPair], int wpairs,
+                                           int32_t* status) {
     constexpr int Q = Elem<TIN>::Q;
     for (int ci = 0; ci < csn; ++ci) {
         const int4 q = ent[ci];
-        const TIN* p = rows + ci * lcap + ((bq + lo[ci]) & (Q - 1)) + q.x + lane_off;
+        const int i0 = ((bq + lo[ci]) & (Q - 1)) + q.x + lane_off;
+        if (!dbg_ok(q.x >= 0 && q.y >= 1 && i0 + min(q.z, 0) >= 0 && i0 + max(q.z, 0) + kRPair + q.y <= lcap &&
+                        q.w >= 0 && q.w + q.y <= wpairs,
+                    status))
+            continue;
+        const TIN* p = rows + ci * lcap + i0;
         const uint64_t* wk = (const uint64_t*)(wts + q.w);
         __builtin_assume(__isShared(p));
         __builtin_assume(__isShared(wk));
@@ -357,7 +384,8 @@ __device__ __forceinline__ void stage_pair(const TIN* rows, const int4* ent, con
 
 template <typename TACC, int R>
 __device__ __forceinline__ void store_row(unsigned char* smem, const TACC (&acc)[R], int warp,
-                                          int lane, int64_t tw, int32_t t_out, TACC* out) {
+                                          int lane, int64_t tw, int32_t t_out, TACC* out,
+                                          int64_t out_ld = INT64_MAX, int32_t* status = nullptr) {
     TACC* st = (TACC*)smem + warp * (32 * R);
 #pragma unroll
     for (int r = 0; r < R; ++r) st[lane * R + r] = acc[r];
@@ -366,7 +394,7 @@ __device__ __forceinline__ void store_row(unsigned char* smem, const TACC (&acc)
 #pragma unroll 4
         for (int j = 0; j < R; ++j) {
             const int64_t t = tw + j * 32 + lane;
-            if (t < t_out) out[t] = st[j * 32 + lane];
+            if (t < t_out && dbg_ok(t >= 0 && t < out_ld, status)) out[t] = st[j * 32 + lane];
         }
     }
     __syncwarp();
@@ -467,6 +495,7 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
                     const int n = q ? nn.y : nn.x;
                     const int len = q ? nn.w : nn.z;
                     if (n <= 0) continue;
+                    if (!dbg_ok(len >= 0 && len <= a.blen && len + n <= a.lcap, a.status)) continue;
                     const uint32_t* pr = rows + ci * a.lcap;
                     uint32_t* br = half + (ci * 2 + q) * a.blen;
 #pragma unroll 4
@@ -494,11 +523,12 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
             const int2* ent = (const int2*)(half + cs * 2 * a.blen) + dmi * cs;
             const int c0 = (s_lo + i) * cs;
             const int csn = min(cs, a.nchan - c0);
-            if (d < a.ndm) stage_rl_rows(half, ent, lo_all + c0, csn, a.blen, bq, lane_off, acc0);
+            if (d < a.ndm) stage_rl_rows(half, ent, lo_all + c0, csn, a.blen, bq, lane_off, acc0, a.status);
 #pragma unroll
             for (int u = 1; u < UPW; ++u)
                 if (d + u < a.ndm)
-                    stage_rl_rows(half, ent + u * cs, lo_all + c0, csn, a.blen, bq, lane_off, accr[u - 1]);
+                    stage_rl_rows(half, ent + u * cs, lo_all + c0, csn, a.blen, bq, lane_off, accr[u - 1],
+                                  a.status);
             if (__syncthreads_or(!got)) {
                 if (tid == 0) atomicExch(a.status, (int)DD_ERR_TIMEOUT);
                 ok = false;
@@ -529,11 +559,11 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
             const int* lo_all = (const int*)(smem + NBUF * g.bytes);
             const int c0 = s * cs;
             const int csn = min(cs, a.nchan - c0);
-            if (d < a.ndm) stage_rl(rows, ent, lo_all + c0, csn, a.lcap, bq, lane_off, acc0);
+            if (d < a.ndm) stage_rl(rows, ent, lo_all + c0, csn, a.lcap, bq, lane_off, acc0, a.status);
 #pragma unroll
             for (int u = 1; u < UPW; ++u)
                 if (d + u < a.ndm)
-                    stage_rl(rows, ent + u * cs, lo_all + c0, csn, a.lcap, bq, lane_off, accr[u - 1]);
+                    stage_rl(rows, ent + u * cs, lo_all + c0, csn, a.lcap, bq, lane_off, accr[u - 1], a.status);
         } else if (d < a.ndm) {
             // pointers derived from the __shared__ array itself, so that every access
             // below compiles to a shared-memory load
@@ -546,9 +576,10 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
             if constexpr (PAIR) {
                 const int4* ent4 = (const int4*)(buf + g.rec_off) + dmi * cs;
                 const float2* wts = (const float2*)(buf + g.rec_off + g.w_off);
-                stage_pair<TIN, SHORT>(rows, ent4, wts, lo_all + c0, csn, a.lcap, bq, lane_off, accp);
+                stage_pair<TIN, SHORT>(rows, ent4, wts, lo_all + c0, csn, a.lcap, bq, lane_off, accp,
+                                       a.kpad, a.status);
             } else {
-                stage_int<TIN, SHORT>(rows, ent, lo_all + c0, csn, a.lcap, bq, lane_off, acc0);
+                stage_int<TIN, SHORT>(rows, ent, lo_all + c0, csn, a.lcap, bq, lane_off, acc0, a.status);
             }
         }
         __syncwarp();
@@ -585,15 +616,17 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
 #pragma unroll
         for (int r = 0; r < R; ++r) unpk(accp[r], acc0[r], acc1[r]);
     }
-    store_row<TACC, R>(smem, acc0, warp, lane, tw, a.t_out, d < a.ndm ? out + (int64_t)d * a.out_ld : nullptr);
+    const int64_t oldx = a.out_ld;  // a row's extent
+    store_row<TACC, R>(smem, acc0, warp, lane, tw, a.t_out, d < a.ndm ? out + (int64_t)d * a.out_ld : nullptr,
+                       oldx, a.status);
     if constexpr (PAIR)
         store_row<float, R>(smem, acc1, warp, lane, tw, a.t_out,
-                         d + 1 < a.ndm ? (float*)out + (int64_t)(d + 1) * a.out_ld : nullptr);
+                         d + 1 < a.ndm ? (float*)out + (int64_t)(d + 1) * a.out_ld : nullptr, oldx, a.status);
     if constexpr (RL) {
 #pragma unroll
         for (int u = 1; u < UPW; ++u)
             store_row<int, R>(smem, accr[u - 1], warp, lane, tw, a.t_out,
-                           d + u < a.ndm ? (int*)out + (int64_t)(d + u) * a.out_ld : nullptr);
+                           d + u < a.ndm ? (int*)out + (int64_t)(d + u) * a.out_ld : nullptr, oldx, a.status);
     }
     if (MULTI) __syncthreads();  // the staging area is the next tile's stage buffers
     return true;

@@ -516,7 +516,7 @@ def batched_extra(dd, dev, flush, stream, reps=3, iadd_tops=None):
 
 
 def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, iadd_tops=None,
-                sm_mhz=None, sms=None):
+                sm_mhz=None, sms=None, dm_range=None):
     """Large low-band configuration: 1024 ch over 700-1000 MHz, dt 64 us, 2^20 uint8
     samples, 8192 trial DMs 0-2000 (unit weights, run-length sums), streamed in
     overlapping chunks of `chunk` outputs (each chunk reads its outputs plus d_max
@@ -529,7 +529,10 @@ def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, 
         sms = torch.cuda.get_device_properties(dev).multi_processor_count
     cfg = synth.make_large(nsamp=nsamp)
     b, T = cfg["band"], cfg["nsamp"]
-    dms = cfg["dms"] if ndm == len(cfg["dms"]) else np.linspace(0.0, cfg["dms"][-1], ndm)
+    if dm_range is not None:   # a profiling case: part of the list at the same spacing
+        dms = np.linspace(dm_range[0], dm_range[1], ndm)
+    else:
+        dms = cfg["dms"] if ndm == len(cfg["dms"]) else np.linspace(0.0, cfg["dms"][-1], ndm)
     plan = dd.Plan(dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, T, "u8"), dms)
     x = torch.from_numpy(cfg["data"]).to(dev)
     dmax = plan.d_max
@@ -567,7 +570,7 @@ def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, 
     graded = float(np.minimum(taps, 2).astype(np.int64).sum()) * t_out + float(b.nchan) * T
     res = {
         "workload": (f"large low-band: {b.nchan} ch 700-1000 MHz, dt 64 us, {T} uint8 samples, "
-                     f"{plan.ndm} trial DMs 0-2000, {len(starts)} overlapping chunks of {chunk} "
+                     f"{plan.ndm} trial DMs {dms[0]:.0f}-{dms[-1]:.0f}, {len(starts)} overlapping chunks of {chunk} "
                      "outputs, int32 out, boxcar widths 1-256"),
         "method": plan.method, "d_max": dmax, "t_out": t_out,
         "dedisp_ms": dd_ms, "step_ms": st_ms,
@@ -764,8 +767,10 @@ def run_only(args):
     elif args.only == "batched":
         r = batched_extra(dd, dev, flush, stream, iadd_tops=dd.alu_peak("iadd") / 1e12)
     else:
+        rng = None if args.large_dm_range is None else tuple(args.large_dm_range)
         r = large_extra(dd, dev, flush, stream, nsamp=args.large_nsamp, ndm=args.large_ndm,
-                        iadd_tops=dd.alu_peak("iadd") / 1e12)
+                        iadd_tops=dd.alu_peak("iadd") / 1e12, dm_range=rng,
+                        chunk=min(1 << 18, args.large_nsamp))
     return {"only": args.only, **r}
 
 
@@ -785,6 +790,8 @@ def main():
                     help="run one extra measurement alone (profiling)")
     ap.add_argument("--large-nsamp", type=int, default=1 << 20)
     ap.add_argument("--large-ndm", type=int, default=8192)
+    ap.add_argument("--large-dm-range", type=float, nargs=2, default=None,
+                    help="profiling case: --large-ndm trials evenly over this DM range")
     ap.add_argument("--no-extras", action="store_true",
                     help="skip the forward+backward, batched-beam and large low-band measurements")
     ap.add_argument("--traffic", type=float, default=None,

@@ -25,6 +25,11 @@
  *   - Input rows are `in_ld` elements apart; in_ld * element size must be a multiple of
  *     16 bytes and the input base pointer 16-byte aligned (rows are staged in 16-byte
  *     chunks).  Violations return DD_ERR_ARG.
+ *   - Tracing and logging: every device call opens an NVTX range named after it (shown by
+ *     timeline tools; a no-op without one), and the environment variable DD_LOG (read once)
+ *     makes the library log to stderr: 1 = plan decisions (tap-sum method, CTA shape, stage
+ *     size, row lengths, shared memory), autotuner results, batch bindings; 2 = also every
+ *     device call with its sizes.
  *   - No call here allocates device memory except dd_plan_create / dd_set_profiles /
  *     the first device call on a plan (tables; on a device's first plan also the 8 MiB
  *     array of dd_boxcar_snr_noalloc), dd_boxcar_snr when the width count

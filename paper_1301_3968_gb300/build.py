@@ -60,7 +60,7 @@ def _compile(src: str, verbose: bool, debug: bool = False) -> str:
 
 def _link(objs: list[str], lib: str) -> None:
     tmp = lib + f".tmp{os.getpid()}"
-    cmd = [_nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static"]
+    cmd = [_nvcc(), "-shared", "-o", tmp] + objs + ARCH + ["-cudart", "static", "-ldl"]
     res = subprocess.run(cmd, capture_output=True, text=True)
     if res.returncode != 0:
         raise RuntimeError(f"link failed:\n{res.stdout}\n{res.stderr}")

@@ -19,6 +19,7 @@
 #include <string>
 
 #include "dd_internal.h"
+#include "dd_trace.h"
 
 struct dd_batch_s {
     std::vector<dd_plan_s*> plans;
@@ -214,10 +215,14 @@ dd_status dd_batch_bind(dd_batch_t b, const void* const* d_in, const int64_t* in
     b->out_ld.assign(out_ld, out_ld + nb);
     b->bound = true;
     b->box_bound = false;
+    dd::logf(1, "batch of %d beams (%s): %zu work items, persistent grid %d CTAs, %zu bytes of shared memory",
+             nb, b->rl ? "run-length sums" : (b->pair ? "fp32 pair units" : "exact integer sums"), b->items.size(),
+             b->grid, b->smem);
     return DD_OK;
 }
 
 dd_status dd_batch_dedisperse(dd_batch_t b, void* stream) {
+    DD_TRACE("dd_batch_dedisperse");
     if (!b) return DD_ERR_ARG;
     if (!b->bound) return DD_ERR_STATE;
     if (b->rl)  // every beam's prefix sums first
@@ -269,6 +274,7 @@ static dd_status batch_run(dd_batch_s* b, cudaStream_t s) {
 }
 
 dd_status dd_batch_run(dd_batch_t b, void* stream) {
+    DD_TRACE("dd_batch_run");
     if (!b) return DD_ERR_ARG;
     if (!b->bound) return DD_ERR_STATE;
     return batch_run(b, (cudaStream_t)stream);
@@ -303,6 +309,7 @@ dd_status dd_batch_capture(dd_batch_t b, void* stream) {
 }
 
 dd_status dd_batch_replay(dd_batch_t b, void* stream) {
+    DD_TRACE("dd_batch_replay");
     if (!b) return DD_ERR_ARG;
     if (!b->exec) return DD_ERR_STATE;
     return dd::cuda_status(cudaGraphLaunch(b->exec, (cudaStream_t)stream));

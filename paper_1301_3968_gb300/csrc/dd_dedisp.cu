@@ -698,7 +698,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_batched(const DedispA
 
 // Fused dedispersion + boxcar scan, one CTA per part: part s walks the
 // items (trial block, time tile) starts[s] .. starts[s + 1] - 1 in order (block-major),
-// a strip per trial block it touches.
+// a strip per trial block it touches.  CTA i takes part order[i].
 template <typename TIN, int NBUF, int SHORT>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_fused(DedispArgs a, const FusedArgs f) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -709,7 +709,7 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_fused(DedispArgs a, c
     // registers across the channel sums (thread 0 writes it before each tile; the tile's
     // barriers order it, and the epilogue's last barrier ends its readers)
     __shared__ fused::FusedTile ft;
-    const int s = blockIdx.x;
+    const int s = (int)f.order[blockIdx.x];
     const int i0 = (int)f.starts[s], i1 = (int)f.starts[s + 1];  // items < 2^31 (host check)
     for (int it = i0; it < i1; ++it) {
         const int blk = it / f.tiles;

@@ -11,6 +11,7 @@
 #include <cstdint>
 
 #include "dd_internal.h"
+#include "dd_trace.h"
 
 namespace dd {
 namespace {
@@ -129,6 +130,22 @@ std::vector<int64_t> cut_parts(const std::vector<double>& cost, int tiles, doubl
     return st;
 }
 
+// Cuts every trial block into nseg segments at the same time tiles (the block-major
+// items stay contiguous per part), and orders the CTAs segment by segment, so that the
+// CTAs resident together work on the same time tiles of different trial blocks and stage
+// the same input columns, which then come from L2.  Returns the parts' first items
+// (plus the end) and the launch order (CTA i takes part order[i]).
+void aligned_parts(int64_t nblk, int tiles, int nseg, std::vector<int64_t>* starts,
+                   std::vector<int64_t>* order) {
+    starts->clear();
+    for (int64_t b = 0; b < nblk; ++b)
+        for (int k = 0; k < nseg; ++k) starts->push_back(b * tiles + (int64_t)tiles * k / nseg);
+    starts->push_back(nblk * tiles);
+    order->clear();
+    for (int k = 0; k < nseg; ++k)
+        for (int64_t b = 0; b < nblk; ++b) order->push_back(b * nseg + k);
+}
+
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 }  // namespace
@@ -139,6 +156,8 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
                                           const double* mean, const double* sd, float* peak,
                                           int32_t* arg, float thresh, dd_candidate* cands,
                                           int32_t cap, int32_t* ncands, void* stream) {
+    DD_TRACE("dd_dedisperse_boxcar");
+    dd::logf(2, "dd_dedisperse_boxcar: %d trials, t_offset %lld, nsamp %lld, %d widths", p ? p->ndm : 0, (long long)t_offset, (long long)nsamp, nw);
     using namespace dd;
     if (!p || !in || !widths || nw < 1 || !mean || !sd || !peak || !arg) return DD_ERR_ARG;
     if (cands && (!ncands || cap < 0)) return DD_ERR_ARG;
@@ -186,26 +205,37 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
     const int64_t nitems = nblk * tiles;
     if (nitems >= INT32_MAX) return DD_ERR_UNSUPPORTED;
     // k parts per resident CTA, k = items / (16 x resident CTAs) clamped to 1..8: parts of
-    // at least ~16 tiles, so that the seams and carry-less first tiles stay a small share,
-    // and on large launches short enough runs that the CTAs on the device work on
-    // neighbouring blocks and time spans (measured on the large low-band block: 2.4k-2.7k
-    // parts beat 300 and 11k)
+    // at least ~16 tiles, so that the seams and carry-less first tiles stay a small share
+    // (measured on the large low-band block: 2.4k-2.7k parts beat 300 and 11k)
     const int64_t slots = (int64_t)bps * nsm;
     const int64_t k_per = std::max<int64_t>(1, std::min<int64_t>(8, nblk * tiles / (16 * slots)));
-    int64_t np = p->debug_fused_parts > 0 ? p->debug_fused_parts : k_per * slots;
-    const int nparts = (int)std::min<int64_t>(np, nitems);
-    // cost of a tile: constant on the run-length path, the block's taps (plus a per-
-    // channel constant) on the direct path
-    std::vector<double> cost((size_t)nblk, 1.0);
-    if (!p->rl)
-        for (int64_t b = 0; b < nblk; ++b) {
-            double c = 0.0;
-            for (int64_t d = b * tpc; d < std::min<int64_t>((b + 1) * tpc, p->ndm); ++d)
-                for (int ch = 0; ch < p->nchan; ++ch) c += p->taps[(size_t)d * p->nchan + ch] + 4.0;
-            cost[(size_t)b] = c;
-        }
-    const double last_frac = (double)(t_out - (int64_t)(tiles - 1) * L) / L;
-    std::vector<int64_t> starts = cut_parts(cost, tiles, last_frac, nparts);
+    std::vector<int64_t> starts, order;
+    int nparts = 0;
+    if (p->debug_fused_parts > 0) {
+        // test hook: that many parts of about equal cost, in block-major order (cost of a
+        // tile: constant on the run-length path, the block's taps plus a per-channel
+        // constant on the direct path)
+        nparts = (int)std::min<int64_t>(p->debug_fused_parts, nitems);
+        std::vector<double> cost((size_t)nblk, 1.0);
+        if (!p->rl)
+            for (int64_t b = 0; b < nblk; ++b) {
+                double c = 0.0;
+                for (int64_t d = b * tpc; d < std::min<int64_t>((b + 1) * tpc, p->ndm); ++d)
+                    for (int ch = 0; ch < p->nchan; ++ch) c += p->taps[(size_t)d * p->nchan + ch] + 4.0;
+                cost[(size_t)b] = c;
+            }
+        const double last_frac = (double)(t_out - (int64_t)(tiles - 1) * L) / L;
+        starts = cut_parts(cost, tiles, last_frac, nparts);
+        for (int i = 0; i < nparts; ++i) order.push_back(i);
+    } else {
+        // up to k_per parts per resident CTA (no more, so that a last partial wave does not
+        // run alone), every block cut at the same time tiles
+        const int nseg = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, k_per * slots / nblk));
+        aligned_parts(nblk, tiles, nseg, &starts, &order);
+        nparts = (int)(starts.size() - 1);
+    }
+    if ((int64_t)nparts * tpc * 2 * C >= INT32_MAX || nparts < 1) return DD_ERR_UNSUPPORTED;
+    starts.insert(starts.end(), order.begin(), order.end());  // one table: starts, then order
 
     FusedArgs f;
     f.w0 = widths[0];
@@ -231,6 +261,7 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
         p->fstarts = starts;
     }
     f.starts = p->d_fstarts;
+    f.order = p->d_fstarts + nparts + 1;
     if ((st = grow(&p->d_fkey, &p->fkey_elems, (int64_t)p->ndm * nw)) != DD_OK) return st;
     if ((st = grow(&p->d_fcarry, &p->fcarry_elems, (int64_t)nparts * tpc * C)) != DD_OK) return st;
     if ((st = grow(&p->d_fseam, &p->fseam_elems, (int64_t)nparts * tpc * 2 * C)) != DD_OK) return st;

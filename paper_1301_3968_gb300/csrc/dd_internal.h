@@ -117,6 +117,9 @@ struct FusedArgs {
     int32_t tiles;      // time tiles per trial block; item = block * tiles + tile
     int32_t mlim;       // largest |x - o| for which every width-wmax sum fits int32
     const int64_t* starts;    // [nparts + 1] first item of each part
+    const int64_t* order;     // [nparts] part taken by CTA i: parts sorted by their first
+                              // time tile, so that CTAs resident together read the same
+                              // input columns (shared in L2)
     const double* off;        // [ndm] per-trial offsets (integer valued)
     unsigned long long* key;  // [ndm][nw]
     int32_t* carry;     // [nparts][trials per CTA][C]

@@ -15,6 +15,7 @@
 #include <mutex>
 
 #include "dd_internal.h"
+#include "dd_trace.h"
 
 namespace {
 
@@ -67,6 +68,7 @@ extern "C" dd_status dd_boxcar_snr_noalloc(dd_plan_t p, const void* x, int64_t l
                                            const double* sd, float* peak, int32_t* arg,
                                            float thresh, dd_candidate* cands, int32_t cap,
                                            int32_t* ncands, void* stream) {
+    DD_TRACE("dd_boxcar_snr_noalloc");
     if (!p || !x || !widths || nw < 1 || !mean || !sd || !peak || !arg) return DD_ERR_ARG;
     if (t_len < 1 || ld < t_len || t_len > INT32_MAX) return DD_ERR_ARG;
     if (cands && (!ncands || cap < 0)) return DD_ERR_ARG;

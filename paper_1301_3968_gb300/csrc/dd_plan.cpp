@@ -2,6 +2,9 @@
 // trial-DM rule (eq. trial DMs, Sec. 6.3), argument checking and the dedispersion
 // schedule (trial blocks and staged window lengths).
 #include <algorithm>
+#include <cstdlib>
+#include <cstdio>
+#include <cstdarg>
 #include <cmath>
 #include <cstring>
 #include <fstream>
@@ -12,6 +15,7 @@
 #include <string>
 
 #include "dd_internal.h"
+#include "dd_trace.h"
 
 namespace {
 
@@ -343,9 +347,17 @@ dd_status build_schedule(dd_plan_s* p) {
             block_span(p, db, &p->blk_lo);
             build_records(p);
             p->dev_dirty = true;
+            dd::logf(1, "plan %d trials x %d channels: %s, %d trials per CTA, %d channels per stage, "
+                        "staged rows of %d elements, difference rows of %d, record %d bytes, %zu bytes "
+                        "of shared memory",
+                     p->ndm, p->nchan,
+                     p->rl ? (p->rl_b ? "run-length sums with shared difference rows" : "run-length sums")
+                           : (p->pair ? "fp32 pair units" : "exact integer sums"),
+                     db, p->cs, p->lcap, p->blen, p->rec_bytes, dd::dedisp_smem_for(p));
             return DD_OK;
         }
     }
+    dd::logf(1, "plan %d trials x %d channels: no CTA shape fits in shared memory", p->ndm, p->nchan);
     return DD_ERR_UNSUPPORTED;
 }
 
@@ -466,6 +478,24 @@ dd_status build_adjoint_plan(dd_plan_s* p) {
     p->adj_stale = false;
     p->adj_w_stale = true;
     return DD_OK;
+}
+
+int log_level() {
+    static const int level = [] {
+        const char* v = std::getenv("DD_LOG");
+        return v ? std::atoi(v) : 0;
+    }();
+    return level;
+}
+
+void logf(int level, const char* fmt, ...) {
+    if (log_level() < level) return;
+    char line[512];
+    va_list ap;
+    va_start(ap, fmt);
+    std::vsnprintf(line, sizeof line, fmt, ap);
+    va_end(ap);
+    std::fprintf(stderr, "[dd] %s\n", line);
 }
 
 dd_status cuda_status(cudaError_t e) {
@@ -732,6 +762,8 @@ static bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 
 dd_status dd_dedisperse(dd_plan_t p, const void* in, int64_t in_ld, int64_t t_offset,
                         int64_t nsamp, void* out, int64_t out_ld, void* stream) {
+    DD_TRACE("dd_dedisperse");
+    dd::logf(2, "dd_dedisperse: %d trials, t_offset %lld, nsamp %lld", p ? p->ndm : 0, (long long)t_offset, (long long)nsamp);
     if (!p || !in || !out) return DD_ERR_ARG;
     const int64_t esz = p->band.in_type == DD_U8 ? 1 : 4;
     if (nsamp <= 0) nsamp = p->band.nsamp;
@@ -749,6 +781,7 @@ dd_status dd_dedisperse(dd_plan_t p, const void* in, int64_t in_ld, int64_t t_of
 
 dd_status dd_channel_stats(dd_plan_t p, const void* in, int64_t in_ld, int64_t t_offset,
                            int64_t nsamp, double* mean, double* sd, void* stream) {
+    DD_TRACE("dd_channel_stats");
     if (!p || !in || !mean || !sd) return DD_ERR_ARG;
     if (nsamp <= 0) nsamp = p->band.nsamp;
     if (t_offset < 0 || nsamp < 1 || t_offset + nsamp > in_ld) return DD_ERR_ARG;
@@ -761,6 +794,8 @@ dd_status dd_boxcar_snr(dd_plan_t p, const void* x, int64_t ld, int64_t t_len,
                         const int32_t* widths, int32_t nw, const double* mean,
                         const double* sd, float* peak, int32_t* arg, float thresh,
                         dd_candidate* cands, int32_t cap, int32_t* ncands, void* stream) {
+    DD_TRACE("dd_boxcar_snr");
+    dd::logf(2, "dd_boxcar_snr: %d trials, %lld samples, %d widths", p ? p->ndm : 0, (long long)t_len, nw);
     if (!p || !x || !widths || nw < 1 || !mean || !sd || !peak || !arg) return DD_ERR_ARG;
     if (t_len < 1 || ld < t_len || t_len > INT32_MAX) return DD_ERR_ARG;
     if (cands && (!ncands || cap < 0)) return DD_ERR_ARG;
@@ -777,6 +812,9 @@ dd_status dd_boxcar_snr(dd_plan_t p, const void* x, int64_t ld, int64_t t_len,
 dd_status dd_backward(dd_plan_t p, const float* in, int64_t in_ld, int64_t t_offset,
                       int64_t nsamp, const float* g, int64_t gld, float* gw, float* gin,
                       int64_t gin_ld, void* stream) {
+    DD_TRACE("dd_backward");
+    dd::logf(2, "dd_backward: %d trials, nsamp %lld, weight gradient %s, input gradient %s", p ? p->ndm : 0,
+             (long long)nsamp, gw ? "yes" : "no", gin ? "yes" : "no");
     if (!p || !in || !g) return DD_ERR_ARG;
     if (p->band.in_type != DD_F32) return DD_ERR_UNSUPPORTED;
     if (nsamp <= 0) nsamp = p->band.nsamp;
@@ -859,6 +897,7 @@ std::map<std::string, std::pair<int, int>> read_cache(const char* path) {
 
 dd_status dd_plan_autotune(dd_plan_t p, const void* d_in, int64_t in_ld, void* d_out,
                            int64_t out_ld, const char* cache_path, float* best_ms, void* stream) {
+    DD_TRACE("dd_plan_autotune");
     if (!p || !d_in || !d_out) return DD_ERR_ARG;
     cudaStream_t s = (cudaStream_t)stream;
     const std::string key = tune_key(p);
@@ -867,6 +906,8 @@ dd_status dd_plan_autotune(dd_plan_t p, const void* d_in, int64_t in_ld, void* d
     auto hit = cache.find(key);
     if (hit != cache.end() && dd_plan_set_schedule(p, hit->second.first, hit->second.second) == DD_OK) {
         if (best_ms) *best_ms = -1.0f;
+        dd::logf(1, "autotune %s: cached schedule (%d time chunks, %d channels per stage)", key.c_str(),
+                 hit->second.first, hit->second.second);
         return DD_OK;
     }
     const bool u8 = stage_esz(p) == 1;
@@ -915,6 +956,8 @@ dd_status dd_plan_autotune(dd_plan_t p, const void* d_in, int64_t in_ld, void* d
     if (build_schedule_fixed(p, best_nch, best_cs) != DD_OK) build_schedule_fixed(p, orig_nch, orig_cs);
     if (st != DD_OK) return st;
     if (best_ms) *best_ms = best;
+    dd::logf(1, "autotune %s: %d time chunks, %d channels per stage, %.3f ms (default %d, %d)", key.c_str(),
+             best_nch, best_cs, best, orig_nch, orig_cs);
     if (cache_path) {
         std::ofstream f(cache_path, std::ios::app);
         if (f) f << key << " " << best_nch << " " << best_cs << " " << best << "\n";

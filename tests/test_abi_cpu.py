@@ -305,3 +305,22 @@ def test_detector_profiles_match_oracle(lib, kind):
                   for c in range(C))
         den = math.sqrt(float((w.astype(np.float64) ** 2).sum()))
         assert num / den == pytest.approx(snr, rel=1e-6)
+
+
+def test_dd_log_reports_plan_decisions(lib):
+    """DD_LOG=1 makes the library log its plan decisions to stderr; without it, nothing."""
+    import subprocess
+    import sys
+    code = ("import sys; sys.path.insert(0, %r)\n"
+            "import numpy as np, paper_1301_3968_gb300 as dd\n"
+            "p = dd.Plan(dd.Band(64, 1200., 4.6875, 1.0, 4096, 'u8'), np.linspace(0, 500, 128))\n"
+            "p.set_method('runlength')\n" % ROOT)
+    env = dict(os.environ, DD_LOG="1")
+    on = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+    assert on.returncode == 0, on.stderr
+    lines = [ln for ln in on.stderr.splitlines() if ln.startswith("[dd] ")]
+    assert any("exact integer sums" in ln and "128 trials x 64 channels" in ln for ln in lines), lines
+    assert any("run-length sums" in ln for ln in lines), lines
+    env.pop("DD_LOG")
+    off = subprocess.run([sys.executable, "-c", code], env=env, capture_output=True, text=True, timeout=120)
+    assert off.returncode == 0 and "[dd]" not in off.stderr

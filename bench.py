@@ -253,7 +253,8 @@ def run_gpu(args):
             "sms": torch.cuda.get_device_properties(dev).multi_processor_count}
     extras = None
     if rank == 0 and ws == 1 and not args.no_extras:
-        extras = {"fwd_bwd": diff_extra(dd, dev, flush, stream),
+        extras = {"plain": plain_extra(dd, dev, flush, stream),
+                  "fwd_bwd": diff_extra(dd, dev, flush, stream),
                   "batched": batched_extra(dd, dev, flush, stream, iadd_tops=live["iadd_tops"]),
                   "large_lowband": large_extra(dd, dev, flush, stream, iadd_tops=live["iadd_tops"],
                                                sms=live["sms"])}
@@ -403,6 +404,34 @@ def diff_extra(dd, dev, flush, stream, reps=5):
         "bwd_w_tflops": flops / (bw_ms / 1e3) / 1e12,
         "bwd_in_tflops": flops / (bi_ms / 1e3) / 1e12,
     }
+
+
+def plain_extra(dd, dev, flush, stream, reps=20):
+    """Plain configuration: 64 channels over 1200-1500 MHz, dt 1 ms, 4096 uint8 samples,
+    128 trial DMs 0-500, unit weights (exact integer sums), boxcar widths 1-16.  About
+    2 MB of data: launch- and latency-bound, reported but not held to a roofline."""
+    import torch
+    import synth
+    cfg = synth.make_plain()
+    b = cfg["band"]
+    plan = dd.Plan(dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, cfg["nsamp"], "u8"), cfg["dms"])
+    x = torch.from_numpy(cfg["data"]).to(dev)
+    out = torch.empty((plan.ndm, cfg["nsamp"] - plan.d_max), dtype=torch.int32, device=dev)
+    widths = np.arange(1, 17, dtype=np.int32)
+
+    def step():
+        m, s = plan.channel_stats(x, nsamp=cfg["nsamp"])
+        plan.dedisperse(x, nsamp=cfg["nsamp"], out=out)
+        plan.boxcar_snr(out, widths, m, s)
+
+    dd_ms = _ev_time(lambda: plan.dedisperse(x, nsamp=cfg["nsamp"], out=out), reps, flush, stream)
+    st_ms = _ev_time(step, reps, flush, stream)
+    units = float(plan.ndm) * out.shape[1]
+    plan.close()
+    return {"workload": "plain: 64 ch 1200-1500 MHz, dt 1 ms, 4096 uint8 samples, 128 trial DMs 0-500, "
+                        "unit weights, int32 out, boxcar widths 1-16",
+            "dedisp_ms": dd_ms, "step_ms": st_ms, "dedisp_value": units / (dd_ms / 1e3),
+            "step_value": units / (st_ms / 1e3), "unit": UNIT}
 
 
 def _batch_case(dd, dev, flush, stream, cfg, reps, tune, widths, graph=True):
@@ -762,7 +791,9 @@ def run_only(args):
     torch.cuda.set_device(dev)
     flush = torch.empty(256 << 20, dtype=torch.uint8, device=dev)
     stream = torch.cuda.current_stream()
-    if args.only == "fwd_bwd":
+    if args.only == "plain":
+        r = plain_extra(dd, dev, flush, stream)
+    elif args.only == "fwd_bwd":
         r = diff_extra(dd, dev, flush, stream)
     elif args.only == "batched":
         r = batched_extra(dd, dev, flush, stream, iadd_tops=dd.alu_peak("iadd") / 1e12)
@@ -786,7 +817,7 @@ def main():
                     help="profiling case: this many consecutive trials from the middle of the "
                          "4096-trial list")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--only", default=None, choices=["fwd_bwd", "batched", "large_lowband"],
+    ap.add_argument("--only", default=None, choices=["plain", "fwd_bwd", "batched", "large_lowband"],
                     help="run one extra measurement alone (profiling)")
     ap.add_argument("--large-nsamp", type=int, default=1 << 20)
     ap.add_argument("--large-ndm", type=int, default=8192)

@@ -23,28 +23,28 @@ namespace {
 __global__ void __launch_bounds__(256) k_fused_seam(const FusedArgs f, int32_t L, int32_t t_out,
                                                     int32_t ndm, int32_t tpc) {
     extern __shared__ uint32_t pf[];  // [2C + 1]
-    const int k = blockIdx.x + 1, local = blockIdx.y;
-    const int64_t item = f.starts[k];
+    const int kb = blockIdx.x + 1, local = blockIdx.y;  // the boundary between parts kb - 1 and kb
+    const int64_t item = f.starts[kb];
     const int blk = (int)(item / f.tiles);
     const int tx = (int)(item - (int64_t)blk * f.tiles);
     const int d = blk * tpc + local;
     if (tx == 0 || d >= ndm) return;  // a part boundary between blocks has no seam
     const int C = f.C;
-    const int32_t* v = f.seam + ((int64_t)k * tpc + local) * 2 * C;
-    const int64_t B = (int64_t)tx * L;  // first output of part k in this block
+    const int32_t* v = f.seam + ((int64_t)kb * tpc + local) * 2 * C;
+    const int64_t B = (int64_t)tx * L;  // first output of part kb in this block
     const int tid = threadIdx.x, lane = tid & 31;
     if (tid < 32) {
         uint32_t carry = 0;
         if (lane == 0) pf[0] = 0;
         for (int k0 = 0; k0 < 2 * C; k0 += 32) {
-            const int k = k0 + lane;
-            uint32_t x = k < 2 * C ? (uint32_t)v[k] : 0u;
+            const int kl = k0 + lane;
+            uint32_t x = kl < 2 * C ? (uint32_t)v[kl] : 0u;
 #pragma unroll
             for (int o = 1; o < 32; o <<= 1) {
                 const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
                 if (lane >= o) x += y;
             }
-            if (k < 2 * C) pf[k + 1] = carry + x;
+            if (kl < 2 * C) pf[kl + 1] = carry + x;
             carry += __shfl_sync(0xffffffffu, x, 31);
         }
     }
@@ -55,8 +55,8 @@ __global__ void __launch_bounds__(256) k_fused_seam(const FusedArgs f, int32_t L
         int best = INT_MIN, bt = -1;
         for (int64_t t = B - w + 1; t < B; ++t) {
             if (t + w > t_out) break;
-            const int k = (int)(t - base);
-            const int val = (int)(pf[k + w] - pf[k]);
+            const int ki = (int)(t - base);
+            const int val = (int)(pf[ki + w] - pf[ki]);
             if (val > best) {
                 best = val;
                 bt = (int)t;

@@ -163,6 +163,25 @@ def test_f32_unit_and_random_weights(dd):
     _assert_f32_close(out, I, delay, taps, w, t_offset=3, nsamp=T)
 
 
+@pytest.mark.parametrize("kmax,maxdel", [(23, 3), (23, 300), (70, 5), (70, 400)])
+def test_f32_pair_windows_all_tap_passes(dd, kmax, maxdel):
+    """Pair units whose two trials start apart (both signs) and have different tap counts,
+    on every tap-pass form: one unrolled pass (<= 27 taps), two (<= 54) and the loop (more).
+    Small delay spreads give the common shifts of 0-3 samples, large ones long shifts and
+    runs that read far past the shorter trial's own taps (with zero weight)."""
+    rng = np.random.default_rng(kmax * 1000 + maxdel)
+    C, T, D = 23, 3100, 21
+    I = (rng.standard_normal((C, 3104)) * 2 - 0.5).astype(np.float32)
+    delay = rng.integers(0, maxdel + 1, size=(D, C)).astype(np.int32)
+    taps = rng.integers(1, kmax + 1, size=(D, C)).astype(np.int32)
+    w = rng.uniform(-1.0, 1.5, size=(D, C, kmax)).astype(np.float32)
+    plan = dd.Plan(dd.Band(C, 1200.0, 1.0, 1.0, T, "f32"), np.zeros(D))
+    plan.set_profiles(delay=delay, taps=taps, weights=w)
+    out = plan.dedisperse(_dev(I), t_offset=2, nsamp=T).cpu().numpy()
+    _assert_f32_close(out, I, delay, taps, w, t_offset=2, nsamp=T)
+    assert plan.device_status() == 0
+
+
 def test_u8_input_with_weights(dd):
     rng = np.random.default_rng(13)
     C, T, D, K = 20, 3000, 12, 7

@@ -102,7 +102,7 @@ def craft_workload(dd, dev, ndm=None, rank=0, ws=1):
               "weights ~ nu^-1.4 on every tap, boxcar widths 1-32"),
         plan=plan, x=x, host=cfg["data"], nsamp=t_out + info["d_max"], t_out=t_out,
         nsamp_in=cfg["nsamp"],
-        ndm=hi - lo, ndm_total=len(dms), shards=shards, dms=dms, wchan=cfg["wchan"],
+        ndm=hi - lo, ndm_total=len(dms), shards=shards, dms=dms, wchan=cfg["wchan"], band=band,
         widths=cfg["widths"], delay=delay, taps=taps, w=w, dtype="f32",
         flops=2.0 * float(taps.astype(np.int64).sum()) * t_out, ns_total=int(info["ns_total"]),
     )
@@ -276,7 +276,7 @@ def merge_check(dd, dev, W, rank, ws, plan, x, out, widths):
         return None
     peak = np.concatenate([g[0] for g in got])
     arg = np.concatenate([g[1] for g in got])
-    fp = dd.Plan(dd.Band(336, 1130.0, 1.0, 1.0, W["host"].shape[1], "f32"), W["dms"])
+    fp = dd.Plan(W["band"], W["dms"])
     _, taps = fp.tables()
     K = W["w"].shape[2]
     w = np.where(np.arange(K)[None, None, :] < taps[:, :, None], W["wchan"][None, :, None], 0.0)

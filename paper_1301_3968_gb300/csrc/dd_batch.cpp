@@ -215,7 +215,7 @@ dd_status dd_batch_bind(dd_batch_t b, const void* const* d_in, const int64_t* in
     b->out_ld.assign(out_ld, out_ld + nb);
     b->bound = true;
     b->box_bound = false;
-    dd::logf(1, "batch of %d beams (%s): %zu work items, persistent grid %d CTAs, %zu bytes of shared memory",
+    dd::log_msg(1, "batch of %d beams (%s): %zu work items, persistent grid %d CTAs, %zu bytes of shared memory",
              nb, b->rl ? "run-length sums" : (b->pair ? "fp32 pair units" : "exact integer sums"), b->items.size(),
              b->grid, b->smem);
     return DD_OK;

@@ -157,7 +157,7 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
                                           int32_t* arg, float thresh, dd_candidate* cands,
                                           int32_t cap, int32_t* ncands, void* stream) {
     DD_TRACE("dd_dedisperse_boxcar");
-    dd::logf(2, "dd_dedisperse_boxcar: %d trials, t_offset %lld, nsamp %lld, %d widths", p ? p->ndm : 0, (long long)t_offset, (long long)nsamp, nw);
+    dd::log_msg(2, "dd_dedisperse_boxcar: %d trials, t_offset %lld, nsamp %lld, %d widths", p ? p->ndm : 0, (long long)t_offset, (long long)nsamp, nw);
     using namespace dd;
     if (!p || !in || !widths || nw < 1 || !mean || !sd || !peak || !arg) return DD_ERR_ARG;
     if (cands && (!ncands || cap < 0)) return DD_ERR_ARG;

@@ -347,7 +347,7 @@ dd_status build_schedule(dd_plan_s* p) {
             block_span(p, db, &p->blk_lo);
             build_records(p);
             p->dev_dirty = true;
-            dd::logf(1, "plan %d trials x %d channels: %s, %d trials per CTA, %d channels per stage, "
+            dd::log_msg(1, "plan %d trials x %d channels: %s, %d trials per CTA, %d channels per stage, "
                         "staged rows of %d elements, difference rows of %d, record %d bytes, %zu bytes "
                         "of shared memory",
                      p->ndm, p->nchan,
@@ -357,7 +357,7 @@ dd_status build_schedule(dd_plan_s* p) {
             return DD_OK;
         }
     }
-    dd::logf(1, "plan %d trials x %d channels: no CTA shape fits in shared memory", p->ndm, p->nchan);
+    dd::log_msg(1, "plan %d trials x %d channels: no CTA shape fits in shared memory", p->ndm, p->nchan);
     return DD_ERR_UNSUPPORTED;
 }
 
@@ -488,7 +488,7 @@ int log_level() {
     return level;
 }
 
-void logf(int level, const char* fmt, ...) {
+void log_msg(int level, const char* fmt, ...) {
     if (log_level() < level) return;
     char line[512];
     va_list ap;
@@ -763,7 +763,7 @@ static bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
 dd_status dd_dedisperse(dd_plan_t p, const void* in, int64_t in_ld, int64_t t_offset,
                         int64_t nsamp, void* out, int64_t out_ld, void* stream) {
     DD_TRACE("dd_dedisperse");
-    dd::logf(2, "dd_dedisperse: %d trials, t_offset %lld, nsamp %lld", p ? p->ndm : 0, (long long)t_offset, (long long)nsamp);
+    dd::log_msg(2, "dd_dedisperse: %d trials, t_offset %lld, nsamp %lld", p ? p->ndm : 0, (long long)t_offset, (long long)nsamp);
     if (!p || !in || !out) return DD_ERR_ARG;
     const int64_t esz = p->band.in_type == DD_U8 ? 1 : 4;
     if (nsamp <= 0) nsamp = p->band.nsamp;
@@ -795,7 +795,7 @@ dd_status dd_boxcar_snr(dd_plan_t p, const void* x, int64_t ld, int64_t t_len,
                         const double* sd, float* peak, int32_t* arg, float thresh,
                         dd_candidate* cands, int32_t cap, int32_t* ncands, void* stream) {
     DD_TRACE("dd_boxcar_snr");
-    dd::logf(2, "dd_boxcar_snr: %d trials, %lld samples, %d widths", p ? p->ndm : 0, (long long)t_len, nw);
+    dd::log_msg(2, "dd_boxcar_snr: %d trials, %lld samples, %d widths", p ? p->ndm : 0, (long long)t_len, nw);
     if (!p || !x || !widths || nw < 1 || !mean || !sd || !peak || !arg) return DD_ERR_ARG;
     if (t_len < 1 || ld < t_len || t_len > INT32_MAX) return DD_ERR_ARG;
     if (cands && (!ncands || cap < 0)) return DD_ERR_ARG;
@@ -813,7 +813,7 @@ dd_status dd_backward(dd_plan_t p, const float* in, int64_t in_ld, int64_t t_off
                       int64_t nsamp, const float* g, int64_t gld, float* gw, float* gin,
                       int64_t gin_ld, void* stream) {
     DD_TRACE("dd_backward");
-    dd::logf(2, "dd_backward: %d trials, nsamp %lld, weight gradient %s, input gradient %s", p ? p->ndm : 0,
+    dd::log_msg(2, "dd_backward: %d trials, nsamp %lld, weight gradient %s, input gradient %s", p ? p->ndm : 0,
              (long long)nsamp, gw ? "yes" : "no", gin ? "yes" : "no");
     if (!p || !in || !g) return DD_ERR_ARG;
     if (p->band.in_type != DD_F32) return DD_ERR_UNSUPPORTED;
@@ -906,7 +906,7 @@ dd_status dd_plan_autotune(dd_plan_t p, const void* d_in, int64_t in_ld, void* d
     auto hit = cache.find(key);
     if (hit != cache.end() && dd_plan_set_schedule(p, hit->second.first, hit->second.second) == DD_OK) {
         if (best_ms) *best_ms = -1.0f;
-        dd::logf(1, "autotune %s: cached schedule (%d time chunks, %d channels per stage)", key.c_str(),
+        dd::log_msg(1, "autotune %s: cached schedule (%d time chunks, %d channels per stage)", key.c_str(),
                  hit->second.first, hit->second.second);
         return DD_OK;
     }
@@ -956,7 +956,7 @@ dd_status dd_plan_autotune(dd_plan_t p, const void* d_in, int64_t in_ld, void* d
     if (build_schedule_fixed(p, best_nch, best_cs) != DD_OK) build_schedule_fixed(p, orig_nch, orig_cs);
     if (st != DD_OK) return st;
     if (best_ms) *best_ms = best;
-    dd::logf(1, "autotune %s: %d time chunks, %d channels per stage, %.3f ms (default %d, %d)", key.c_str(),
+    dd::log_msg(1, "autotune %s: %d time chunks, %d channels per stage, %.3f ms (default %d, %d)", key.c_str(),
              best_nch, best_cs, best, orig_nch, orig_cs);
     if (cache_path) {
         std::ofstream f(cache_path, std::ios::app);

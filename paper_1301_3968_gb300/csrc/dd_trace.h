@@ -4,7 +4,7 @@
 // scope, so a timeline tool (Nsight Systems, or ncu's NVTX filter) shows every library
 // call around its kernels; with no tool attached an NVTX call is a cheap no-op.
 //
-// dd::logf(level, ...) writes one line "[dd] ..." to stderr when the DD_LOG environment
+// dd::log_msg(level, ...) writes one line "[dd] ..." to stderr when the DD_LOG environment
 // variable (read once) is at least `level`: 1 = plan decisions (tap-sum method, CTA
 // shape, stage size, staged row length, shared memory), autotuner results and batch
 // bindings; 2 = also every device call with its sizes.
@@ -22,7 +22,7 @@ struct TraceRange {
 };
 
 int log_level();
-void logf(int level, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
+void log_msg(int level, const char* fmt, ...) __attribute__((format(printf, 2, 3)));
 
 }  // namespace dd
 

@@ -213,3 +213,51 @@ def test_batch_refuses_mixed_methods(dd):
     beams[1][0].set_method("direct")
     with pytest.raises(dd.DDError):
         dd.Batch([p for p, _, _, _ in beams])
+
+
+def test_batched_fp32_weighted_equals_per_beam_and_oracle(dd):
+    """fp32 weighted beams (pair units with each trial's own run in the shared window) in
+    one persistent launch: bit for bit the per-beam launches, sampled rows within the fp32
+    tolerance of the oracle, and the graph replay repeats them."""
+    import torch
+    rng = np.random.default_rng(71)
+    b = synth.CRAFT_BAND
+    beams = []
+    for i in range(4):
+        T = int(rng.integers(5000, 9000)) // 4 * 4
+        D = int(rng.integers(20, 70))
+        band = dd.Band(b.nchan, b.f_lo_mhz, b.df_mhz, b.dt_ms, T, "f32")
+        dms, _ = dd.trial_dms(band, 0.0, float(rng.uniform(300.0, 1500.0)), D, tau_av_ms=1.0)
+        plan = dd.Plan(band, dms)
+        _, taps = plan.tables()
+        K = int(taps.max())
+        w = (rng.uniform(0.2, 1.5, size=(D, b.nchan, K))
+             * (np.arange(K)[None, None, :] < taps[:, :, None])).astype(np.float32)
+        plan.set_profiles(weights=w)
+        data = rng.standard_normal((b.nchan, T)).astype(np.float32)
+        x = torch.from_numpy(data).cuda()
+        out = torch.zeros((D, T - plan.d_max), dtype=torch.float32, device="cuda")
+        beams.append((plan, x, out, data, w))
+    batch = dd.Batch([p for p, _, _, _, _ in beams])
+    batch.bind([x for _, x, _, _, _ in beams], [o for _, _, o, _, _ in beams])
+    batch.dedisperse()
+    torch.cuda.synchronize()
+    for plan, x, o, data, w in beams:
+        ref_ = plan.dedisperse(x, nsamp=plan.band.nsamp)
+        assert torch.equal(o, ref_)
+        delay, taps = plan.tables()
+        rows = [0, plan.ndm // 2, plan.ndm - 1]
+        want = oracle.c_dedisperse(data, delay, taps, w=w, nsamp=plan.band.nsamp, rows=rows)
+        scale = oracle.c_abs_scale(data, delay, taps, w=w, nsamp=plan.band.nsamp, rows=rows)
+        assert (np.abs(o.cpu().numpy()[rows] - want) <= 1e-5 * scale + 1e-30).all()
+    before = [o.clone() for _, _, o, _, _ in beams]
+    s = torch.cuda.Stream()
+    with torch.cuda.stream(s):
+        batch.capture(s)
+        for _, _, o, _, _ in beams:
+            o.zero_()
+        batch.replay(s)
+    s.synchronize()
+    for b_, (_, _, o, _, _) in zip(before, beams):
+        assert torch.equal(b_, o)
+    batch.close()

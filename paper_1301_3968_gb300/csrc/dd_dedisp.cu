@@ -653,19 +653,29 @@ __device__ __forceinline__ unsigned char* pipeline_area(unsigned char* smem, siz
     return smem + smem_bytes - (size_t)(nbuf * 8 + 2 * nbuf * 4);
 }
 
-// Grid: time tiles along x and trial blocks along y, except on the run-length path,
-// where trial blocks run along x so that the CTAs resident together share time tiles
-// and each tile's prefix rows come from L2 for all trial blocks (instead of every trial
-// block reading the whole prefix array from DRAM).
+// Order of the tiles.  Run-length path: trial blocks along x, time tiles along y, so that
+// the CTAs resident together share time tiles and each tile's prefix rows come from L2
+// for all trial blocks (instead of every trial block reading the whole prefix array from
+// DRAM).  Other paths: the grid is (time tiles, trial blocks) and runs in groups of
+// kGroupBlocks trial blocks, blocks fastest within a group and then time tiles, so that
+// each group reads the input about once from DRAM (and its blocks' stage records from
+// L2) instead of each trial block re-reading the input.
+constexpr int kGroupBlocks = 16;
 template <typename TIN, bool PAIR, int NBUF, int SHORT>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ TileState ts;
     if (threadIdx.x == 0) init_pipeline<NBUF>(pipeline_area(smem, a.smem_bytes, NBUF), ts);
     __syncthreads();
-    constexpr bool BLK_X = std::is_same<TIN, uint32_t>::value;
-    dedisp_tile<TIN, PAIR, NBUF, false, SHORT>(a, smem, BLK_X ? blockIdx.x : blockIdx.y,
-                                               BLK_X ? blockIdx.y : blockIdx.x, ts);
+    if constexpr (std::is_same<TIN, uint32_t>::value) {
+        dedisp_tile<TIN, PAIR, NBUF, false, SHORT>(a, smem, blockIdx.x, blockIdx.y, ts);
+    } else {
+        const int ntile = (int)gridDim.x, nblk = (int)gridDim.y;
+        const int L = (int)blockIdx.y * ntile + (int)blockIdx.x;  // < 2^31: grid.y <= 65535
+        const int g = L / (kGroupBlocks * ntile), r = L - g * kGroupBlocks * ntile;
+        const int gb = min(kGroupBlocks, nblk - g * kGroupBlocks);
+        dedisp_tile<TIN, PAIR, NBUF, false, SHORT>(a, smem, g * kGroupBlocks + r % gb, r / gb, ts);
+    }
 }
 
 // Persistent form: each CTA takes work items (beam, trial block, time tile) from an
@@ -757,6 +767,7 @@ dd_status run(DedispArgs a, cudaStream_t s) {
     const bool blk_x = std::is_same<TIN, uint32_t>::value;
     dim3 grid(blk_x ? nblk : ntile, blk_x ? ntile : nblk, (unsigned)a.nsplit);
     if (grid.y > 65535 || a.nsplit < 1 || a.nsplit > 64) return DD_ERR_UNSUPPORTED;
+    if ((int64_t)grid.x * grid.y >= INT32_MAX) return DD_ERR_UNSUPPORTED;  // the tile index is int
     kern<<<grid, kWarps * 32, smem, s>>>(a);
     return cuda_status(cudaGetLastError());
 }

@@ -23,7 +23,7 @@ LIB_DEBUG = os.path.join(OUT_DIR, "libdd_debug.so")
 ARCH = ["-gencode", "arch=compute_103a,code=sm_103a"]
 SOURCES = ["dd_plan.cpp", "dd_dedisp.cu", "dd_boxcar.cu", "dd_adjoint.cu", "dd_noalloc.cu", "dd_batch.cpp",
            "dd_peak.cu", "dd_select.cpp", "dd_fused.cu"]
-DEBUG_SOURCES = ["dd_dedisp.cu", "dd_boxcar.cu"]   # the kernels with bounds checks
+DEBUG_SOURCES = ["dd_dedisp.cu", "dd_fused.cu", "dd_boxcar.cu"]   # the kernels with bounds checks
 
 
 def _nvcc() -> str:

@@ -11,10 +11,66 @@
 #include <cstdint>
 
 #include "dd_internal.h"
+#include "dd_tile.cuh"
 #include "dd_trace.h"
 
 namespace dd {
 namespace {
+
+// Fused dedispersion + boxcar scan, one CTA per part: part s walks the
+// items (trial block, time tile) starts[s] .. starts[s + 1] - 1 in order (block-major),
+// a strip per trial block it touches.  CTA i takes part order[i].
+template <typename TIN, int NBUF, int SHORT>
+__global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_fused(DedispArgs a, const FusedArgs f) {
+    extern __shared__ __align__(128) unsigned char smem[];
+    __shared__ TileState ts;
+    if (threadIdx.x == 0) init_pipeline<NBUF>(pipeline_area(smem, a.smem_bytes, NBUF), ts);
+    __syncthreads();
+    // the tile's strip, kept in shared memory so that no per-strip state stays live in
+    // registers across the channel sums (thread 0 writes it before each tile; the tile's
+    // barriers order it, and the epilogue's last barrier ends its readers)
+    __shared__ fused::FusedTile ft;
+    const int s = (int)f.order[blockIdx.x];
+    const int i0 = (int)f.starts[s], i1 = (int)f.starts[s + 1];  // items < 2^31 (host check)
+    for (int it = i0; it < i1; ++it) {
+        const int blk = it / f.tiles;
+        const int tx = it - blk * f.tiles;
+        if (threadIdx.x == 0) {
+            const int L = chunk_t(false) * a.nch;
+            const int tpc = kWarps / a.nch * upw<TIN>();
+            const int tx0 = it - tx <= i0 ? i0 - (it - tx) : 0;                    // strip start
+            const int tx1 = i1 - (it - tx) < f.tiles ? i1 - (it - tx) : f.tiles;  // strip end
+            ft.first = tx == tx0;
+            ft.last = tx == tx1 - 1;
+            ft.s1 = min((int64_t)tx1 * L, (int64_t)a.t_out);
+            ft.carry = f.carry + (int64_t)s * tpc * f.C;
+            ft.seam_in = tx0 > 0 ? f.seam + (int64_t)s * tpc * 2 * f.C : nullptr;
+            ft.seam_out = tx1 < f.tiles ? f.seam + (int64_t)(s + 1) * tpc * 2 * f.C : nullptr;
+        }
+        if (!dedisp_tile<TIN, false, NBUF, true, SHORT, true>(a, smem, blk, tx, ts, &f, &ft)) break;
+    }
+}
+
+template <typename TIN, int NBUF, int SHORT>
+dd_status run_fused(DedispArgs a, const FusedArgs& f, size_t smem, cudaStream_t s) {
+    a.smem_bytes = (uint32_t)smem;
+    auto kern = k_dedisp_fused<TIN, NBUF, SHORT>;
+    cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
+    if (e != cudaSuccess) return cuda_status(e);
+    kern<<<(unsigned)f.nparts, kWarps * 32, smem, s>>>(a, f);
+    return cuda_status(cudaGetLastError());
+}
+
+template <typename TIN, int NBUF, int SHORT>
+int fused_bps(size_t smem) {
+    int n = 0;
+    auto kern = k_dedisp_fused<TIN, NBUF, SHORT>;
+    if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
+        return 0;
+    if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kWarps * 32, smem) != cudaSuccess) return 0;
+    return n;
+}
+
 
 // Windows that cross the boundary between parts k-1 and k inside a trial block (start
 // t < B < t + w, t + w <= t_out), one CTA per (boundary, trial of the block): the 2C
@@ -149,6 +205,26 @@ void aligned_parts(int64_t nblk, int tiles, int nseg, std::vector<int64_t>* star
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 
 }  // namespace
+
+size_t fused_smem_for(const dd_plan_s* p, int rowlen, int C) {
+    const int nbuf = p->rl ? kStagesRl : kStagesInt;
+    const int spill = p->rl ? kWarps * (kRlUnits - 1) * chunk_t(false) : 0;
+    const size_t rows = (size_t)(fused_rows_ints(kWarps / p->nch, rowlen, C) + spill) * 4 + nbuf * 8 + 2 * nbuf * 4;
+    return (std::max(dedisp_smem_for(p), rows) + 15) & ~(size_t)15;
+}
+
+int fused_blocks_per_sm(const dd_plan_s* p, size_t smem) {
+    if (p->rl) return p->rl_b ? fused_bps<uint32_t, kStagesRl, 1>(smem) : fused_bps<uint32_t, kStagesRl, 0>(smem);
+    return p->kmax <= kRInt ? fused_bps<uint8_t, kStagesInt, 1>(smem) : fused_bps<uint8_t, kStagesInt, 0>(smem);
+}
+
+dd_status launch_dedisperse_fused(const dd_plan_s* p, DedispArgs a, const FusedArgs& f, size_t smem,
+                                  cudaStream_t s) {
+    if (p->rl)
+        return p->rl_b ? run_fused<uint32_t, kStagesRl, 1>(a, f, smem, s) : run_fused<uint32_t, kStagesRl, 0>(a, f, smem, s);
+    return p->kmax <= kRInt ? run_fused<uint8_t, kStagesInt, 1>(a, f, smem, s)
+                            : run_fused<uint8_t, kStagesInt, 0>(a, f, smem, s);
+}
 }  // namespace dd
 
 extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t in_ld, int64_t t_offset,

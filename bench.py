@@ -253,7 +253,8 @@ def run_gpu(args):
             "sms": torch.cuda.get_device_properties(dev).multi_processor_count}
     extras = None
     if rank == 0 and ws == 1 and not args.no_extras:
-        extras = {"plain": plain_extra(dd, dev, flush, stream),
+        extras = {"craft_fused": craft_fused_extra(W, plan, x, out, widths, flush, stream, ms),
+                  "plain": plain_extra(dd, dev, flush, stream),
                   "fwd_bwd": diff_extra(dd, dev, flush, stream),
                   "batched": batched_extra(dd, dev, flush, stream, iadd_tops=live["iadd_tops"]),
                   "large_lowband": large_extra(dd, dev, flush, stream, iadd_tops=live["iadd_tops"],
@@ -371,6 +372,30 @@ def _ev_time(fn, reps, flush, stream):
         torch.cuda.synchronize()
         ts.append(e0.elapsed_time(e1))
     return sum(ts) / len(ts)
+
+
+def craft_fused_extra(W, plan, x, out, widths, flush, stream, step_ms, reps=10):
+    """The CRAFT-like step with the boxcar scan fused into the dedispersion CTAs
+    (dd_dedisperse_boxcar: the 4096 x 60261 fp32 series is never stored): its time against
+    the unfused step's, and its peak S/N and times against the unfused step's, bit for bit."""
+    import torch
+
+    def fstep():
+        mean, sd = plan.channel_stats(x, nsamp=W["nsamp_in"])
+        return plan.dedisperse_boxcar(x, widths, mean, sd, nsamp=W["nsamp"])
+
+    ms = _ev_time(fstep, reps, flush, stream)
+    pf, af, _ = fstep()
+    mean, sd = plan.channel_stats(x, nsamp=W["nsamp_in"])
+    plan.dedisperse(x, nsamp=W["nsamp"], out=out)
+    pu, au, _ = plan.boxcar_snr(out, widths, mean, sd, t_len=W["t_out"])
+    units = float(W["ndm"]) * W["t_out"]
+    return {"step_ms": ms, "value": units / (ms / 1e3), "unit": "DM-trial\u00b7samples/s",
+            "unfused_step_ms": step_ms, "fused_over_unfused": ms / step_ms if step_ms else None,
+            "peaks_equal_unfused_bitwise": bool(torch.equal(pf.view(torch.int32), pu.view(torch.int32))
+                                                and torch.equal(af, au)),
+            "status": plan.device_status(),
+            "series_bytes_not_stored": int(W["ndm"]) * W["t_out"] * 4}
 
 
 def diff_extra(dd, dev, flush, stream, reps=5):
@@ -811,6 +836,17 @@ def run_only(args):
     stream = torch.cuda.current_stream()
     if args.only == "plain":
         r = plain_extra(dd, dev, flush, stream)
+    elif args.only == "craft_fused":
+        W = craft_workload(dd, dev, args.ndm)
+        out = torch.empty((W["ndm"], W["t_out"]), dtype=torch.float32, device=dev)
+        plan, x = W["plan"], W["x"]
+
+        def ustep():
+            mean, sd = plan.channel_stats(x, nsamp=W["nsamp_in"])
+            plan.dedisperse(x, nsamp=W["nsamp"], out=out)
+            return plan.boxcar_snr(out, W["widths"], mean, sd, t_len=W["t_out"])
+
+        r = craft_fused_extra(W, plan, x, out, W["widths"], flush, stream, _ev_time(ustep, 10, flush, stream))
     elif args.only == "fwd_bwd":
         r = diff_extra(dd, dev, flush, stream)
     elif args.only == "batched":
@@ -835,7 +871,7 @@ def main():
                     help="profiling case: this many consecutive trials from the middle of the "
                          "4096-trial list")
     ap.add_argument("--no-e2e", action="store_true")
-    ap.add_argument("--only", default=None, choices=["plain", "fwd_bwd", "batched", "large_lowband"],
+    ap.add_argument("--only", default=None, choices=["plain", "craft_fused", "fwd_bwd", "batched", "large_lowband"],
                     help="run one extra measurement alone (profiling)")
     ap.add_argument("--large-nsamp", type=int, default=1 << 20)
     ap.add_argument("--large-ndm", type=int, default=8192)

@@ -199,16 +199,21 @@ dd_status dd_boxcar_snr_noalloc(dd_plan_t plan, const void* d_series, int64_t ld
  * results as dd_dedisperse(plan, d_in, in_ld, t_offset, nsamp, x, ...) followed by
  * dd_boxcar_snr(plan, x, ..., nsamp - d_max, widths, ...), bit for bit, but the
  * dedispersed series x is never written to device memory: the dedispersion CTAs scan
- * their finished tiles in shared memory (C = wmax - 1 outputs per tile and trial are
- * carried to the CTA's next tile, and 2C per part boundary go to a seam pass, through
- * plan-owned scratch).  For a caller that only needs the detections.
- * Limits (DD_ERR_UNSUPPORTED otherwise): integer plans (uint8 input, unit weights; both
- * tap-sum methods), contiguous widths (w_j = w_0 + j), wmax - 1 <= 992 * nch (the
- * schedule's tile), and nsamp <= 2^24 on the run-length path.  Every boxcar sum of
- * x - o_d (o_d the normaliser's per-trial integer offset) must fit int32: the kernel
- * checks wmax * |x - o_d| < 2^31 per output and otherwise records DD_ERR_OVERFLOW in
- * the plan's device status word (dd_get_device_status), the results of that call being
- * undefined; dd_boxcar_snr on the stored series handles that case with 64-bit sums.
+ * their finished tiles in shared memory (C outputs per tile and trial are carried to
+ * the CTA's next tile, and 2C per part boundary go to a seam pass, through plan-owned
+ * scratch).  For a caller that only needs the detections.
+ * Every plan kind is taken:
+ *   - integer plans (uint8 input, unit weights; both tap-sum methods): C = wmax - 1.
+ *     Every boxcar sum of x - o_d (o_d the normaliser's per-trial integer offset) must
+ *     fit int32: the kernel checks wmax * |x - o_d| < 2^31 per output and otherwise
+ *     records DD_ERR_OVERFLOW in the plan's device status word (dd_get_device_status),
+ *     the results of that call being undefined; dd_boxcar_snr on the stored series
+ *     handles that case with 64-bit sums.
+ *   - fp32 plans (fp32 input, or weighted uint8): the fp32 sums of dd_boxcar_snr, whose
+ *     prefix chains start every 31 outputs, formed the same way; C = wmax + 29.
+ * Limits (DD_ERR_UNSUPPORTED otherwise): contiguous widths (w_j = w_0 + j), C <= the
+ * schedule's tile (992 * nch outputs on the integer paths, 864 * nch on fp32 plans), and
+ * nsamp <= 2^24 on the run-length path.
  * Other arguments, outputs and errors as dd_dedisperse and dd_boxcar_snr.  Allocates
  * plan-owned device scratch when the sizes grow: the merged maxima (8 bytes per trial
  * and width) and, per part, its carried outputs and seams (12 C bytes per trial of a

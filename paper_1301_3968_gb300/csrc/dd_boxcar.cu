@@ -216,7 +216,7 @@ __device__ __forceinline__ int lowest<int>() { return INT_MIN; }
 template <>
 __device__ __forceinline__ long long lowest<long long>() { return LLONG_MIN; }
 
-constexpr int kBoxS = 31;  // samples per thread segment (odd: conflict-free)
+constexpr int kBoxS = kBoxSeg;  // samples per thread segment
 constexpr int kBoxG = 16;  // widths per CTA
 
 // grid (width groups, trials).  The CTA walks the row in chunks of 256*S samples;
@@ -381,16 +381,30 @@ __device__ __forceinline__ void run_segment(const TX* xl, TX o, int w0, int t0, 
     win[0] = q;
 #pragma unroll
     for (int j = 1; j < G; ++j) win[j] = win[j - 1] + to_acc<TX, TB>((TX)(xl[w0 + j - 1] - o));
+    // two starts per step, their sums merged with one three-input max
 #pragma unroll
-    for (int s = 0; s < S; ++s) {
+    for (int s = 0; s < S; s += 2) {
+        TB v0[G];
 #pragma unroll
         for (int j = 0; j < G; ++j) {
-            TB v = (TB)(win[(j + s) % G] - p);
-            if (!FULL) v = (t0 + s + w0 + j <= t_len) ? v : lowest<TB>();
-            seg[j] = max(seg[j], v);
+            v0[j] = (TB)(win[(j + s) % G] - p);
+            if (!FULL) v0[j] = (t0 + s + w0 + j <= t_len) ? v0[j] : lowest<TB>();
         }
         p += to_acc<TX, TB>((TX)(xl[s] - o));
         win[s % G] = win[(s + G - 1) % G] + to_acc<TX, TB>((TX)(xl[s + w0 + G - 1] - o));
+        if (s + 1 < S) {
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                TB v = (TB)(win[(j + s + 1) % G] - p);
+                if (!FULL) v = (t0 + s + 1 + w0 + j <= t_len) ? v : lowest<TB>();
+                seg[j] = max3(seg[j], v0[j], v);
+            }
+            p += to_acc<TX, TB>((TX)(xl[s + 1] - o));
+            win[(s + 1) % G] = win[(s + G) % G] + to_acc<TX, TB>((TX)(xl[s + w0 + G] - o));
+        } else {
+#pragma unroll
+            for (int j = 0; j < G; ++j) seg[j] = max(seg[j], v0[j]);
+        }
     }
 }
 

@@ -1,12 +1,13 @@
 // Dedispersion fused with the boxcar S/N scan (eq. p_dedisp followed by eq. snr with
-// boxcars, Sec. 5) for integer plans: the dedispersed series never leaves the chip.
-// The dedispersion CTAs scan their tiles in shared memory (dd_fused_scan.cuh); this
-// file holds the launcher, the pass over the windows that cross strip boundaries and
-// the pass that turns the merged maxima into S/N.  Results equal dd_dedisperse followed
-// by dd_boxcar_snr bit for bit: both take the maximum of the same exact integer sums
-// around the same per-trial offset, with the earliest start, and convert it with the
-// same normaliser.
+// boxcars, Sec. 5): the dedispersed series never leaves the chip.  The dedispersion
+// CTAs scan their tiles in shared memory (dd_fused_scan.cuh); this file holds the fused
+// kernel and its launcher, the pass over the windows that strip boundaries cut and the
+// pass that turns the merged maxima into S/N.  Results equal dd_dedisperse followed by
+// dd_boxcar_snr bit for bit: integer plans take the maximum of the same exact sums
+// around the same per-trial offset, fp32 plans the same fp32 prefix-chain sums as the
+// unfused fp32 scan, both with the earliest start, converted by the same normaliser.
 #include <algorithm>
+#include <cfloat>
 #include <climits>
 #include <cstdint>
 
@@ -19,8 +20,9 @@ namespace {
 
 // Fused dedispersion + boxcar scan, one CTA per part: part s walks the
 // items (trial block, time tile) starts[s] .. starts[s + 1] - 1 in order (block-major),
-// a strip per trial block it touches.  CTA i takes part order[i].
-template <typename TIN, int NBUF, int SHORT>
+// a strip per trial block it touches.  CTA i takes part order[i].  PAIR: fp32 pair
+// units (fp32 sums, two trials per warp group).
+template <typename TIN, bool PAIR, int NBUF, int SHORT>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_fused(DedispArgs a, const FusedArgs f) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ TileState ts;
@@ -36,8 +38,8 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_fused(DedispArgs a, c
         const int blk = it / f.tiles;
         const int tx = it - blk * f.tiles;
         if (threadIdx.x == 0) {
-            const int L = chunk_t(false) * a.nch;
-            const int tpc = kWarps / a.nch * upw<TIN>();
+            const int L = chunk_t(PAIR) * a.nch;
+            const int tpc = kWarps / a.nch * upw<TIN>() * (PAIR ? 2 : 1);
             const int tx0 = it - tx <= i0 ? i0 - (it - tx) : 0;                    // strip start
             const int tx1 = i1 - (it - tx) < f.tiles ? i1 - (it - tx) : f.tiles;  // strip end
             ft.first = tx == tx0;
@@ -47,24 +49,24 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_fused(DedispArgs a, c
             ft.seam_in = tx0 > 0 ? f.seam + (int64_t)s * tpc * 2 * f.C : nullptr;
             ft.seam_out = tx1 < f.tiles ? f.seam + (int64_t)(s + 1) * tpc * 2 * f.C : nullptr;
         }
-        if (!dedisp_tile<TIN, false, NBUF, true, SHORT, true>(a, smem, blk, tx, ts, &f, &ft)) break;
+        if (!dedisp_tile<TIN, PAIR, NBUF, true, SHORT, true>(a, smem, blk, tx, ts, &f, &ft)) break;
     }
 }
 
-template <typename TIN, int NBUF, int SHORT>
+template <typename TIN, bool PAIR, int NBUF, int SHORT>
 dd_status run_fused(DedispArgs a, const FusedArgs& f, size_t smem, cudaStream_t s) {
     a.smem_bytes = (uint32_t)smem;
-    auto kern = k_dedisp_fused<TIN, NBUF, SHORT>;
+    auto kern = k_dedisp_fused<TIN, PAIR, NBUF, SHORT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
     kern<<<(unsigned)f.nparts, kWarps * 32, smem, s>>>(a, f);
     return cuda_status(cudaGetLastError());
 }
 
-template <typename TIN, int NBUF, int SHORT>
+template <typename TIN, bool PAIR, int NBUF, int SHORT>
 int fused_bps(size_t smem) {
     int n = 0;
-    auto kern = k_dedisp_fused<TIN, NBUF, SHORT>;
+    auto kern = k_dedisp_fused<TIN, PAIR, NBUF, SHORT>;
     if (cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem) != cudaSuccess)
         return 0;
     if (cudaOccupancyMaxActiveBlocksPerMultiprocessor(&n, kern, kWarps * 32, smem) != cudaSuccess) return 0;
@@ -148,6 +150,83 @@ __global__ void __launch_bounds__(256) k_fused_final(const unsigned long long* k
     }
 }
 
+// fp32 plans: the windows of the segments that begin before the boundary B between
+// parts kb - 1 and kb inside a trial block and end past it (chain start m * kBoxSeg < B
+// < t + w, t + w <= t_out), one CTA per (boundary, trial of the block), one thread per
+// (segment, width): each forms the segment's prefix chain from the 2C outputs around B
+// (C = wmax + kBoxSeg - 2 reaches back to the earliest such chain start) and merges the
+// largest sum with its earliest start into the key.
+__global__ void __launch_bounds__(128) k_fused_seam_f32(const FusedArgs f, int32_t L, int32_t t_out,
+                                                        int32_t ndm, int32_t tpc) {
+    constexpr int S = kBoxSeg;
+    const int kb = blockIdx.x + 1, local = blockIdx.y;
+    const int64_t item = f.starts[kb];
+    const int blk = (int)(item / f.tiles);
+    const int tx = (int)(item - (int64_t)blk * f.tiles);
+    const int d = blk * tpc + local;
+    if (tx == 0 || d >= ndm) return;  // a part boundary between blocks has no seam
+    const int C = f.C;
+    const float* v = (const float*)f.seam + ((int64_t)kb * tpc + local) * 2 * C;
+    const int64_t B = (int64_t)tx * L;  // first output of part kb in this block
+    const int64_t base = B - C;         // output of index 0 of the seam (>= 0: B >= L >= C)
+    const int64_t m_lo = (base + S - 1) / S, m_hi = (B + S - 1) / S;
+    const int nseg = (int)(m_hi - m_lo);
+    const int64_t e_abs = min((int64_t)t_out, B + C);  // outputs at or past it are not read
+    for (int i = threadIdx.x; i < nseg * f.nw; i += blockDim.x) {
+        const int sg = i / f.nw, j = i - sg * f.nw;
+        const int64_t t0 = (m_lo + sg) * S;
+        const int w = f.w0 + j;
+        const float* x = v + (t0 - base);
+        const int e_rel = (int)(e_abs - t0);
+        auto ld = [&](int k) { return k < e_rel ? x[k] : 0.f; };
+        float r = 0.f, p = 0.f;
+        for (int k = 0; k < w; ++k) r += ld(k);
+        float best = -FLT_MAX;
+        int bt = -1;
+        for (int s = 0; s < S; ++s) {
+            const int64_t t = t0 + s;
+            if (t + w > t_out) break;
+            if (t + w > B) {
+                const float val = r - p;
+                if (bt < 0 || val > best) {
+                    best = val;
+                    bt = (int)t;
+                }
+            }
+            p += ld(s);
+            r += ld(s + w);
+        }
+        if (bt >= 0) atomicMax(f.key + (int64_t)d * f.nw + j, fused_key_f32(best, bt));
+    }
+}
+
+// Merged (value, start) of fp32 plans -> S/N exactly as the unfused boxcar kernel
+// converts it.
+__global__ void __launch_bounds__(256) k_fused_final_f32(const unsigned long long* key, int32_t ndm,
+                                                         int32_t nw, const float* mu, const float* isd,
+                                                         float* peak, int32_t* arg, float thresh,
+                                                         dd_candidate* cands, int32_t cap, int32_t* ncands) {
+    const int64_t i = (int64_t)blockIdx.x * blockDim.x + threadIdx.x;
+    if (i >= (int64_t)ndm * nw) return;
+    const unsigned long long k = key[i];
+    const float b = k ? fused_key_value_f32(k) : -FLT_MAX;
+    const int t = k ? (int)(0xffffffffu - (uint32_t)k) : -1;
+    const float snr = (float)(((double)b - (double)mu[i]) * (double)isd[i]);
+    peak[i] = snr;
+    arg[i] = t;
+    if (cands && snr > thresh) {
+        const int c = atomicAdd(ncands, 1);
+        if (c < cap) {
+            dd_candidate cd;
+            cd.dm_index = (int32_t)(i / nw);
+            cd.width_index = (int32_t)(i % nw);
+            cd.t = t;
+            cd.snr = snr;
+            cands[c] = cd;
+        }
+    }
+}
+
 template <typename T>
 dd_status grow(T** buf, int64_t* have, int64_t need) {
     if (need <= *have) return DD_OK;
@@ -207,24 +286,50 @@ bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
 }  // namespace
 
 size_t fused_smem_for(const dd_plan_s* p, int rowlen, int C) {
-    const int nbuf = p->rl ? kStagesRl : kStagesInt;
+    const int nbuf = p->rl ? kStagesRl : (p->pair ? kStagesPair : kStagesInt);
+    // fp32 pair units: a row per trial; run-length path: a row per warp group and the
+    // group's other trials' sums
+    const int nrow = kWarps / p->nch * (p->pair ? 2 : 1);
     const int spill = p->rl ? kWarps * (kRlUnits - 1) * chunk_t(false) : 0;
-    const size_t rows = (size_t)(fused_rows_ints(kWarps / p->nch, rowlen, C) + spill) * 4 + nbuf * 8 + 2 * nbuf * 4;
+    const size_t rows = (size_t)(fused_rows_ints(nrow, rowlen, C) + spill) * 4 + nbuf * 8 + 2 * nbuf * 4;
     return (std::max(dedisp_smem_for(p), rows) + 15) & ~(size_t)15;
 }
 
+// Pair path: union windows of at most R taps, one unrolled pass; at most 2R, two; longer,
+// a loop (as the plain launch).
+int pair_passes(const dd_plan_s* p) { return p->umax <= kRPair ? 1 : (p->umax <= 2 * kRPair ? 2 : 0); }
+
 int fused_blocks_per_sm(const dd_plan_s* p, size_t smem) {
-    if (p->rl) return p->rl_b ? fused_bps<uint32_t, kStagesRl, 1>(smem) : fused_bps<uint32_t, kStagesRl, 0>(smem);
-    return p->kmax <= kRInt ? fused_bps<uint8_t, kStagesInt, 1>(smem) : fused_bps<uint8_t, kStagesInt, 0>(smem);
+    if (p->rl) return p->rl_b ? fused_bps<uint32_t, false, kStagesRl, 1>(smem) : fused_bps<uint32_t, false, kStagesRl, 0>(smem);
+    if (p->pair) {
+        const int np = pair_passes(p);
+        if (p->band.in_type == DD_U8)
+            return np == 1 ? fused_bps<uint8_t, true, kStagesPair, 1>(smem)
+                           : (np == 2 ? fused_bps<uint8_t, true, kStagesPair, 2>(smem) : fused_bps<uint8_t, true, kStagesPair, 0>(smem));
+        return np == 1 ? fused_bps<float, true, kStagesPair, 1>(smem)
+                       : (np == 2 ? fused_bps<float, true, kStagesPair, 2>(smem) : fused_bps<float, true, kStagesPair, 0>(smem));
+    }
+    return p->kmax <= kRInt ? fused_bps<uint8_t, false, kStagesInt, 1>(smem) : fused_bps<uint8_t, false, kStagesInt, 0>(smem);
 }
 
 dd_status launch_dedisperse_fused(const dd_plan_s* p, DedispArgs a, const FusedArgs& f, size_t smem,
                                   cudaStream_t s) {
     if (p->rl)
-        return p->rl_b ? run_fused<uint32_t, kStagesRl, 1>(a, f, smem, s) : run_fused<uint32_t, kStagesRl, 0>(a, f, smem, s);
-    return p->kmax <= kRInt ? run_fused<uint8_t, kStagesInt, 1>(a, f, smem, s)
-                            : run_fused<uint8_t, kStagesInt, 0>(a, f, smem, s);
+        return p->rl_b ? run_fused<uint32_t, false, kStagesRl, 1>(a, f, smem, s) : run_fused<uint32_t, false, kStagesRl, 0>(a, f, smem, s);
+    if (p->pair) {
+        const int np = pair_passes(p);
+        if (p->band.in_type == DD_U8)
+            return np == 1 ? run_fused<uint8_t, true, kStagesPair, 1>(a, f, smem, s)
+                           : (np == 2 ? run_fused<uint8_t, true, kStagesPair, 2>(a, f, smem, s)
+                                      : run_fused<uint8_t, true, kStagesPair, 0>(a, f, smem, s));
+        return np == 1 ? run_fused<float, true, kStagesPair, 1>(a, f, smem, s)
+                       : (np == 2 ? run_fused<float, true, kStagesPair, 2>(a, f, smem, s)
+                                  : run_fused<float, true, kStagesPair, 0>(a, f, smem, s));
+    }
+    return p->kmax <= kRInt ? run_fused<uint8_t, false, kStagesInt, 1>(a, f, smem, s)
+                            : run_fused<uint8_t, false, kStagesInt, 0>(a, f, smem, s);
 }
+
 }  // namespace dd
 
 extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t in_ld, int64_t t_offset,
@@ -244,13 +349,16 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
         if (widths[i] < 1 || widths[i] > t_out) return DD_ERR_ARG;
         if (i && widths[i] <= widths[i - 1]) return DD_ERR_ARG;
     }
-    if (p->band.in_type != DD_U8 || !p->out_int || p->pair) return DD_ERR_UNSUPPORTED;
+    const bool fp = p->pair;  // fp32 sums (fp32 input, or weighted uint8)
+    if (!fp && (p->band.in_type != DD_U8 || !p->out_int)) return DD_ERR_UNSUPPORTED;
     if (widths[nw - 1] - widths[0] != nw - 1) return DD_ERR_UNSUPPORTED;  // w_j = w_0 + j only
-    const int L = chunk_t(false) * p->nch;
-    const int C = widths[nw - 1] - 1;
+    const int L = chunk_t(fp) * p->nch;
+    // carried outputs: the longest window (integer), or back to its prefix chain's start
+    const int C = fp ? widths[nw - 1] + kBoxSeg - 2 : widths[nw - 1] - 1;
     if (C > L) return DD_ERR_UNSUPPORTED;
-    if (!aligned16(in) || in_ld % 16 != 0) return DD_ERR_ARG;
-    if (t_out > INT32_MAX - chunk_t(false) * kWarps || in_ld > (int64_t)1 << 40) return DD_ERR_OVERFLOW;
+    const int64_t esz = p->band.in_type == DD_U8 ? 1 : 4;
+    if (!aligned16(in) || (in_ld * esz) % 16 != 0) return DD_ERR_ARG;
+    if (t_out > INT32_MAX - chunk_t(fp) * kWarps || in_ld > (int64_t)1 << 40) return DD_ERR_OVERFLOW;
     if (p->rl && nsamp > ((int64_t)1 << 24)) return DD_ERR_UNSUPPORTED;
     cudaStream_t s = (cudaStream_t)stream;
     dd_status st = upload_tables(p);
@@ -266,11 +374,12 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
         fill_dedisp_args(p, in, in_ld, t_offset, t_out, nullptr, 0, &a);
     }
     const int tiles = (int)((t_out + L - 1) / L);
-    const int tpc = kWarps / p->nch * (p->rl ? kRlUnits : 1);
+    const int tpc = kWarps / p->nch * (p->rl ? kRlUnits : 1) * (fp ? 2 : 1);
     const int64_t nblk = (p->ndm + tpc - 1) / tpc;
-    // row: C carried outputs, the tile and 32 spare; the last tile's extra starts read up
-    // to C + 14 past a row, into the next one or the padding behind the last
-    const int rowlen = L + C + 32;
+    // row: C carried outputs, the tile and 32 spare (fp32: 48); the last tile's extra
+    // starts read up to C + 14 past a row (fp32: 15 past the row's windows), into the
+    // next one or the padding behind the last
+    const int rowlen = L + C + (fp ? 48 : 32);
     const size_t smem = fused_smem_for(p, rowlen, C);
     int dev = 0, nsm = 0;
     cudaError_t e = cudaGetDevice(&dev);
@@ -287,11 +396,13 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
     const int64_t k_per = std::max<int64_t>(1, std::min<int64_t>(8, nblk * tiles / (16 * slots)));
     std::vector<int64_t> starts, order;
     int nparts = 0;
-    if (p->debug_fused_parts > 0) {
-        // test hook: that many parts of about equal cost, in block-major order (cost of a
-        // tile: constant on the run-length path, the block's taps plus a per-channel
-        // constant on the direct path)
-        nparts = (int)std::min<int64_t>(p->debug_fused_parts, nitems);
+    if (p->debug_fused_parts > 0 || fp) {
+        // parts of about equal cost in block-major order (cost of a tile: constant on the
+        // run-length path, the block's taps plus a per-channel constant otherwise): the
+        // test hook's count, or on fp32 plans k_per per resident CTA, a whole number of
+        // waves (their input is re-read from L2 by every trial block in any order when it
+        // fits there, as on the CRAFT-like block)
+        nparts = (int)std::min<int64_t>(p->debug_fused_parts > 0 ? p->debug_fused_parts : k_per * slots, nitems);
         std::vector<double> cost((size_t)nblk, 1.0);
         if (!p->rl)
             for (int64_t b = 0; b < nblk; ++b) {
@@ -347,14 +458,23 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
     e = cudaMemsetAsync(f.key, 0, (size_t)p->ndm * nw * sizeof(unsigned long long), s);
     if (e != cudaSuccess) return cuda_status(e);
     if ((st = launch_dedisperse_fused(p, a, f, smem, s)) != DD_OK) return st;
-    if (nparts > 1 && C > 0) {
+    if (nparts > 1 && fp) {
+        k_fused_seam_f32<<<dim3((unsigned)(nparts - 1), (unsigned)tpc), 128, 0, s>>>(f, L, (int32_t)t_out,
+                                                                                   p->ndm, tpc);
+        if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
+    } else if (nparts > 1 && C > 0) {
         k_fused_seam<<<dim3((unsigned)(nparts - 1), (unsigned)tpc), 256, (size_t)(2 * C + 1) * 4, s>>>(
             f, L, (int32_t)t_out, p->ndm, tpc);
         if ((e = cudaGetLastError()) != cudaSuccess) return cuda_status(e);
     }
     const int64_t n = (int64_t)p->ndm * nw;
-    k_fused_final<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(f.key, p->ndm, nw, p->dev.mu, p->dev.isd,
-                                                              peak, arg, thresh, cands, cap, ncands);
+    const unsigned nb = (unsigned)((n + 255) / 256);
+    if (fp)
+        k_fused_final_f32<<<nb, 256, 0, s>>>(f.key, p->ndm, nw, p->dev.mu, p->dev.isd, peak, arg, thresh, cands,
+                                             cap, ncands);
+    else
+        k_fused_final<<<nb, 256, 0, s>>>(f.key, p->ndm, nw, p->dev.mu, p->dev.isd, peak, arg, thresh, cands,
+                                         cap, ncands);
     return cuda_status(cudaGetLastError());
 }
 

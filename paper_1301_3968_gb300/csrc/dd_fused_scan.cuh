@@ -1,6 +1,7 @@
 // Boxcar scan of finished dedispersion tiles inside the dedispersion CTA: the fused
-// path of dd_dedisperse_boxcar (integer plans, contiguous widths w0 .. w0 + nw - 1).
-// Included by dd_dedisp.cu only.
+// path of dd_dedisperse_boxcar (contiguous widths w0 .. w0 + nw - 1).  Integer plans
+// (exact sums) first, then fp32 plans (the unfused fp32 scan's prefix chains).
+// Included by dd_tile.cuh.
 //
 // A CTA walks its part of the launch's (trial block, time tile) items in order, a strip
 // of consecutive tiles per trial block it touches.  After a tile's channel sum, each
@@ -22,6 +23,7 @@
 // merge (value, start) with one 64-bit atomicMax.
 #pragma once
 
+#include <cfloat>
 #include <climits>
 
 #include "dd_internal.h"
@@ -254,6 +256,217 @@ __device__ __forceinline__ void epilogue(const DedispArgs& a, const FusedArgs& f
         }
         scan_row(f, row, f.key + (int64_t)du * f.nw, T0, C, chunk, a.nch, lane, i_lo, i_hi, e_hi);
     }
+    // the next tile's bulk copies overwrite the rows
+    asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
+    __syncthreads();
+}
+
+
+// ----------------------------------------------------------------------------- fp32 plans
+//
+// The unfused fp32 scan (k_boxcar_run) gives each thread kBoxSeg consecutive starts from
+// a multiple of kBoxSeg and forms the segment's prefix chain P_0 = 0,
+// P_{k+1} = P_k + x[k] (x = series - o_d in fp32), left to right; the window of width w
+// at start s sums to P_{s+w} - P_s.  fp32 addition is deterministic, so a chain formed
+// the same way anywhere gives the same sums bit for bit.  The fused scan therefore
+// walks whole segments: a tile owns the segments whose first start lies in its start
+// range, reads them from its shared-memory row (C = wmax + kBoxSeg - 2 outputs carried
+// from the previous tile reach back to any such segment), and keeps the window ends
+// that its strip holds; windows of a segment that begins before a strip boundary and
+// ends past it go to the seam pass (dd_fused.cu).
+
+// Segment at x (kBoxSeg starts) for widths w0g + j, j < G; q = P_{w0g}.  !FULL: windows
+// ending past index e_rel are left out and no sample at or past it is read.  FULL
+// reads up to 15 samples past the last window of the group's widths below cnt.
+template <bool FULL>
+__device__ __forceinline__ void scan_segment_f32(const float* x, float q, int w0g, int e_rel,
+                                                 float (&seg)[G]) {
+    constexpr int S = kBoxSeg;
+    auto ld = [&](int k) { return (FULL || k < e_rel) ? x[k] : 0.f; };
+    float win[G];
+    win[0] = q;
+#pragma unroll
+    for (int j = 1; j < G; ++j) win[j] = win[j - 1] + ld(w0g + j - 1);
+    float p = 0.f;
+    // two starts per step, their sums merged with one three-input max
+#pragma unroll
+    for (int s = 0; s < S; s += 2) {
+        float v0[G];
+#pragma unroll
+        for (int j = 0; j < G; ++j) {
+            v0[j] = win[(j + s) % G] - p;
+            if (!FULL) v0[j] = (s + w0g + j <= e_rel) ? v0[j] : -FLT_MAX;
+        }
+        if (s + 1 < S) {
+            p += ld(s);
+            win[s % G] = win[(s + G - 1) % G] + ld(s + w0g + G - 1);
+#pragma unroll
+            for (int j = 0; j < G; ++j) {
+                float v = win[(j + s + 1) % G] - p;
+                if (!FULL) v = (s + 1 + w0g + j <= e_rel) ? v : -FLT_MAX;
+                seg[j] = max3(seg[j], v0[j], v);
+            }
+            if (s + 2 < S) {
+                p += ld(s + 1);
+                win[(s + 1) % G] = win[(s + G) % G] + ld(s + w0g + G);
+            }
+        } else {
+#pragma unroll
+            for (int j = 0; j < G; ++j) seg[j] = fmaxf(seg[j], v0[j]);
+        }
+    }
+}
+
+// Earliest start s of the segment whose width-w sum equals m (the same chain), or -1.
+__device__ __noinline__ int find_start_f32(const float* x, int w, float m, int e_rel) {
+    auto ld = [&](int k) { return k < e_rel ? x[k] : 0.f; };
+    float r = 0.f, p = 0.f;
+    for (int k = 0; k < w; ++k) r += ld(k);
+    for (int s = 0; s < kBoxSeg; ++s) {
+        if (s + w <= e_rel && r - p == m) return s;
+        p += ld(s);
+        r += ld(s + w);
+    }
+    return -1;
+}
+
+// warp_max16 for fp32 maxima (fmaxf, as the unfused scan).
+__device__ __forceinline__ float warp_max16_f32(const float (&seg)[G], int lane) {
+    const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
+    float v8[8], v4[4], v2[2];
+#pragma unroll
+    for (int j = 0; j < 8; ++j)
+        v8[j] = fmaxf(b4 ? seg[j + 8] : seg[j], __shfl_xor_sync(0xffffffffu, b4 ? seg[j] : seg[j + 8], 16));
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+        v4[j] = fmaxf(b3 ? v8[j + 4] : v8[j], __shfl_xor_sync(0xffffffffu, b3 ? v8[j] : v8[j + 4], 8));
+#pragma unroll
+    for (int j = 0; j < 2; ++j)
+        v2[j] = fmaxf(b2 ? v4[j + 2] : v4[j], __shfl_xor_sync(0xffffffffu, b2 ? v4[j] : v4[j + 2], 4));
+    const float v = fmaxf(b1 ? v2[1] : v2[0], __shfl_xor_sync(0xffffffffu, b1 ? v2[0] : v2[1], 2));
+    return fmaxf(v, __shfl_xor_sync(0xffffffffu, v, 1));
+}
+
+// The segments m_lo <= m < m_hi of one trial's row (row index of output t: t - base;
+// windows end at or before row index e_hi), 32 per warp pass, passes shared by the
+// nch warps of the trial's group.  Arguments are warp-uniform.
+__device__ __forceinline__ void scan_row_f32(int w0, int nw, const float* row, unsigned long long* keyrow,
+                                             int64_t base, int chunk, int nch, int lane, int64_t m_lo,
+                                             int64_t m_hi, int e_hi) {
+    constexpr int S = kBoxSeg;
+    __builtin_assume(__isShared(row));
+    const int ng = (nw + G - 1) / G;
+    const int jl = lane >> 1;
+    for (int64_t mb = m_lo + (int64_t)chunk * 32; mb < m_hi; mb += (int64_t)nch * 32) {
+        const int64_t m = mb + lane;
+        const bool any = m < m_hi;
+        const int i0 = any ? (int)(m * S - base) : 0;
+        const float* x = row + i0;
+        const int e_rel = e_hi - i0;
+        const int t_first = (int)(mb * S);  // earliest start of the pass
+        float q = 0.f;
+        if (any)
+            for (int k = 0; k < w0; ++k) q += k < e_rel ? x[k] : 0.f;
+        for (int g = 0; g < ng; ++g) {
+            const int w0g = w0 + g * G;
+            const int cnt = min(G, nw - g * G);
+            unsigned long long bk = 0;
+            if (!(lane & 1) && jl < cnt) bk = __ldcg(keyrow + g * G + jl);
+            const float bv = bk ? fused_key_value_f32(bk) : -INFINITY;
+            const int bt = (int)(0xffffffffu - (uint32_t)bk);
+            const bool full = any && S - 1 + w0g + cnt - 1 <= e_rel;
+            float seg[G];
+#pragma unroll
+            for (int j = 0; j < G; ++j) seg[j] = -FLT_MAX;
+            if (full)
+                scan_segment_f32<true>(x, q, w0g, e_rel, seg);
+            else if (any)
+                scan_segment_f32<false>(x, q, w0g, e_rel, seg);
+            const float mx = warp_max16_f32(seg, lane);
+            const bool better = !(lane & 1) && jl < cnt && mx > -FLT_MAX &&
+                                (mx > bv || (mx == bv && t_first < bt));
+            unsigned need = __ballot_sync(0xffffffffu, better);
+            while (need) {  // warp-uniform
+                const int hl = __ffs(need) - 1;
+                need &= need - 1;
+                const int j = hl >> 1;
+                const float mj = __shfl_sync(0xffffffffu, mx, hl);
+                float sj = -FLT_MAX;
+#pragma unroll
+                for (int jj = 0; jj < G; ++jj) sj = jj == j ? seg[jj] : sj;
+                const unsigned hit = __ballot_sync(0xffffffffu, any && sj == mj);
+                if (lane == __ffs(hit) - 1) {
+                    const int st = find_start_f32(x, w0g + j, mj, e_rel);
+                    if (st >= 0) atomicMax(keyrow + g * G + j, fused_key_f32(mj, (int)(m * S) + st));
+                }
+            }
+            if (any)
+#pragma unroll
+                for (int kk = 0; kk < G; ++kk) q += w0g + kk < e_rel ? x[w0g + kk] : 0.f;
+        }
+    }
+}
+
+// Carries, seams and the scan of a warp group's two trial rows (rows[u], trial d + u).
+// Not inlined: its registers are then allocated apart from the channel sums', which
+// keep the whole register file (the call comes once per tile).
+__device__ __noinline__ void scan_pair_rows_f32(float* rows, int rowlen, int w0, int nw, int C, int L,
+                                                unsigned long long* key, int ndm, int d, int cb0,
+                                                int chunk, int nch, int lane, int64_t base, int64_t m_lo,
+                                                int64_t m_hi, int e_hi, bool first, bool last,
+                                                float* carry, float* seam_in, float* seam_out) {
+    for (int u = 0; u < 2; ++u) {
+        const int du = d + u;
+        if (du >= ndm) break;
+        float* row = rows + u * rowlen;
+        const int64_t cb = (int64_t)(cb0 + u) * C;  // this trial's carry and seam rows
+        if (chunk == 0) {
+            if (!last)
+                for (int k = lane; k < C; k += 32) carry[cb + k] = row[L + k];
+            if (first && seam_in)
+                for (int k = lane; k < C; k += 32) seam_in[2 * cb + C + k] = row[C + k];
+            if (last && seam_out)
+                for (int k = lane; k < C; k += 32) seam_out[2 * cb + k] = row[e_hi - C + k];
+        }
+        scan_row_f32(w0, nw, row, key + (int64_t)du * nw, base, chunk, nch, lane, m_lo, m_hi, e_hi);
+    }
+}
+
+// The fused epilogue of one fp32 pair tile (every thread of the CTA calls it): the warp
+// group's two trials d, d + 1 (sums acc0, acc1), T0 = the tile's first output; one row
+// per trial.  The tile owns the segments whose first start lies in [T0 - C, T0 + L - C)
+// (the strip's first tile: from T0; its last: up to the strip end S1, windows ending at
+// or before S1).
+template <int R>
+__device__ __forceinline__ void epilogue_f32(const DedispArgs& a, const FusedArgs& f, unsigned char* smem,
+                                             int wu, int chunk, int lane, int d, int64_t T0,
+                                             const FusedTile& ft, const float (&acc0)[R],
+                                             const float (&acc1)[R]) {
+    constexpr int S = kBoxSeg, TT = 32 * R;
+    const int L = TT * a.nch;
+    const int C = f.C;
+    float* rows = (float*)smem + 2 * wu * f.rowlen;
+    const int64_t S1 = ft.s1;
+    const bool first = ft.first, last = ft.last;
+    const int64_t base = T0 - C;  // output of row index 0
+    const int e_hi = (int)((last ? S1 : T0 + L) - base);
+    const int64_t t_lo = first ? T0 : base, t_hi = last ? S1 : T0 + L - C;
+    const int64_t m_lo = (t_lo + S - 1) / S, m_hi = (t_hi + S - 1) / S;
+    float* carry = (float*)ft.carry;
+    const int ib = C + chunk * TT + lane * R;
+#pragma unroll
+    for (int u = 0; u < 2; ++u) {
+        const bool live = d + u < a.ndm;
+        const float o = live ? (float)f.off[d + u] : 0.f;
+        float* row = rows + u * f.rowlen;
+#pragma unroll
+        for (int r = 0; r < R; ++r) row[ib + r] = (u == 0 ? acc0[r] : acc1[r]) - o;
+        if (live && chunk == 0 && !first)
+            for (int k = lane; k < C; k += 32) row[k] = carry[(int64_t)(wu * 2 + u) * C + k];
+    }
+    __syncthreads();  // the rows and their carries are complete
+    scan_pair_rows_f32(rows, f.rowlen, f.w0, f.nw, C, L, f.key, a.ndm, d, wu * 2, chunk, a.nch, lane, base,
+                       m_lo, m_hi, e_hi, first, last, carry, (float*)ft.seam_in, (float*)ft.seam_out);
     // the next tile's bulk copies overwrite the rows
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();

@@ -22,6 +22,10 @@ constexpr int kRInt = 31;
 constexpr int kRMax = 31;
 __host__ __device__ constexpr int lane_r(bool pair) { return pair ? kRPair : kRInt; }
 __host__ __device__ constexpr int chunk_t(bool pair) { return 32 * lane_r(pair); }
+// Start times per thread segment of the contiguous-width boxcar scan (k_boxcar_run):
+// each segment's prefix chain starts at a multiple of kBoxSeg (odd: lane-strided shared
+// loads are conflict-free).  The fused fp32 scan forms the same chains.
+constexpr int kBoxSeg = 31;
 constexpr int kRlUnits = 3;                // trials per warp on the run-length path
 constexpr int kRlMinMeanTaps = 12;         // automatic run-length choice (uint8, unit weights)
 // Bulk-copy pipeline depth (buffers in the ring) per path: the pair and run-length paths
@@ -100,19 +104,21 @@ struct DedispArgs {
     uint32_t smem_bytes;  // dynamic shared memory of the launch
 };
 
-// The boxcar scan fused into the dedispersion CTAs (integer plans, contiguous widths
-// w0 .. w0 + nw - 1; dd_fused.cu).  The launch's items (trial block, time tile), block-
-// major, are cut into nparts contiguous parts of about equal cost, one CTA each.  A
-// CTA walks its items in order and scans each finished tile in shared memory,
-// with the last C = wmax - 1 outputs of the previous tile of the same block carried in
-// front of it (through `carry`, a per-CTA global buffer).  Windows that cross a part
-// boundary inside a trial block are scanned afterwards from `seam`, which holds C
-// outputs on each side of such a boundary.  Maxima are merged in `key` as (value,
-// earliest start) packed into one 64-bit word.
+// The boxcar scan fused into the dedispersion CTAs (contiguous widths w0 .. w0 + nw - 1;
+// dd_fused.cu).  The launch's items (trial block, time tile), block-major, are cut into
+// nparts contiguous parts, one CTA each.  A CTA walks its items in order and scans each
+// finished tile in shared memory, with the last C outputs of the previous tile of the
+// same block carried in front of it (through `carry`, a per-CTA global buffer).
+// Windows that a part boundary inside a trial block separates from their data are
+// scanned afterwards from `seam`, which holds C outputs on each side of such a boundary.
+// Maxima are merged in `key` as (value, earliest start) packed into one 64-bit word.
+// Integer plans: C = wmax - 1 and exact sums.  fp32 plans: the sums of the unfused fp32
+// scan, whose prefix chains start at multiples of kBoxSeg outputs, so C = wmax +
+// kBoxSeg - 2 reaches back to the chain start of every window a tile owns.
 struct FusedArgs {
     int32_t w0, nw;
-    int32_t C;          // wmax - 1
-    int32_t rowlen;     // shared-memory row stride (ints)
+    int32_t C;          // carried outputs: wmax - 1 (integer), wmax + kBoxSeg - 2 (fp32)
+    int32_t rowlen;     // shared-memory row stride (4-byte words)
     int32_t nparts;
     int32_t tiles;      // time tiles per trial block; item = block * tiles + tile
     int32_t mlim;       // largest |x - o| for which every width-wmax sum fits int32
@@ -120,9 +126,9 @@ struct FusedArgs {
     const int64_t* order;     // [nparts] part taken by CTA i: parts sorted by their first
                               // time tile, so that CTAs resident together read the same
                               // input columns (shared in L2)
-    const double* off;        // [ndm] per-trial offsets (integer valued)
+    const double* off;        // [ndm] per-trial offsets (integer valued on integer plans)
     unsigned long long* key;  // [ndm][nw]
-    int32_t* carry;     // [nparts][trials per CTA][C]
+    int32_t* carry;     // [nparts][trials per CTA][C] (fp32 plans: float bits)
     int32_t* seam;      // [nparts][trials per CTA][2 C]; entry s: boundary between parts s-1, s
 };
 
@@ -136,6 +142,31 @@ __host__ __device__ inline int fused_rows_ints(int nrow, int rowlen, int C) { re
 __host__ __device__ inline unsigned long long fused_key(int v, int t) {
     return ((unsigned long long)((uint32_t)v ^ 0x80000000u) << 32) | (unsigned long long)(0xffffffffu - (uint32_t)t);
 }
+
+// The fp32 form: the float's bits mapped to an unsigned order (negative values with every
+// bit flipped, others with the sign bit set) after -0 is made +0, so that equal sums
+// compare equal and the earlier start wins, as in the unfused scan's comparisons.
+#ifdef __CUDACC__
+// max(a, b, c): one three-input max.f32 for fp32 (maxima are exact, so any grouping
+// gives the same value), pairwise for the integer types.
+__device__ __forceinline__ float max3(float a, float b, float c) {
+    float m;
+    asm("max.f32 %0, %1, %2, %3;" : "=f"(m) : "f"(a), "f"(b), "f"(c));
+    return m;
+}
+__device__ __forceinline__ int max3(int a, int b, int c) { return max(max(a, b), c); }
+__device__ __forceinline__ long long max3(long long a, long long b, long long c) { return max(max(a, b), c); }
+
+__device__ __forceinline__ unsigned long long fused_key_f32(float v, int t) {
+    const uint32_t u = __float_as_uint(v == 0.f ? 0.f : v);
+    const uint32_t o = (u & 0x80000000u) ? ~u : (u | 0x80000000u);
+    return ((unsigned long long)o << 32) | (unsigned long long)(0xffffffffu - (uint32_t)t);
+}
+__device__ __forceinline__ float fused_key_value_f32(unsigned long long k) {
+    const uint32_t o = (uint32_t)(k >> 32);
+    return __uint_as_float((o & 0x80000000u) ? (o & 0x7fffffffu) : ~o);
+}
+#endif
 
 // One work item of the batched dedispersion kernel: a CTA tile of one beam.
 struct BatchItem {

@@ -418,7 +418,8 @@ struct TileState {
 // `a` is taken by value: with a reference to the kernel parameter the compiler picked
 // a register allocation for the FMA loop that ran 11 % slower.
 // FUSED: instead of storing the tile, scan it for boxcar maxima (fa: the scan's
-// arguments, ft: the strip the tile belongs to).
+// arguments, ft: the strip the tile belongs to); exact sums on the integer paths, the
+// unfused fp32 scan's prefix chains on the pair path.
 template <typename TIN, bool PAIR, int NBUF, bool MULTI, int SHORT, bool FUSED = false>
 __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* smem, int blk,
                                             int tx, TileState& ts, const FusedArgs* fa = nullptr,
@@ -611,8 +612,14 @@ __device__ __forceinline__ bool dedisp_tile(const DedispArgs a, unsigned char* s
         for (int b = 0; b < NBUF && b < nloc; ++b) ts.uses[b] += (nloc - b + NBUF - 1) / NBUF;
 
     if constexpr (FUSED) {
-        static_assert(!PAIR, "the fused scan takes integer sums");
-        fused::epilogue<UPW, RL ? UPW - 1 : 1>(a, *fa, smem, wu, chunk, lane, d, t0, *ft, acc0, accr);
+        if constexpr (PAIR) {
+            float f0[R], f1[R];
+#pragma unroll
+            for (int r = 0; r < R; ++r) unpk(accp[r], f0[r], f1[r]);
+            fused::epilogue_f32<R>(a, *fa, smem, wu, chunk, lane, d, t0, *ft, f0, f1);
+        } else {
+            fused::epilogue<UPW, RL ? UPW - 1 : 1>(a, *fa, smem, wu, chunk, lane, d, t0, *ft, acc0, accr);
+        }
         return true;
     }
     // transpose through shared memory and store coalesced, one trial row at a time

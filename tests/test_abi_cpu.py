@@ -135,8 +135,8 @@ def test_argument_errors(lib):
 
 def test_fused_argument_checks(lib):
     """dd_dedisperse_boxcar refuses, before any device work, what its kernels do not cover:
-    fp32 or weighted plans, non-contiguous widths, widths longer than a tile plus one, and
-    the usual argument errors."""
+    non-contiguous widths, carries longer than a tile (wmax - 1 on integer plans, wmax + 29
+    on fp32 plans), and the usual argument errors."""
     import paper_1301_3968_gb300 as dd
     fake = ctypes.c_void_p(1 << 20)
 
@@ -146,7 +146,9 @@ def test_fused_argument_checks(lib):
                                         fake, fake, fake, ctypes.c_float(1.0), None, 0, None, None)
 
     f32 = dd.Plan(dd.Band(8, 1200.0, 1.0, 1.0, 2048, "f32"), np.zeros(4))
-    assert call(f32, [1, 2, 3]) == 8
+    assert f32.schedule()["nch"] == 1
+    assert call(f32, [1, 2, 4]) == 8                      # not contiguous
+    assert call(f32, np.arange(1, 837)) == 8              # wmax + 29 > 864
     u8 = dd.Plan(dd.Band(8, 1200.0, 1.0, 1.0, 2048, "u8"), np.zeros(4))
     assert u8.schedule()["nch"] == 1
     assert call(u8, [1, 2, 4]) == 8                       # not contiguous
@@ -158,7 +160,8 @@ def test_fused_argument_checks(lib):
     assert call(u8, [1, 2], t_offset=16) == 1             # runs past the row
     weighted = dd.Plan(dd.Band(8, 1200.0, 1.0, 1.0, 2048, "u8"), np.zeros(4))
     weighted.set_profiles(weights=np.full((4, 8, 1), 0.5, np.float32))
-    assert call(weighted, [1, 2]) == 8
+    assert call(weighted, np.arange(1, 837)) == 8         # fp32 sums: wmax + 29 > 864
+    assert call(f32, [1, 2], ld=2047, nsamp=2047) == 1    # fp32 rows not 16-byte aligned
 
 
 def test_int32_overflow_is_refused(lib):

@@ -27,9 +27,20 @@ __device__ __forceinline__ T warp_sum(T v) {
     return v;
 }
 
-// One CTA per channel.  uint8: exact int64 sums of x and x^2.  fp32: double sums of
-// (x - x0) and (x - x0)^2 around the row's first sample, which keeps the variance
-// free of cancellation for rows with a large mean.
+// One CTA per channel.  uint8: exact int64 sums of x and x^2.  fp32: sums of (x - x0)
+// and (x - x0)^2 around x0 = the mean of the row's first 256 samples, which keeps the
+// variance free of cancellation for rows with a large mean.  Each thread sums runs of 32
+// of its samples as unevaluated pairs hi + lo of fp32 values (Knuth's TwoSum for every
+// addition, squares split exactly by an FMA), which carry about twice fp32's precision,
+// and adds the run sums in double: the slow FP64 pipe then sees two adds per 32 samples
+// instead of three operations per sample, with the double-precision result unchanged.
+__device__ __forceinline__ void two_sum_add(float& hi, float& lo, float a) {
+    const float s = hi + a;
+    const float bp = s - hi;
+    lo += (hi - (s - bp)) + (a - bp);
+    hi = s;
+}
+
 template <typename TIN>
 __global__ void __launch_bounds__(256) k_chan_stats(const TIN* in, int64_t ld, int64_t t_offset,
                                                     int64_t n, double* mean, double* sd) {
@@ -64,12 +75,36 @@ __global__ void __launch_bounds__(256) k_chan_stats(const TIN* in, int64_t ld, i
             sd[c] = sqrt(var > 0 ? var : 0.0);
         }
     } else {
-        const double x0 = (double)row[0];
+        __shared__ float sx0;
+        if (warp == 0) {  // x0: the mean of the first min(n, 256) samples
+            const int n0 = (int)(n < 256 ? n : 256);
+            float a = 0.f;
+            for (int t = lane; t < n0; t += 32) a += (float)row[t];
+            a = warp_sum(a);
+            if (lane == 0) sx0 = a / (float)n0;
+        }
+        __syncthreads();
+        const float x0 = sx0;
         double s1 = 0, s2 = 0;
-        for (int64_t t = threadIdx.x; t < n; t += blockDim.x) {
-            double v = (double)row[t] - x0;
-            s1 += v;
-            s2 += v * v;
+        for (int64_t t0 = threadIdx.x; t0 < n; t0 += (int64_t)blockDim.x * 32) {
+            float h1 = 0.f, l1 = 0.f, h2 = 0.f, l2 = 0.f;
+#pragma unroll 8
+            for (int k = 0; k < 32; ++k) {
+                const int64_t t = t0 + (int64_t)k * blockDim.x;
+                const float x = t < n ? (float)row[t] : x0;
+                // x - x0 = vh + vl exactly (TwoSum)
+                const float vh = x - x0;
+                const float bp = vh - x;
+                const float vl = (x - (vh - bp)) + (-x0 - bp);
+                two_sum_add(h1, l1, vh);
+                l1 += vl;
+                // (vh + vl)^2 = p + (the FMA's exact remainder of vh^2) + 2 vh vl + vl^2
+                const float p = vh * vh;
+                l2 += fmaf(vh, vh, -p) + 2.f * vh * vl;
+                two_sum_add(h2, l2, p);
+            }
+            s1 += (double)h1 + (double)l1;
+            s2 += (double)h2 + (double)l2;
         }
         s1 = warp_sum(s1);
         s2 = warp_sum(s2);
@@ -86,7 +121,7 @@ __global__ void __launch_bounds__(256) k_chan_stats(const TIN* in, int64_t ld, i
             }
             const double m = a / (double)n;
             double var = b / (double)n - m * m;
-            mean[c] = x0 + m;
+            mean[c] = (double)x0 + m;
             sd[c] = sqrt(var > 0 ? var : 0.0);
         }
     }

@@ -18,10 +18,12 @@
 namespace dd {
 namespace {
 
-// Fused dedispersion + boxcar scan, one CTA per part: part s walks the
-// items (trial block, time tile) starts[s] .. starts[s + 1] - 1 in order (block-major),
-// a strip per trial block it touches.  CTA i takes part order[i].  PAIR: fp32 pair
-// units (fp32 sums, two trials per warp group).
+// Fused dedispersion + boxcar scan, one CTA per part: part s walks the items (trial
+// block, time tile) starts[s] .. starts[s + 1] - 1 in order (block-major), a strip per
+// trial block it touches.  CTA i takes part order[i] (the hardware starts CTAs in index
+// order as earlier ones finish; measured on the CRAFT-like block, parts handed out by an
+// atomic counter to persistent CTAs ran 11 % slower, and a fixed round-robin 3 %).
+// PAIR: fp32 pair units (fp32 sums, two trials per warp group).
 template <typename TIN, bool PAIR, int NBUF, int SHORT>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_fused(DedispArgs a, const FusedArgs f) {
     extern __shared__ __align__(128) unsigned char smem[];
@@ -290,7 +292,8 @@ size_t fused_smem_for(const dd_plan_s* p, int rowlen, int C) {
     // fp32 pair units: a row per trial; run-length path: a row per warp group and the
     // group's other trials' sums
     const int nrow = kWarps / p->nch * (p->pair ? 2 : 1);
-    const int spill = p->rl ? kWarps * (kRlUnits - 1) * chunk_t(false) : 0;
+    // (fp32: and the warps' chain scratch of the earliest-start search)
+    const int spill = p->rl ? kWarps * (kRlUnits - 1) * chunk_t(false) : (p->pair ? kWarps * fused::kChainFloats : 0);
     const size_t rows = (size_t)(fused_rows_ints(nrow, rowlen, C) + spill) * 4 + nbuf * 8 + 2 * nbuf * 4;
     return (std::max(dedisp_smem_for(p), rows) + 15) & ~(size_t)15;
 }
@@ -399,9 +402,9 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
     if (p->debug_fused_parts > 0 || fp) {
         // parts of about equal cost in block-major order (cost of a tile: constant on the
         // run-length path, the block's taps plus a per-channel constant otherwise): the
-        // test hook's count, or on fp32 plans k_per per resident CTA, a whole number of
-        // waves (their input is re-read from L2 by every trial block in any order when it
-        // fits there, as on the CRAFT-like block)
+        // test hook's count, or on fp32 plans k_per per resident CTA.  Block-major order
+        // keeps the stage records of the few trial blocks in progress in L2 (fp32 records
+        // hold every tap's weight pair: 139 MB for the 4096-trial CRAFT-like list)
         nparts = (int)std::min<int64_t>(p->debug_fused_parts > 0 ? p->debug_fused_parts : k_per * slots, nitems);
         std::vector<double> cost((size_t)nblk, 1.0);
         if (!p->rl)
@@ -415,13 +418,17 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
         starts = cut_parts(cost, tiles, last_frac, nparts);
         for (int i = 0; i < nparts; ++i) order.push_back(i);
     } else {
-        // up to k_per parts per resident CTA (no more, so that a last partial wave does not
-        // run alone), every block cut at the same time tiles
+        // up to k_per parts per resident CTA, every block cut at the same time tiles and
+        // taken segment by segment, so that the CTAs working together stage the same input
+        // columns (from L2)
         const int nseg = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, k_per * slots / nblk));
         aligned_parts(nblk, tiles, nseg, &starts, &order);
         nparts = (int)(starts.size() - 1);
     }
     if ((int64_t)nparts * tpc * 2 * C >= INT32_MAX || nparts < 1) return DD_ERR_UNSUPPORTED;
+    log_msg(1, "fused scan: %s sums, %d parts of %lld tiles (%lld trial blocks x %d), %d CTAs per SM, "
+            "carry %d, %zu bytes of shared memory", fp ? "fp32" : "integer", nparts,
+            (long long)(nitems / nparts), (long long)nblk, tiles, bps, C, smem);
     starts.insert(starts.end(), order.begin(), order.end());  // one table: starts, then order
 
     FusedArgs f;

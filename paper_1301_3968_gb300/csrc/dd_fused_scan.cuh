@@ -275,6 +275,11 @@ __device__ __forceinline__ void epilogue(const DedispArgs& a, const FusedArgs& f
 // that its strip holds; windows of a segment that begins before a strip boundary and
 // ends past it go to the seam pass (dd_fused.cu).
 
+// A warp's shared scratch for the earliest-start search: the chain values P_0 .. P_30 of
+// one segment, then P_{w0g} .. P_{w0g+45} (every P_s and P_{s+w} a width of the group
+// forms).
+constexpr int kChainFloats = 80;
+
 // Segment at x (kBoxSeg starts) for widths w0g + j, j < G; q = P_{w0g}.  !FULL: windows
 // ending past index e_rel are left out and no sample at or past it is read.  FULL
 // reads up to 15 samples past the last window of the group's widths below cnt.
@@ -317,19 +322,6 @@ __device__ __forceinline__ void scan_segment_f32(const float* x, float q, int w0
     }
 }
 
-// Earliest start s of the segment whose width-w sum equals m (the same chain), or -1.
-__device__ __noinline__ int find_start_f32(const float* x, int w, float m, int e_rel) {
-    auto ld = [&](int k) { return k < e_rel ? x[k] : 0.f; };
-    float r = 0.f, p = 0.f;
-    for (int k = 0; k < w; ++k) r += ld(k);
-    for (int s = 0; s < kBoxSeg; ++s) {
-        if (s + w <= e_rel && r - p == m) return s;
-        p += ld(s);
-        r += ld(s + w);
-    }
-    return -1;
-}
-
 // warp_max16 for fp32 maxima (fmaxf, as the unfused scan).
 __device__ __forceinline__ float warp_max16_f32(const float (&seg)[G], int lane) {
     const bool b4 = lane & 16, b3 = lane & 8, b2 = lane & 4, b1 = lane & 2;
@@ -350,9 +342,9 @@ __device__ __forceinline__ float warp_max16_f32(const float (&seg)[G], int lane)
 // The segments m_lo <= m < m_hi of one trial's row (row index of output t: t - base;
 // windows end at or before row index e_hi), 32 per warp pass, passes shared by the
 // nch warps of the trial's group.  Arguments are warp-uniform.
-__device__ __forceinline__ void scan_row_f32(int w0, int nw, const float* row, unsigned long long* keyrow,
-                                             int64_t base, int chunk, int nch, int lane, int64_t m_lo,
-                                             int64_t m_hi, int e_hi) {
+__device__ __forceinline__ void scan_row_f32(int w0, int nw, const float* row, float* chain,
+                                             unsigned long long* keyrow, int64_t base, int chunk, int nch,
+                                             int lane, int64_t m_lo, int64_t m_hi, int e_hi) {
     constexpr int S = kBoxSeg;
     __builtin_assume(__isShared(row));
     const int ng = (nw + G - 1) / G;
@@ -385,20 +377,42 @@ __device__ __forceinline__ void scan_row_f32(int w0, int nw, const float* row, u
             const float mx = warp_max16_f32(seg, lane);
             const bool better = !(lane & 1) && jl < cnt && mx > -FLT_MAX &&
                                 (mx > bv || (mx == bv && t_first < bt));
+            // widths whose maximum beats the merged one: the earliest segment holding it
+            // writes its chain to the warp's scratch, and the lanes test one start each for
+            // every such width that this segment holds first
             unsigned need = __ballot_sync(0xffffffffu, better);
-            while (need) {  // warp-uniform
-                const int hl = __ffs(need) - 1;
-                need &= need - 1;
+            auto holder = [&](int hl) {  // earliest lane whose segment holds width hl / 2's maximum
                 const int j = hl >> 1;
                 const float mj = __shfl_sync(0xffffffffu, mx, hl);
                 float sj = -FLT_MAX;
 #pragma unroll
                 for (int jj = 0; jj < G; ++jj) sj = jj == j ? seg[jj] : sj;
-                const unsigned hit = __ballot_sync(0xffffffffu, any && sj == mj);
-                if (lane == __ffs(hit) - 1) {
-                    const int st = find_start_f32(x, w0g + j, mj, e_rel);
-                    if (st >= 0) atomicMax(keyrow + g * G + j, fused_key_f32(mj, (int)(m * S) + st));
+                return __ffs(__ballot_sync(0xffffffffu, any && sj == mj)) - 1;
+            };
+            while (need) {  // warp-uniform
+                const int h = holder(__ffs(need) - 1);
+                if (lane == h) {
+                    float P = 0.f;
+                    for (int k = 0; k <= w0g + 45; ++k) {
+                        if (k < S) chain[k] = P;
+                        if (k >= w0g) chain[S + k - w0g] = P;
+                        P += k < e_rel ? x[k] : 0.f;
+                    }
                 }
+                __syncwarp();
+                const int eh = __shfl_sync(0xffffffffu, e_rel, h);
+                const int th = __shfl_sync(0xffffffffu, (int)(m * S), h);
+                for (unsigned rest = need; rest; rest &= rest - 1) {
+                    const int hl = __ffs(rest) - 1;
+                    if (holder(hl) != h) continue;  // held first by another segment: a later round
+                    const int j = hl >> 1;
+                    const float mj = __shfl_sync(0xffffffffu, mx, hl);
+                    const bool eq = lane < S && lane + w0g + j <= eh && chain[S + lane + j] - chain[lane] == mj;
+                    const unsigned st = __ballot_sync(0xffffffffu, eq);
+                    if (lane == 0 && st) atomicMax(keyrow + g * G + j, fused_key_f32(mj, th + __ffs(st) - 1));
+                    need &= ~(1u << hl);
+                }
+                __syncwarp();  // the scratch is rewritten for the next holder
             }
             if (any)
 #pragma unroll
@@ -410,8 +424,8 @@ __device__ __forceinline__ void scan_row_f32(int w0, int nw, const float* row, u
 // Carries, seams and the scan of a warp group's two trial rows (rows[u], trial d + u).
 // Not inlined: its registers are then allocated apart from the channel sums', which
 // keep the whole register file (the call comes once per tile).
-__device__ __noinline__ void scan_pair_rows_f32(float* rows, int rowlen, int w0, int nw, int C, int L,
-                                                unsigned long long* key, int ndm, int d, int cb0,
+__device__ __noinline__ void scan_pair_rows_f32(float* rows, float* chain, int rowlen, int w0, int nw, int C,
+                                                int L, unsigned long long* key, int ndm, int d, int cb0,
                                                 int chunk, int nch, int lane, int64_t base, int64_t m_lo,
                                                 int64_t m_hi, int e_hi, bool first, bool last,
                                                 float* carry, float* seam_in, float* seam_out) {
@@ -428,7 +442,7 @@ __device__ __noinline__ void scan_pair_rows_f32(float* rows, int rowlen, int w0,
             if (last && seam_out)
                 for (int k = lane; k < C; k += 32) seam_out[2 * cb + k] = row[e_hi - C + k];
         }
-        scan_row_f32(w0, nw, row, key + (int64_t)du * nw, base, chunk, nch, lane, m_lo, m_hi, e_hi);
+        scan_row_f32(w0, nw, row, chain, key + (int64_t)du * nw, base, chunk, nch, lane, m_lo, m_hi, e_hi);
     }
 }
 
@@ -465,8 +479,10 @@ __device__ __forceinline__ void epilogue_f32(const DedispArgs& a, const FusedArg
             for (int k = lane; k < C; k += 32) row[k] = carry[(int64_t)(wu * 2 + u) * C + k];
     }
     __syncthreads();  // the rows and their carries are complete
-    scan_pair_rows_f32(rows, f.rowlen, f.w0, f.nw, C, L, f.key, a.ndm, d, wu * 2, chunk, a.nch, lane, base,
-                       m_lo, m_hi, e_hi, first, last, carry, (float*)ft.seam_in, (float*)ft.seam_out);
+    // the warp's chain scratch lies behind the rows
+    float* chain = (float*)smem + fused_rows_ints(2 * kWarps / a.nch, f.rowlen, C) + (threadIdx.x >> 5) * kChainFloats;
+    scan_pair_rows_f32(rows, chain, f.rowlen, f.w0, f.nw, C, L, f.key, a.ndm, d, wu * 2, chunk, a.nch, lane,
+                       base, m_lo, m_hi, e_hi, first, last, carry, (float*)ft.seam_in, (float*)ft.seam_out);
     // the next tile's bulk copies overwrite the rows
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
     __syncthreads();

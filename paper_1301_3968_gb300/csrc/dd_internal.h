@@ -106,9 +106,9 @@ struct DedispArgs {
 
 // The boxcar scan fused into the dedispersion CTAs (contiguous widths w0 .. w0 + nw - 1;
 // dd_fused.cu).  The launch's items (trial block, time tile), block-major, are cut into
-// nparts contiguous parts, one CTA each.  A CTA walks its items in order and scans each
-// finished tile in shared memory, with the last C outputs of the previous tile of the
-// same block carried in front of it (through `carry`, a per-CTA global buffer).
+// nparts contiguous parts, one CTA each.  A CTA walks its part's items in order and
+// scans each finished tile in shared memory, with the last C outputs of the previous tile of the same block carried
+// in front of it (through `carry`, a per-part global buffer).
 // Windows that a part boundary inside a trial block separates from their data are
 // scanned afterwards from `seam`, which holds C outputs on each side of such a boundary.
 // Maxima are merged in `key` as (value, earliest start) packed into one 64-bit word.

@@ -670,16 +670,28 @@ def large_extra(dd, dev, flush, stream, chunk=1 << 18, nsamp=1 << 20, ndm=8192, 
     return res
 
 
+TRAFFIC_SOURCES = ["dd_tile.cuh", "dd_dedisp.cu", "dd_internal.h", "dd_packed.cuh", "dd_fused_scan.cuh",
+                   "dd_debug.cuh"]
+
+
+def kernel_source_sha():
+    """sha256 over the sources the dedispersion kernel is compiled from, in a fixed order."""
+    import hashlib
+    h = hashlib.sha256()
+    for name in TRAFFIC_SOURCES:
+        with open(os.path.join(ROOT, "paper_1301_3968_gb300", "csrc", name), "rb") as f:
+            h.update(f.read())
+    return h.hexdigest()
+
+
 def _profile_traffic():
     """DRAM bytes per dedispersion launch from the ncu capture recorded in
-    profiles/traffic.json, if it was taken on the current kernel source (else None)."""
-    import hashlib
+    profiles/traffic.json, if it was taken on the current kernel sources (else None)."""
     path = os.path.join(ROOT, "profiles", "traffic.json")
-    src = os.path.join(ROOT, "paper_1301_3968_gb300", "csrc", "dd_dedisp.cu")
     try:
         with open(path) as f:
             rec = json.load(f)["k_dedisp_f32_craft"]
-        sha = hashlib.sha256(open(src, "rb").read()).hexdigest()
+        sha = kernel_source_sha()
     except (OSError, KeyError, ValueError):
         return None
     if rec.get("source_sha256") != sha:

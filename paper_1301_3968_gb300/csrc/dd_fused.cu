@@ -292,8 +292,8 @@ size_t fused_smem_for(const dd_plan_s* p, int rowlen, int C) {
     // fp32 pair units: a row per trial; run-length path: a row per warp group and the
     // group's other trials' sums
     const int nrow = kWarps / p->nch * (p->pair ? 2 : 1);
-    // (fp32: and the warps' chain scratch of the earliest-start search)
-    const int spill = p->rl ? kWarps * (kRlUnits - 1) * chunk_t(false) : (p->pair ? kWarps * fused::kChainFloats : 0);
+    // and the warps' scratch of the earliest-start search
+    const int spill = (p->rl ? kWarps * (kRlUnits - 1) * chunk_t(false) : 0) + kWarps * fused::kChainFloats;
     const size_t rows = (size_t)(fused_rows_ints(nrow, rowlen, C) + spill) * 4 + nbuf * 8 + 2 * nbuf * 4;
     return (std::max(dedisp_smem_for(p), rows) + 15) & ~(size_t)15;
 }

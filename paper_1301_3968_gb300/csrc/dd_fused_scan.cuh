@@ -34,6 +34,11 @@ namespace {
 
 constexpr int G = 16;  // widths per register window
 
+// A warp's shared scratch for the earliest-start search (4-byte words): the prefix values
+// P_0 .. P_30 of one segment, then P_{w0g} .. P_{w0g+45} (every P_s and P_{s+w} that a
+// width of the group forms).
+constexpr int kChainFloats = 80;
+
 // S = kRInt starts of one lane segment (x = row + i0) for widths w0g + j, j < G.
 // q = sum_{k < w0g} x[k] on entry.  !FULL: starts outside [i_lo, i_hi) and windows
 // ending past row index e_hi are left out.
@@ -57,20 +62,6 @@ __device__ __forceinline__ void scan_segment(const int* x, uint32_t q, int w0g, 
         p += (uint32_t)x[s];
         win[s % G] = win[(s + G - 1) % G] + (uint32_t)x[s + w0g + G - 1];
     }
-}
-
-// Earliest start s of the segment whose width-w sum equals m (the same arithmetic as
-// scan_segment), or -1.
-__device__ __noinline__ int find_start(const int* x, int w, int m, int i0, int i_lo, int i_hi, int e_hi) {
-    uint32_t r = 0, p = 0;
-    for (int k = 0; k < w; ++k) r += (uint32_t)x[k];
-    for (int s = 0; s < kRInt; ++s) {
-        const int i = i0 + s;
-        if (i >= i_lo && i < i_hi && i + w <= e_hi && (int)(r - p) == m) return s;
-        p += (uint32_t)x[s];
-        r += (uint32_t)x[s + w];
-    }
-    return -1;
 }
 
 // Maximum over the warp of seg[j] for all j at once (each exchange level halves the
@@ -111,9 +102,9 @@ __device__ __forceinline__ long long group_bound(const int* x, uint32_t q, uint3
 constexpr int kPruneW = 48;
 
 // The scan of one row for one trial (warp-uniform arguments; see epilogue).
-__device__ __forceinline__ void scan_row(const FusedArgs& f, const int* row, unsigned long long* keyrow,
-                                      int64_t T0, int C, int chunk, int nch, int lane, int i_lo,
-                                      int i_hi, int e_hi) {
+__device__ __forceinline__ void scan_row(const FusedArgs& f, const int* row, uint32_t* chain,
+                                      unsigned long long* keyrow, int64_t T0, int C, int chunk, int nch,
+                                      int lane, int i_lo, int i_hi, int e_hi) {
     constexpr int R = kRInt, TT = 32 * R;
     __builtin_assume(__isShared(row));
     const int ng = (f.nw + G - 1) / G;
@@ -164,20 +155,45 @@ __device__ __forceinline__ void scan_row(const FusedArgs& f, const int* row, uns
                 const int mx = warp_max16(seg, lane);
                 const bool better = !(lane & 1) && jl < cnt && mx > INT_MIN &&
                                     (mx > bv || (mx == bv && t_lo < bt));
+                // widths whose maximum beats (or ties from an earlier start) the merged one:
+                // the earliest segment holding it writes its prefix values to the warp's
+                // scratch, and the lanes test one start each for every such width that this
+                // segment holds first
                 unsigned need = __ballot_sync(0xffffffffu, better);
-                while (need) {  // warp-uniform
-                    const int hl = __ffs(need) - 1;
-                    need &= need - 1;
+                auto holder = [&](int hl) {  // earliest lane whose segment holds width hl / 2's maximum
                     const int j = hl >> 1;
                     const int mj = __shfl_sync(0xffffffffu, mx, hl);
                     int sj = INT_MIN;
 #pragma unroll
                     for (int jj = 0; jj < G; ++jj) sj = jj == j ? seg[jj] : sj;
-                    const unsigned hit = __ballot_sync(0xffffffffu, scan && sj == mj);
-                    if (lane == __ffs(hit) - 1) {
-                        const int st = find_start(x, w0g + j, mj, i0, i_lo, i_hi, e_hi);
-                        if (st >= 0) atomicMax(keyrow + g * G + j, fused_key(mj, (int)(T0 - C) + i0 + st));
+                    return __ffs(__ballot_sync(0xffffffffu, scan && sj == mj)) - 1;
+                };
+                while (need) {  // warp-uniform
+                    const int h = holder(__ffs(need) - 1);
+                    if (lane == h) {
+                        uint32_t P = 0;
+                        for (int kk = 0; kk <= w0g + 45; ++kk) {
+                            if (kk < R) chain[kk] = P;
+                            if (kk >= w0g) chain[R + kk - w0g] = P;
+                            P += (uint32_t)x[kk];
+                        }
                     }
+                    __syncwarp();
+                    const int ih = __shfl_sync(0xffffffffu, i0, h);
+                    for (unsigned rest = need; rest; rest &= rest - 1) {
+                        const int hl = __ffs(rest) - 1;
+                        if (holder(hl) != h) continue;  // held first by another segment: a later round
+                        const int j = hl >> 1;
+                        const int mj = __shfl_sync(0xffffffffu, mx, hl);
+                        const int i = ih + lane;
+                        const bool eq = lane < R && i >= i_lo && i < i_hi && i + w0g + j <= e_hi &&
+                                        (int)(chain[R + lane + j] - chain[lane]) == mj;
+                        const unsigned st = __ballot_sync(0xffffffffu, eq);
+                        if (lane == 0 && st)
+                            atomicMax(keyrow + g * G + j, fused_key(mj, (int)(T0 - C) + ih + __ffs(st) - 1));
+                        need &= ~(1u << hl);
+                    }
+                    __syncwarp();  // the scratch is rewritten for the next holder
                 }
             }
             if (any)
@@ -225,6 +241,9 @@ __device__ __forceinline__ void epilogue(const DedispArgs& a, const FusedArgs& f
     for (int u = 1; u < NU; ++u)
 #pragma unroll
         for (int r = 0; r < R; ++r) spill[(u - 1) * TT + r] = accr[u - 1][r];
+    // the warp's scratch for the earliest-start search lies behind the spilled sums
+    uint32_t* chain = (uint32_t*)smem + fused_rows_ints(kWarps / a.nch, f.rowlen, C) + kWarps * (NU - 1) * TT +
+                      (threadIdx.x >> 5) * kChainFloats;
 #pragma unroll
     for (int u = 0; u < NU; ++u) {
         __syncthreads();  // the rows are free (stages consumed, or the previous trial scanned)
@@ -254,7 +273,7 @@ __device__ __forceinline__ void epilogue(const DedispArgs& a, const FusedArgs& f
             if (last && ft.seam_out)
                 for (int k = lane; k < C; k += 32) ft.seam_out[2 * cb + k] = row[e_hi - C + k];
         }
-        scan_row(f, row, f.key + (int64_t)du * f.nw, T0, C, chunk, a.nch, lane, i_lo, i_hi, e_hi);
+        scan_row(f, row, chain, f.key + (int64_t)du * f.nw, T0, C, chunk, a.nch, lane, i_lo, i_hi, e_hi);
     }
     // the next tile's bulk copies overwrite the rows
     asm volatile("fence.proxy.async.shared::cta;\n" ::: "memory");
@@ -274,11 +293,6 @@ __device__ __forceinline__ void epilogue(const DedispArgs& a, const FusedArgs& f
 // from the previous tile reach back to any such segment), and keeps the window ends
 // that its strip holds; windows of a segment that begins before a strip boundary and
 // ends past it go to the seam pass (dd_fused.cu).
-
-// A warp's shared scratch for the earliest-start search: the chain values P_0 .. P_30 of
-// one segment, then P_{w0g} .. P_{w0g+45} (every P_s and P_{s+w} a width of the group
-// forms).
-constexpr int kChainFloats = 80;
 
 // Segment at x (kBoxSeg starts) for widths w0g + j, j < G; q = P_{w0g}.  !FULL: windows
 // ending past index e_rel are left out and no sample at or past it is read.  FULL

@@ -283,7 +283,21 @@ void aligned_parts(int64_t nblk, int tiles, int nseg, std::vector<int64_t>* star
         for (int64_t b = 0; b < nblk; ++b) order->push_back(b * nseg + k);
 }
 
+// aligned_parts' cut with the blocks taken gb at a time: within a group of gb blocks the
+// parts go segment by segment, and the groups one after another, so that the CTAs
+// working together stay on about gb blocks (whose stage records then stay in L2).
+void grouped_parts(int64_t nblk, int tiles, int nseg, int64_t gb, std::vector<int64_t>* starts,
+                   std::vector<int64_t>* order) {
+    aligned_parts(nblk, tiles, nseg, starts, order);
+    order->clear();
+    for (int64_t g0 = 0; g0 < nblk; g0 += gb)
+        for (int k = 0; k < nseg; ++k)
+            for (int64_t b = g0; b < std::min(nblk, g0 + gb); ++b) order->push_back(b * nseg + k);
+}
+
 bool aligned16(const void* p) { return ((uintptr_t)p & 15) == 0; }
+
+constexpr int64_t kFusedGroup = 16;  // trial blocks per group of fp32 fused parts
 
 }  // namespace
 
@@ -399,13 +413,11 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
     const int64_t k_per = std::max<int64_t>(1, std::min<int64_t>(8, nblk * tiles / (16 * slots)));
     std::vector<int64_t> starts, order;
     int nparts = 0;
-    if (p->debug_fused_parts > 0 || fp) {
-        // parts of about equal cost in block-major order (cost of a tile: constant on the
-        // run-length path, the block's taps plus a per-channel constant otherwise): the
-        // test hook's count, or on fp32 plans k_per per resident CTA.  Block-major order
-        // keeps the stage records of the few trial blocks in progress in L2 (fp32 records
-        // hold every tap's weight pair: 139 MB for the 4096-trial CRAFT-like list)
-        nparts = (int)std::min<int64_t>(p->debug_fused_parts > 0 ? p->debug_fused_parts : k_per * slots, nitems);
+    if (p->debug_fused_parts > 0) {
+        // test hook: that many parts of about equal cost, in block-major order (cost of a
+        // tile: constant on the run-length path, the block's taps plus a per-channel
+        // constant on the direct path)
+        nparts = (int)std::min<int64_t>(p->debug_fused_parts, nitems);
         std::vector<double> cost((size_t)nblk, 1.0);
         if (!p->rl)
             for (int64_t b = 0; b < nblk; ++b) {
@@ -417,6 +429,14 @@ extern "C" dd_status dd_dedisperse_boxcar(dd_plan_t p, const void* in, int64_t i
         const double last_frac = (double)(t_out - (int64_t)(tiles - 1) * L) / L;
         starts = cut_parts(cost, tiles, last_frac, nparts);
         for (int i = 0; i < nparts; ++i) order.push_back(i);
+    } else if (fp) {
+        // fp32 stage records hold every tap's weight pair (544 kB per 16-trial block of the
+        // CRAFT-like list), so the CTAs working together must share few blocks: groups of
+        // kFusedGroup blocks, each block cut into as many segments as fill the resident CTAs
+        const int64_t gb = std::min<int64_t>(nblk, kFusedGroup);
+        const int nseg = (int)std::max<int64_t>(1, std::min<int64_t>(tiles, (slots + gb - 1) / gb));
+        grouped_parts(nblk, tiles, nseg, gb, &starts, &order);
+        nparts = (int)(starts.size() - 1);
     } else {
         // up to k_per parts per resident CTA, every block cut at the same time tiles and
         // taken segment by segment, so that the CTAs working together stage the same input

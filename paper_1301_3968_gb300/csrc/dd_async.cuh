@@ -1,6 +1,6 @@
-// Asynchronous global -> shared copies (cp.async, 4 bytes per thread and copy) for the
-// kernels that stage irregularly aligned rows one element at a time.  A copy with
-// ok == false writes zeros and reads nothing.
+// Asynchronous global -> shared copies (cp.async) of 4 or 16 bytes per thread and copy
+// for the kernels that stage irregularly aligned rows.  A 4-byte copy with ok == false
+// writes zeros and reads nothing.
 #pragma once
 
 #include <cstdint>
@@ -11,6 +11,14 @@ __device__ __forceinline__ void cp_async4(void* dst, const void* src, bool ok) {
     asm volatile("cp.async.ca.shared.global [%0], [%1], 4, %2;\n" ::"r"(
                      (uint32_t)__cvta_generic_to_shared(dst)),
                  "l"(src), "r"(ok ? 4 : 0)
+                 : "memory");
+}
+// 16 bytes (both addresses 16-byte aligned), of which the first nbytes are read and the
+// rest written as zeros.
+__device__ __forceinline__ void cp_async16(void* dst, const void* src, int nbytes) {
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(
+                     (uint32_t)__cvta_generic_to_shared(dst)),
+                 "l"(src), "r"(nbytes)
                  : "memory");
 }
 __device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::: "memory"); }

@@ -471,7 +471,7 @@ __global__ void __launch_bounds__(256, std::is_same<TB, float>::value ? 3 : 2) k
     const int w0_last = a.widths[((a.nw - 1) / G) * G];
     // two chunk buffers (sized for the launch's last width group): the next chunk's
     // copies are in flight while the current one is scanned
-    const int bufl = (256 * S + w0_last + G + 3) & ~3;
+    const int bufl = (256 * S + w0_last + G + 4 + 3) & ~3;
     TX* const xs0 = (TX*)smem_raw;
     TX* const xs1 = xs0 + bufl;
     const int wlast = w0 + cnt - 1;
@@ -488,15 +488,26 @@ __global__ void __launch_bounds__(256, std::is_same<TB, float>::value ? 3 : 2) k
     const int chunk = 256 * S;
     const int stage = chunk + w0 + G;
     const int ls = tid * S;
+    // 16-byte copies from the row's 16-byte boundaries: buffer element k holds series
+    // element tc - mis + k (chunks start at multiples of 4 elements)
+    const int mis = (int)(((uintptr_t)xrow >> 2) & 3);
     // the staged chunk fits its buffer and every width of the group fits the series
-    if (!dbg_ok(stage <= bufl && w0 >= 1 && wlast <= a.t_len, a.status)) return;
-    // past the end of the row the buffer holds zeros; only windows that run past the
+    if (!dbg_ok(stage + mis <= bufl && w0 >= 1 && wlast <= a.t_len, a.status)) return;
+    // pieces past the end of the row are not copied (their buffer words keep older
+    // values) and a piece that crosses it is zero-filled: only windows that run past the
     // series end read them, and those are excluded
     auto load = [&](int tc, TX* dst) {
-        for (int i = tid; i < stage; i += 256) {
-            const int t = tc + i;
-            const bool ok = t < a.t_len;
-            cp_async4(dst + i, ok ? xrow + t : xrow, ok);
+        const int n16 = (stage + mis + 3) >> 2;
+        for (int i = tid; i < n16; i += 256) {
+            const int t = tc - mis + 4 * i;  // first element of the piece
+            if (t < 0) {  // the row's first piece: nothing before the row is read
+                for (int k = -t; k < 4; ++k) {
+                    const bool ok = t + k < a.t_len;
+                    cp_async4(dst + 4 * i + k, ok ? xrow + t + k : xrow, ok);
+                }
+            } else if (t < a.t_len) {
+                cp_async16(dst + 4 * i, xrow + t, 4 * min(4, a.t_len - t));
+            }
         }
         cp_async_commit();
     };
@@ -514,9 +525,9 @@ __global__ void __launch_bounds__(256, std::is_same<TB, float>::value ? 3 : 2) k
 #pragma unroll
         for (int j = 0; j < G; ++j) seg[j] = lowest<TB>();
         if (tc + chunk - 1 + wlast <= a.t_len)
-            run_segment<TX, TB, true>(xs + ls, o, w0, tc + ls, a.t_len, seg);
+            run_segment<TX, TB, true>(xs + mis + ls, o, w0, tc + ls, a.t_len, seg);
         else if (tc + ls < tvalid)
-            run_segment<TX, TB, false>(xs + ls, o, w0, tc + ls, a.t_len, seg);
+            run_segment<TX, TB, false>(xs + mis + ls, o, w0, tc + ls, a.t_len, seg);
 #pragma unroll
         for (int j = 0; j < G; ++j) {
             if (seg[j] > best[j]) {
@@ -604,7 +615,7 @@ __global__ void __launch_bounds__(256, std::is_same<TB, float>::value ? 3 : 2) k
 
 template <typename TX, typename TB>
 dd_status run_boxcar_contig(const BoxArgs& a, int w0_last, cudaStream_t s) {
-    const size_t smem = (size_t)2 * ((256 * kBoxS + w0_last + kBoxG + 3) & ~3) * sizeof(TX);
+    const size_t smem = (size_t)2 * ((256 * kBoxS + w0_last + kBoxG + 4 + 3) & ~3) * sizeof(TX);
     auto kern = k_boxcar_run<TX, TB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);

@@ -479,7 +479,7 @@ def plain_extra(dd, dev, flush, stream, reps=20):
 
 def _batch_case(dd, dev, flush, stream, cfg, reps, tune, widths, graph=True):
     """Plans for a set of beams (default schedules timed one launch after another, then
-    autotuned), their persistent launch, and optionally the graph of the whole block."""
+    autotuned), their batched launch, and optionally the graph of the whole block."""
     import torch
     import synth
     b = cfg["band"]
@@ -545,7 +545,7 @@ def _batch_case(dd, dev, flush, stream, cfg, reps, tune, widths, graph=True):
 def batched_extra(dd, dev, flush, stream, reps=3, iadd_tops=None):
     """Batched configuration: 36 beams on the CRAFT band, uint8 in / int32 out, per-beam
     lengths 2^14-2^17 and 512-8192 trial DMs (seeded log-uniform), each plan autotuned.
-    One persistent launch (and the CUDA graph of the whole block, boxcars included)
+    One batched launch (and the CUDA graph of the whole block, boxcars included)
     against the same beams run one plain launch after another; the autotuner's gain over
     the default schedules; and 36 beams from the lower end of both ranges (2^14-2^15
     samples, 512-1024 trials), where each beam's own launch is a few waves."""

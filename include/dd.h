@@ -289,16 +289,17 @@ dd_status dd_plan_get_method(dd_plan_t plan, int32_t* method);
 dd_status dd_plan_autotune(dd_plan_t plan, const void* d_in, int64_t in_ld, void* d_out,
                            int64_t out_ld, const char* cache_path, float* best_ms, void* stream);
 
-/* Many beams in one persistent launch (uneven lengths and trial lists; no counterpart in
+/* Many beams in one launch (uneven lengths and trial lists; no counterpart in
  * the paper, which describes one beam).  Each beam has its own plan (the same input type
  * and tap-sum path for all: DD_ERR_ARG for mixed input types, DD_ERR_UNSUPPORTED for mixed
  * methods, or run-length beams longer than 2^24 samples; the plans must outlive the
  * batch); a beam's block is the band's nsamp samples from column 0.  The work list has
- * one item per CTA tile (beam, trial block, time tile), sorted by estimated cost, largest
- * first; the kernel's CTAs take items from an atomic counter that each launch resets.
+ * one item per CTA tile (beam, trial block, time tile), and the launch one CTA per item in
+ * list order: beams by decreasing estimated cost, each beam's tiles in the order of its
+ * own launch (dd_dedisperse).
  * Run-length beams first get their per-channel prefix sums (one small launch per beam,
  * into device memory the batch owns: 4 bytes per channel and sample, allocated by
- * dd_batch_bind), then the persistent launch sums them. */
+ * dd_batch_bind), then the batched launch sums them. */
 typedef struct dd_batch_s* dd_batch_t;
 dd_status dd_batch_create(dd_batch_t* batch, const dd_plan_t* plans, int32_t nbeams);
 /* Binds each beam's device input [nchan][in_ld] and output [ndm][out_ld] (host arrays of
@@ -306,8 +307,8 @@ dd_status dd_batch_create(dd_batch_t* batch, const dd_plan_t* plans, int32_t nbe
  * (allocates; synchronous).  Rebinding invalidates a captured graph. */
 dd_status dd_batch_bind(dd_batch_t batch, const void* const* d_in, const int64_t* in_ld,
                         void* const* d_out, const int64_t* out_ld);
-/* The persistent dedispersion launch for all bound beams (counter reset + kernel; on
- * run-length beams the prefix passes before it). */
+/* The batched dedispersion launch for all bound beams (on run-length beams the prefix
+ * passes before it). */
 dd_status dd_batch_dedisperse(dd_batch_t batch, void* stream);
 /* Binds, per beam, the outputs of the detection stage (boxcar widths shared by all beams;
  * device channel mean/std [nchan], peak S/N and peak time [ndm][nw]). */
@@ -322,7 +323,8 @@ dd_status dd_batch_run(dd_batch_t batch, void* stream);
  * the graph. */
 dd_status dd_batch_capture(dd_batch_t batch, void* stream);
 dd_status dd_batch_replay(dd_batch_t batch, void* stream);
-/* Work items, persistent grid size, and total trial x output samples of one block. */
+/* Work items, CTAs per launch (one per item), and total trial x output samples of one
+ * block. */
 dd_status dd_batch_info(dd_batch_t batch, int32_t* nitems, int32_t* grid, int64_t* units);
 dd_status dd_batch_destroy(dd_batch_t batch);
 

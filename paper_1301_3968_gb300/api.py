@@ -396,7 +396,7 @@ class Plan:
 
 
 class Batch:
-    """Many beams (one plan each) dedispersed in one persistent launch; optionally the
+    """Many beams (one plan each) dedispersed in one launch; optionally the
     beams' boxcar S/N too, and the whole block captured as a CUDA graph."""
 
     def __init__(self, plans):

@@ -1,12 +1,11 @@
-// Many beams in one persistent dedispersion launch, its CUDA graph, and the schedule
-// autotuner.
+// Many beams in one dedispersion launch, its CUDA graph, and the schedule autotuner.
 //
 // A batch holds one plan per beam (uneven trial counts, DM ranges and lengths).  Its
 // work list has one item per CTA tile of every beam -- (beam, trial block, time tile) --
-// sorted by estimated cost, largest first; the persistent kernel's CTAs take items from
-// an atomic counter, so long and short beams are balanced dynamically.  The graph
-// captures the counter reset, the persistent kernel and, when bound, every beam's
-// channel statistics and boxcar S/N, so one graph launch processes a block of all beams.
+// and the launch one CTA per item, in list order: beams by decreasing cost (the small
+// ones fill the last wave), each beam's tiles in the plain launch's grouped order.  The
+// graph captures the launch and, when bound, every beam's channel statistics and boxcar
+// S/N, so one graph launch processes a block of all beams.
 #include <algorithm>
 #include <cmath>
 #include <cstdio>
@@ -36,7 +35,6 @@ struct dd_batch_s {
     int64_t units = 0;  // sum over beams of trials x outputs
     dd::DedispArgs* d_args = nullptr;
     dd::BatchItem* d_items = nullptr;
-    int32_t* d_counter = nullptr;
     bool bound = false;
     // per-beam buffers bound for the boxcar stage of the graph
     std::vector<const void*> in;
@@ -64,55 +62,56 @@ void free_batch_dev(dd_batch_s* b) {
     b->ldp.clear();
     cudaFree(b->d_args);
     cudaFree(b->d_items);
-    cudaFree(b->d_counter);
     b->exec = nullptr;
     b->graph = nullptr;
     b->d_args = nullptr;
     b->d_items = nullptr;
-    b->d_counter = nullptr;
 }
 
 // Work list: one item per CTA tile, with the tile's FMA count (run-length beams: its
 // trial-channel pairs, each costing the same per output whatever its taps) plus a fixed
 // per-stage cost as the estimate; sorted largest first.
+// The work list: beams in decreasing order of estimated cost (so that the small ones fill
+// the last wave), and within a beam the plain launch's tile order: trial blocks taken
+// kGroupBlocks at a time, blocks fastest within a group and then time tiles, so that the
+// CTAs working together share the beam's input columns and stage records in L2.
 void build_items(dd_batch_s* b) {
-    struct Est {
+    constexpr int kGroupBlocks = 16;
+    struct Beam {
         double cost;
-        dd::BatchItem it;
+        int beam;
     };
-    std::vector<Est> all;
+    std::vector<Beam> order;
     b->units = 0;
     for (int beam = 0; beam < (int)b->plans.size(); ++beam) {
         const dd_plan_s* p = b->plans[beam];
-        const int tpw = p->pair ? 2 : (p->rl ? dd::kRlUnits : 1);
-        const int db = tpw * dd::kWarps / p->nch;
+        const int64_t t_out = plan_t_out(p);
+        const int nst = (p->nchan + p->cs - 1) / p->cs;
+        const int64_t tile = (int64_t)dd::chunk_t(p->pair) * p->nch;
+        const int64_t ntile = (t_out + tile - 1) / tile;
+        double taps = 0;
+        for (int64_t i = 0; i < (int64_t)p->ndm * p->nchan; ++i) taps += p->rl ? 1.0 : p->taps[(size_t)i];
+        b->units += (int64_t)p->ndm * t_out;
+        order.push_back({taps * (double)t_out + 2.0e4 * nst * ntile * p->nblk, beam});
+    }
+    std::stable_sort(order.begin(), order.end(), [](const Beam& x, const Beam& y) { return x.cost > y.cost; });
+    b->items.clear();
+    for (const Beam& bm : order) {
+        const dd_plan_s* p = b->plans[bm.beam];
         const int64_t t_out = plan_t_out(p);
         const int64_t tile = (int64_t)dd::chunk_t(p->pair) * p->nch;
         const int ntile = (int)((t_out + tile - 1) / tile);
-        const int nst = (p->nchan + p->cs - 1) / p->cs;
-        b->units += (int64_t)p->ndm * t_out;
-        for (int blk = 0; blk < p->nblk; ++blk) {
-            double taps = 0;
-            for (int i = 0; i < db; ++i) {
-                const int d = blk * db + i;
-                if (d >= p->ndm) break;
-                for (int c = 0; c < p->nchan; ++c) taps += p->rl ? 1.0 : p->taps[(size_t)d * p->nchan + c];
-            }
-            for (int tx = 0; tx < ntile; ++tx) {
-                const double len = (double)std::min<int64_t>(tile, t_out - (int64_t)tx * tile);
-                Est e;
-                e.cost = taps * len + 2.0e4 * nst;
-                e.it.beam = beam;
-                e.it.blk = blk;
-                e.it.tx = tx;
-                e.it.pad = 0;
-                all.push_back(e);
-            }
-        }
+        for (int g0 = 0; g0 < p->nblk; g0 += kGroupBlocks)
+            for (int tx = 0; tx < ntile; ++tx)
+                for (int blk = g0; blk < std::min(p->nblk, g0 + kGroupBlocks); ++blk) {
+                    dd::BatchItem it;
+                    it.beam = bm.beam;
+                    it.blk = blk;
+                    it.tx = tx;
+                    it.pad = 0;
+                    b->items.push_back(it);
+                }
     }
-    std::stable_sort(all.begin(), all.end(), [](const Est& x, const Est& y) { return x.cost > y.cost; });
-    b->items.resize(all.size());
-    for (size_t i = 0; i < all.size(); ++i) b->items[i] = all[i].it;
 }
 
 bool aligned16(const void* ptr) { return ((uintptr_t)ptr & 15u) == 0; }
@@ -195,11 +194,11 @@ dd_status dd_batch_bind(dd_batch_t b, const void* const* d_in, const int64_t* in
         b->short_taps = b->short_taps && (p->rl ? p->rl_b : p->pair ? p->umax <= dd::kRPair : p->kmax <= dd::kRInt);
     const int per_sm = dd::dedisp_batched_blocks_per_sm(b->u8, b->pair, b->short_taps, b->smem, b->rl);
     if (per_sm < 1) return DD_ERR_UNSUPPORTED;
-    b->grid = std::min<int>(per_sm * sms, (int)b->items.size());
+    if (b->items.size() >= (size_t)INT32_MAX) return DD_ERR_UNSUPPORTED;
+    b->grid = (int)b->items.size();  // one CTA per work item
     b->device = dev;
     e = cudaMalloc((void**)&b->d_args, nb * sizeof(dd::DedispArgs));
     if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_items, b->items.size() * sizeof(dd::BatchItem));
-    if (e == cudaSuccess) e = cudaMalloc((void**)&b->d_counter, sizeof(int32_t));
     if (e == cudaSuccess)
         e = cudaMemcpy(b->d_args, args.data(), nb * sizeof(dd::DedispArgs), cudaMemcpyHostToDevice);
     if (e == cudaSuccess)
@@ -215,9 +214,9 @@ dd_status dd_batch_bind(dd_batch_t b, const void* const* d_in, const int64_t* in
     b->out_ld.assign(out_ld, out_ld + nb);
     b->bound = true;
     b->box_bound = false;
-    dd::log_msg(1, "batch of %d beams (%s): %zu work items, persistent grid %d CTAs, %zu bytes of shared memory",
-             nb, b->rl ? "run-length sums" : (b->pair ? "fp32 pair units" : "exact integer sums"), b->items.size(),
-             b->grid, b->smem);
+    dd::log_msg(1, "batch of %d beams (%s): %zu work items (one CTA each, %d resident per SM on %d SMs), "
+             "%zu bytes of shared memory", nb, b->rl ? "run-length sums" : (b->pair ? "fp32 pair units" : "exact integer sums"),
+             b->items.size(), per_sm, sms, b->smem);
     return DD_OK;
 }
 
@@ -233,7 +232,7 @@ dd_status dd_batch_dedisperse(dd_batch_t b, void* stream) {
             if (st != DD_OK) return st;
         }
     return dd::launch_dedisperse_batched(b->u8, b->pair, b->short_taps, b->d_args, b->d_items, (int32_t)b->items.size(),
-                                         b->d_counter, b->smem, b->grid, (cudaStream_t)stream, b->rl);
+                                         b->smem, (cudaStream_t)stream, b->rl);
 }
 
 dd_status dd_batch_bind_boxcar(dd_batch_t b, const int32_t* widths, int32_t nw, double* const* d_mean,
@@ -256,7 +255,7 @@ dd_status dd_batch_bind_boxcar(dd_batch_t b, const int32_t* widths, int32_t nw, 
     return DD_OK;
 }
 
-// Runs one block of every beam: the persistent dedispersion launch and, when bound,
+// Runs one block of every beam: the batched dedispersion launch and, when bound,
 // every beam's channel statistics and boxcar S/N.
 static dd_status batch_run(dd_batch_s* b, cudaStream_t s) {
     dd_status st = dd_batch_dedisperse(b, s);

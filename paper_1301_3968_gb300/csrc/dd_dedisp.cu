@@ -32,32 +32,26 @@ __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp(DedispArgs a) {
     }
 }
 
-// Persistent form: each CTA takes work items (beam, trial block, time tile) from an
-// atomic counter until none remain.  Items are sorted by estimated cost, largest
-// first, so the uneven beams finish together.  The counter is reset before each launch.
+// Batched form: one CTA per work item (beam, trial block, time tile) of the list, in list
+// order (beams by decreasing cost, each in the plain grid's tile order); the hardware
+// starts CTAs in index order as earlier ones finish, which balances uneven beams.
+// Measured on 36 beams: a persistent form whose CTAs took items from an atomic counter
+// was 3.6 % slower (and slower than separate launches).
 template <typename TIN, bool PAIR, int NBUF, int SHORT>
 __global__ void __launch_bounds__(kWarps * 32, 2) k_dedisp_batched(const DedispArgs* beams,
                                                                     const BatchItem* items,
-                                                                    int32_t nitems, int32_t* counter,
                                                                     uint32_t smem_bytes) {
     extern __shared__ __align__(128) unsigned char smem[];
     __shared__ TileState ts;
     __shared__ DedispArgs sa;
-    __shared__ int s_item;
     if (threadIdx.x == 0) init_pipeline<NBUF>(pipeline_area(smem, smem_bytes, NBUF), ts);
-    for (;;) {
-        if (threadIdx.x == 0) s_item = atomicAdd(counter, 1);
-        __syncthreads();
-        const int item = s_item;
-        if (item >= nitems) break;
-        const BatchItem it = items[item];
-        if (threadIdx.x == 0) {
-            sa = beams[it.beam];
-            sa.smem_bytes = smem_bytes;
-        }
-        __syncthreads();
-        if (!dedisp_tile<TIN, PAIR, NBUF, true, SHORT>(sa, smem, it.blk, it.tx, ts)) break;
+    const BatchItem it = items[blockIdx.x];
+    if (threadIdx.x == 0) {
+        sa = beams[it.beam];
+        sa.smem_bytes = smem_bytes;
     }
+    __syncthreads();
+    dedisp_tile<TIN, PAIR, NBUF, false, SHORT>(sa, smem, it.blk, it.tx, ts);
 }
 
 template <typename TIN, bool PAIR, int NBUF, int SHORT = 0>
@@ -81,17 +75,15 @@ dd_status run(DedispArgs a, cudaStream_t s) {
 }
 
 template <typename TIN, bool PAIR, int NBUF, int SHORT = 0>
-dd_status run_batched(const DedispArgs* d_args, const BatchItem* d_items, int32_t nitems,
-                      int32_t* d_counter, size_t smem, int grid, cudaStream_t s) {
+dd_status run_batched(const DedispArgs* d_args, const BatchItem* d_items, int32_t nitems, size_t smem,
+                      cudaStream_t s) {
     auto kern = k_dedisp_batched<TIN, PAIR, NBUF, SHORT>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
-    e = cudaMemsetAsync(d_counter, 0, sizeof(int32_t), s);
-    if (e != cudaSuccess) return cuda_status(e);
-    kern<<<grid, kWarps * 32, smem, s>>>(d_args, d_items, nitems, d_counter, (uint32_t)smem);
+    if (nitems < 1) return DD_OK;
+    kern<<<(unsigned)nitems, kWarps * 32, smem, s>>>(d_args, d_items, (uint32_t)smem);
     return cuda_status(cudaGetLastError());
 }
-
 
 template <typename TIN, bool PAIR, int NBUF, int SHORT = 0>
 int blocks_per_sm(size_t smem) {
@@ -307,19 +299,19 @@ dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t
 }
 
 dd_status launch_dedisperse_batched(bool u8, bool pair, bool short_taps, const DedispArgs* d_args,
-                                    const BatchItem* d_items, int32_t nitems, int32_t* d_counter,
-                                    size_t smem, int grid, cudaStream_t s, bool rl) {
+                                    const BatchItem* d_items, int32_t nitems, size_t smem, cudaStream_t s,
+                                    bool rl) {
     if (rl)  // run-length beams: short_taps = difference rows shared by the CTA
-        return short_taps ? run_batched<uint32_t, false, kStagesRl, 1>(d_args, d_items, nitems, d_counter, smem, grid, s)
-                          : run_batched<uint32_t, false, kStagesRl>(d_args, d_items, nitems, d_counter, smem, grid, s);
+        return short_taps ? run_batched<uint32_t, false, kStagesRl, 1>(d_args, d_items, nitems, smem, s)
+                          : run_batched<uint32_t, false, kStagesRl>(d_args, d_items, nitems, smem, s);
     if (!pair)
-        return short_taps ? run_batched<uint8_t, false, kStagesInt, 1>(d_args, d_items, nitems, d_counter, smem, grid, s)
-                          : run_batched<uint8_t, false, kStagesInt>(d_args, d_items, nitems, d_counter, smem, grid, s);
+        return short_taps ? run_batched<uint8_t, false, kStagesInt, 1>(d_args, d_items, nitems, smem, s)
+                          : run_batched<uint8_t, false, kStagesInt>(d_args, d_items, nitems, smem, s);
     if (u8)
-        return short_taps ? run_batched<uint8_t, true, kStagesPair, 1>(d_args, d_items, nitems, d_counter, smem, grid, s)
-                          : run_batched<uint8_t, true, kStagesPair>(d_args, d_items, nitems, d_counter, smem, grid, s);
-    return short_taps ? run_batched<float, true, kStagesPair, 1>(d_args, d_items, nitems, d_counter, smem, grid, s)
-                      : run_batched<float, true, kStagesPair>(d_args, d_items, nitems, d_counter, smem, grid, s);
+        return short_taps ? run_batched<uint8_t, true, kStagesPair, 1>(d_args, d_items, nitems, smem, s)
+                          : run_batched<uint8_t, true, kStagesPair>(d_args, d_items, nitems, smem, s);
+    return short_taps ? run_batched<float, true, kStagesPair, 1>(d_args, d_items, nitems, smem, s)
+                      : run_batched<float, true, kStagesPair>(d_args, d_items, nitems, smem, s);
 }
 
 int dedisp_batched_blocks_per_sm(bool u8, bool pair, bool short_taps, size_t smem, bool rl) {

@@ -268,8 +268,8 @@ size_t dedisp_smem_for(const dd_plan_s* p);
 dd_status launch_dedisperse_rl(dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
                                int64_t nsamp, void* out, int64_t out_ld, cudaStream_t s);
 dd_status launch_dedisperse_batched(bool u8, bool pair, bool short_taps, const DedispArgs* d_args,
-                                    const BatchItem* d_items, int32_t nitems, int32_t* d_counter,
-                                    size_t smem, int grid, cudaStream_t s, bool rl = false);
+                                    const BatchItem* d_items, int32_t nitems, size_t smem, cudaStream_t s,
+                                    bool rl = false);
 int dedisp_batched_blocks_per_sm(bool u8, bool pair, bool short_taps, size_t smem, bool rl = false);
 dd_status launch_prefix_into(const dd_plan_s* p, const void* in, int64_t ld, int64_t t_offset,
                              int64_t nsamp, uint32_t* P, int64_t ldp, cudaStream_t s);

@@ -59,7 +59,7 @@ def test_batched_equals_per_beam_and_oracle(dd):
         rows = [0, plan.ndm // 2, plan.ndm - 1]
         want = oracle.c_dedisperse(data, delay, taps, nsamp=plan.band.nsamp, rows=rows)
         np.testing.assert_array_equal(o.cpu().numpy()[rows].astype(np.int64), want)
-    # a second launch (the work counter is reset) gives the same result
+    # a second launch gives the same result
     before = [o.clone() for _, _, o, _ in beams]
     for _, _, o, _ in beams:
         o.zero_()
@@ -176,7 +176,7 @@ def _rl_beams(dd, n=5, seed=47, share_rows=True):
 
 @pytest.mark.parametrize("share_rows", [True, False])
 def test_batched_runlength_equals_per_beam_and_oracle(dd, share_rows):
-    """Run-length beams in one persistent launch (prefix passes first) give the per-beam
+    """Run-length beams in one batched launch (prefix passes first) give the per-beam
     run-length sums bit for bit, sampled rows equal the oracle, and the graph replay
     repeats them."""
     import torch
@@ -217,7 +217,7 @@ def test_batch_refuses_mixed_methods(dd):
 
 def test_batched_fp32_weighted_equals_per_beam_and_oracle(dd):
     """fp32 weighted beams (pair units with each trial's own run in the shared window) in
-    one persistent launch: bit for bit the per-beam launches, sampled rows within the fp32
+    one batched launch: bit for bit the per-beam launches, sampled rows within the fp32
     tolerance of the oracle, and the graph replay repeats them."""
     import torch
     rng = np.random.default_rng(71)

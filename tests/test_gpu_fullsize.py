@@ -26,7 +26,7 @@ def _dev(a):
 
 
 def test_batched_36_beams_full_size(dd):
-    """36 beams of 2^14-2^17 samples and 512-8192 trials, uint8 -> int32, one persistent
+    """36 beams of 2^14-2^17 samples and 512-8192 trials, uint8 -> int32, one batched
     launch: three rows of every beam bit-exact against the oracle."""
     import torch
     cfg = synth.make_batched_beams()

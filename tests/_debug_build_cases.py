@@ -86,6 +86,30 @@ def main():
         _emit(f"runlength_{'rows' if share else 'pairs'}", plan.device_status(),
               float(np.abs(out[rows].astype(np.int64) - want).max()))
         plan.close()
+    # 4. the fused boxcar scan on an integer and an fp32 plan (five parts, so seams too):
+    # err 0 when its peaks and starts equal the unfused path's bit for bit
+    for kind in ("u8", "f32"):
+        C, T, D = 24, 6000, 30
+        plan = dd.Plan(dd.Band(C, 1200.0, 1.0, 1.0, T, kind), np.zeros(D))
+        delay = rng.integers(0, 300, size=(D, C)).astype(np.int32)
+        taps = rng.integers(1, 20, size=(D, C)).astype(np.int32)
+        w = None if kind == "u8" else (rng.standard_normal((D, C, 19)) * 0.5 + 1.0).astype(np.float32)
+        plan.set_profiles(delay=delay, taps=taps, weights=w)
+        if kind == "u8":
+            data = rng.integers(0, 256, size=(C, T)).astype(np.uint8)
+        else:
+            data = rng.standard_normal((C, T)).astype(np.float32)
+        x = torch.from_numpy(data).cuda()
+        mean, sd = plan.channel_stats(x, nsamp=T)
+        widths = np.arange(1, 33, dtype=np.int32)
+        plan.test_set_fused_parts(5)
+        out = plan.dedisperse(x, nsamp=T)
+        p0, a0, _ = plan.boxcar_snr(out, widths, mean, sd)
+        p1, a1, _ = plan.dedisperse_boxcar(x, widths, mean, sd, nsamp=T)
+        same = (np.array_equal(p0.cpu().numpy().view(np.int32), p1.cpu().numpy().view(np.int32))
+                and np.array_equal(a0.cpu().numpy(), a1.cpu().numpy()))
+        _emit(f"fused_{kind}", plan.device_status(), 0.0 if same else 1.0)
+        plan.close()
 
 
 if __name__ == "__main__":

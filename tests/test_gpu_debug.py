@@ -1,7 +1,7 @@
 """The debug build (libdd_debug.so: bounds checks on every staged window and output store
-of the dedispersion and boxcar kernels, recording DD_ERR_ARG in the plan's device status
-word instead of faulting) on small cases of every path: status 0 and results equal to the
-oracle.  Runs in a child process, since a process loads one of the two libraries."""
+of the dedispersion (plain, batched and fused) and boxcar kernels, recording DD_ERR_ARG in
+the plan's device status word instead of faulting) on small cases of every path: status 0
+and results equal to the oracle (the fused scan: equal to the unfused path).  Runs in a child process, since a process loads one of the two libraries."""
 import json
 import os
 import subprocess
@@ -23,10 +23,12 @@ def test_debug_build_clean_on_every_path():
     assert res.returncode == 0, res.stderr[-3000:]
     cases = {d["case"]: d for d in (json.loads(ln) for ln in res.stdout.splitlines() if ln.startswith("{"))}
     assert set(cases) == {"plain_int_w16", "plain_int_w6", "craft_f32_pairs", "craft_f32_adjoint",
-                          "runlength_rows", "runlength_pairs"}
+                          "runlength_rows", "runlength_pairs", "fused_u8", "fused_f32"}
     for name, d in cases.items():
         assert d["status"] == 0, (name, d)
-        if name.startswith("plain_int") or name.startswith("runlength"):
+        if name.startswith("fused"):
+            assert d["err"] == 0.0, (name, d)        # fused = unfused, bit for bit
+        elif name.startswith("plain_int") or name.startswith("runlength"):
             assert d["err"] < 1e-5, (name, d)        # integer sums exact, S/N to 1e-5
         else:
             assert d["err"] < 1e-5, (name, d)        # fp32: scale-aware 1e-5

@@ -249,6 +249,7 @@ struct BoxArgs {
     const uint8_t* narrow;
     int32_t narrow_sel;
     int32_t* status;  // the plan's device status word (debug-build bounds checks)
+    int32_t gpc;      // k_boxcar_run: width groups per CTA (1, 2 or 4)
 };
 
 template <typename T>
@@ -452,8 +453,12 @@ __device__ __forceinline__ void run_segment(const TX* xl, TX o, int w0, int t0, 
     }
 }
 
-// fp32: three CTAs per SM (80 registers, 72 bytes spilled), 8 % faster than two with no
-// spills on the CRAFT-like series (1.283 -> 1.185 ms with the normaliser).
+// grid (CTAs of gpc width groups, trials).  The CTA's warps split into gpc groups of
+// 8 / gpc warps; all of them scan the same staged chunk of 32 * (8 / gpc) * S samples,
+// each group for its own 16 widths, so a row is read once per gpc groups.  Thread
+// segments still start at multiples of S (chunks are whole segments).  fp32: three CTAs
+// per SM (80 registers, 72 bytes spilled), 8 % faster than two with no spills on the
+// CRAFT-like series (1.283 -> 1.185 ms with the normaliser).
 template <typename TX, typename TB>
 __global__ void __launch_bounds__(256, std::is_same<TB, float>::value ? 3 : 2) k_boxcar_run(BoxArgs a) {
     constexpr int S = kBoxS, G = kBoxG;
@@ -464,14 +469,22 @@ __global__ void __launch_bounds__(256, std::is_same<TB, float>::value ? 3 : 2) k
     __shared__ int rt[8][G];
     const int d = blockIdx.y;
     if (a.narrow && (int)a.narrow[d] != a.narrow_sel) return;
-    const int j0 = blockIdx.x * G;
-    const int cnt = min(G, a.nw - j0);
     const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+    const int gpc = a.gpc, wpg = 8 / gpc, tpg = 32 * wpg;  // groups per CTA, warps and threads per group
+    const int ng = (a.nw + G - 1) / G;
+    const int gi = warp / wpg, gt = tid - gi * tpg;      // this thread's group in the CTA, index in it
+    const int g = blockIdx.x * gpc + gi;                  // its width group (>= ng: idle)
+    const int g_first = blockIdx.x * gpc, g_last = min(ng, g_first + gpc) - 1;
+    const bool active = g < ng;
+    const int j0 = (active ? g : g_last) * G;
+    const int cnt = min(G, a.nw - j0);
     const int w0 = a.widths[j0];
-    const int w0_last = a.widths[((a.nw - 1) / G) * G];
+    const int w0_first = a.widths[g_first * G], w0_cta = a.widths[g_last * G];
+    const int w0_last = a.widths[(ng - 1) * G];
+    const int chunk = tpg * S;
     // two chunk buffers (sized for the launch's last width group): the next chunk's
     // copies are in flight while the current one is scanned
-    const int bufl = (256 * S + w0_last + G + 4 + 3) & ~3;
+    const int bufl = (chunk + w0_last + G + 4 + 3) & ~3;
     TX* const xs0 = (TX*)smem_raw;
     TX* const xs1 = xs0 + bufl;
     const int wlast = w0 + cnt - 1;
@@ -485,14 +498,14 @@ __global__ void __launch_bounds__(256, std::is_same<TB, float>::value ? 3 : 2) k
         bch[j] = -1;
     }
     const int tvalid = a.t_len - w0 + 1;
-    const int chunk = 256 * S;
-    const int stage = chunk + w0 + G;
-    const int ls = tid * S;
+    const int tvalid_cta = a.t_len - w0_first + 1;  // the CTA's longest scan
+    const int stage = chunk + w0_cta + G;
+    const int ls = gt * S;
     // 16-byte copies from the row's 16-byte boundaries: buffer element k holds series
     // element tc - mis + k (chunks start at multiples of 4 elements)
     const int mis = (int)(((uintptr_t)xrow >> 2) & 3);
     // the staged chunk fits its buffer and every width of the group fits the series
-    if (!dbg_ok(stage + mis <= bufl && w0 >= 1 && wlast <= a.t_len, a.status)) return;
+    if (!dbg_ok(stage + mis <= bufl && w0 >= 1 && wlast <= a.t_len && (chunk & 3) == 0, a.status)) return;
     // pieces past the end of the row are not copied (their buffer words keep older
     // values) and a piece that crosses it is zero-filled: only windows that run past the
     // series end read them, and those are excluded
@@ -512,9 +525,9 @@ __global__ void __launch_bounds__(256, std::is_same<TB, float>::value ? 3 : 2) k
         cp_async_commit();
     };
     load(0, xs0);
-    for (int ci = 0, tc = 0; tc < tvalid; ++ci, tc += chunk) {
+    for (int ci = 0, tc = 0; tc < tvalid_cta; ++ci, tc += chunk) {
         TX* const xs = (ci & 1) ? xs1 : xs0;
-        if (tc + chunk < tvalid) {
+        if (tc + chunk < tvalid_cta) {
             load(tc + chunk, (ci & 1) ? xs0 : xs1);
             cp_async_wait<1>();
         } else {
@@ -524,9 +537,9 @@ __global__ void __launch_bounds__(256, std::is_same<TB, float>::value ? 3 : 2) k
         TB seg[G];
 #pragma unroll
         for (int j = 0; j < G; ++j) seg[j] = lowest<TB>();
-        if (tc + chunk - 1 + wlast <= a.t_len)
+        if (active && tc + chunk - 1 + wlast <= a.t_len)
             run_segment<TX, TB, true>(xs + mis + ls, o, w0, tc + ls, a.t_len, seg);
-        else if (tc + ls < tvalid)
+        else if (active && tc + ls < tvalid)
             run_segment<TX, TB, false>(xs + mis + ls, o, w0, tc + ls, a.t_len, seg);
 #pragma unroll
         for (int j = 0; j < G; ++j) {
@@ -537,12 +550,12 @@ __global__ void __launch_bounds__(256, std::is_same<TB, float>::value ? 3 : 2) k
         }
         __syncthreads();  // this buffer is reloaded by the next iteration but one
     }
-    // (max, earliest chunk, earliest thread) over the CTA
+    // (max, earliest chunk, earliest thread) over each group's warps
 #pragma unroll
     for (int j = 0; j < G; ++j) {
         TB b = best[j];
         int c = bch[j];
-        int t = tid;
+        int t = gt;
 #pragma unroll
         for (int ofs = 16; ofs > 0; ofs >>= 1) {
             const TB ob = __shfl_xor_sync(0xffffffffu, b, ofs);
@@ -561,11 +574,12 @@ __global__ void __launch_bounds__(256, std::is_same<TB, float>::value ? 3 : 2) k
         }
     }
     __syncthreads();
-    if (tid < cnt) {
-        const int j = tid;
-        TB b = rb[0][j];
-        int c = rc[0][j], th = rt[0][j];
-        for (int k = 1; k < 8; ++k) {
+    if (active && gt < cnt) {
+        const int j = gt;
+        const int k0 = gi * wpg;
+        TB b = rb[k0][j];
+        int c = rc[k0][j], th = rt[k0][j];
+        for (int k = k0 + 1; k < k0 + wpg; ++k) {
             const TB ob = rb[k][j];
             const int oc = rc[k][j], ot = rt[k][j];
             if (oc >= 0 && (c < 0 || ob > b || (ob == b && (oc < c || (oc == c && ot < th))))) {
@@ -613,13 +627,19 @@ __global__ void __launch_bounds__(256, std::is_same<TB, float>::value ? 3 : 2) k
     }
 }
 
+// Width groups per CTA: up to four (a row is read once per four groups; chunks of 31 x 64
+// samples or more, so that the w0_last + 16 staged beyond a chunk stay a small share).
 template <typename TX, typename TB>
-dd_status run_boxcar_contig(const BoxArgs& a, int w0_last, cudaStream_t s) {
-    const size_t smem = (size_t)2 * ((256 * kBoxS + w0_last + kBoxG + 4 + 3) & ~3) * sizeof(TX);
+dd_status run_boxcar_contig(const BoxArgs& a0, int w0_last, cudaStream_t s) {
+    BoxArgs a = a0;
+    const int ng = (a.nw + kBoxG - 1) / kBoxG;
+    a.gpc = ng >= 4 ? 4 : (ng >= 2 ? 2 : 1);
+    const int chunk = 32 * (8 / a.gpc) * kBoxS;
+    const size_t smem = (size_t)2 * ((chunk + w0_last + kBoxG + 4 + 3) & ~3) * sizeof(TX);
     auto kern = k_boxcar_run<TX, TB>;
     cudaError_t e = cudaFuncSetAttribute(kern, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)smem);
     if (e != cudaSuccess) return cuda_status(e);
-    dim3 grid((unsigned)((a.nw + kBoxG - 1) / kBoxG), (unsigned)a.ndm);
+    dim3 grid((unsigned)((ng + a.gpc - 1) / a.gpc), (unsigned)a.ndm);
     if (grid.y > 65535) return DD_ERR_UNSUPPORTED;
     kern<<<grid, 256, smem, s>>>(a);
     return cuda_status(cudaGetLastError());

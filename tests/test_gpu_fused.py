@@ -351,3 +351,35 @@ def test_fused_f32_reduced_craft(dd):
     assert plan.device_status() == 0
     np.testing.assert_array_equal(a1.cpu().numpy(), a0.cpu().numpy())
     np.testing.assert_array_equal(_bits(p1), _bits(p0))
+
+
+@pytest.mark.parametrize("kind", ["u8", "f32"])
+@pytest.mark.parametrize("t_out", [1, 30, 31, 40, 863, 864, 865, 992, 993])
+def test_fused_short_series(dd, kind, t_out):
+    """Series shorter than, equal to and one past a tile (864 fp32 / 992 integer outputs)
+    and a boxcar segment (31): fused = unfused, widths up to the series length (or the
+    longest one whose carry fits a tile)."""
+    rng = np.random.default_rng(100 + t_out)
+    C, D, K = 12, 20, 3
+    delay = rng.integers(0, 4, size=(D, C)).astype(np.int32)
+    taps = rng.integers(1, K + 1, size=(D, C)).astype(np.int32)
+    T = t_out + int((delay + taps - 1).max())
+    ld = (T + 15) // 16 * 16
+    plan = dd.Plan(dd.Band(C, 1200.0, 1.0, 1.0, T, kind), np.zeros(D))
+    w = None if kind == "u8" else (rng.standard_normal((D, C, K)) * 0.5 + 1.0).astype(np.float32)
+    plan.set_profiles(delay=delay, taps=taps, weights=w)
+    if kind == "u8":
+        I = np.zeros((C, ld), np.uint8)
+        I[:, :T] = rng.integers(0, 256, size=(C, T))
+    else:
+        I = np.zeros((C, ld), np.float32)
+        I[:, :T] = rng.standard_normal((C, T))
+    x = _dev(I)
+    mean, sd = plan.channel_stats(x, nsamp=T)
+    wcap = 835 if kind == "f32" else 993  # the longest width whose carry fits a tile
+    for widths in (np.arange(1, min(32, t_out) + 1, dtype=np.int32), np.array([min(t_out, wcap)], np.int32)):
+        p0, a0, _ = _unfused(plan, x, widths, mean, sd, 0, T)
+        p1, a1, _ = plan.dedisperse_boxcar(x, widths, mean, sd, nsamp=T)
+        assert plan.device_status() == 0
+        np.testing.assert_array_equal(a1.cpu().numpy(), a0.cpu().numpy())
+        np.testing.assert_array_equal(_bits(p1), _bits(p0))

@@ -19,8 +19,9 @@
 // exact while every window sum of x - o fits int32 (checked per output against mlim;
 // DD_ERR_OVERFLOW otherwise).  A warp reduction gives the tile's maximum per width;
 // only where it beats (or ties from an earlier start) the merged maximum read from
-// `key` does the first lane holding it rescan its segment for the earliest start and
-// merge (value, start) with one 64-bit atomicMax.
+// `key` is the earliest start searched -- the earliest segment holding the maximum
+// writes its prefix values to the warp's scratch and the lanes test one start each --
+// and (value, start) merged with one 64-bit atomicMax.
 #pragma once
 
 #include <cfloat>

@@ -823,7 +823,7 @@ def run_reference(args):
     value = rows_per_step * t_out / (el / args.steps)
     return {
         "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": 1, "steps": args.steps,
-        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "weak",
+        "warmup": args.warmup, "ms_per_step": ms, "higher_is_better": True, "scaling": "strong",
         "vs_baseline": None, "dtype": "f64", "data": "synthetic", "impl": "reference",
         "config": {"workload": "CRAFT-like: 336 ch x 1 MHz, dt 1 ms, 65536 fp32 samples, 4096 trial "
                                "DMs 0-4000 (eq. trial DMs), weights ~ nu^-1.4, boxcar widths 1-32",

@@ -383,3 +383,39 @@ def test_fused_short_series(dd, kind, t_out):
         assert plan.device_status() == 0
         np.testing.assert_array_equal(a1.cpu().numpy(), a0.cpu().numpy())
         np.testing.assert_array_equal(_bits(p1), _bits(p0))
+
+
+@pytest.mark.parametrize("kind", ["u8", "f32"])
+def test_fused_call_replays_in_a_cuda_graph(dd, kind):
+    """After one eager call (which sends the part tables and widths), the fused call captures
+    into a CUDA graph; replays on new input data give the eager call's results for that data."""
+    import torch
+    rng = np.random.default_rng(120)
+    C, T, D = 16, 6000, 24
+    plan = dd.Plan(dd.Band(C, 1200.0, 1.0, 1.0, T, kind), np.zeros(D))
+    delay = rng.integers(0, 200, size=(D, C)).astype(np.int32)
+    taps = rng.integers(1, 12, size=(D, C)).astype(np.int32)
+    w = None if kind == "u8" else (rng.standard_normal((D, C, 11)) * 0.5 + 1.0).astype(np.float32)
+    plan.set_profiles(delay=delay, taps=taps, weights=w)
+
+    def data():
+        if kind == "u8":
+            return rng.integers(0, 256, size=(C, T)).astype(np.uint8)
+        return rng.standard_normal((C, T)).astype(np.float32)
+
+    x = _dev(data())
+    mean, sd = plan.channel_stats(x, nsamp=T)
+    widths = np.arange(1, 41, dtype=np.int32)
+    plan.dedisperse_boxcar(x, widths, mean, sd, nsamp=T)       # eager: tables on the device
+    torch.cuda.synchronize()
+    g = torch.cuda.CUDAGraph()
+    with torch.cuda.graph(g):
+        gp, ga, _ = plan.dedisperse_boxcar(x, widths, mean, sd, nsamp=T)
+    for _ in range(2):
+        x.copy_(_dev(data()))
+        g.replay()
+        torch.cuda.synchronize()
+        p0, a0, _ = plan.dedisperse_boxcar(x, widths, mean, sd, nsamp=T)
+        assert plan.device_status() == 0
+        np.testing.assert_array_equal(ga.cpu().numpy(), a0.cpu().numpy())
+        np.testing.assert_array_equal(_bits(gp), _bits(p0))
